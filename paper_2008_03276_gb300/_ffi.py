@@ -1,0 +1,63 @@
+"""ctypes view of the C ABI in ``include/ehl.h`` (argument marshalling only).
+
+The shared library is loaded from ``_lib/libehl_gb300.so`` next to this file.
+There is no fallback: if the library is missing or cannot be loaded, every
+entry point raises.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+EHL_OK, EHL_EINVAL, EHL_ENOMEM, EHL_ECUDA, EHL_ENOCONV, EHL_ENONFINITE, EHL_ESINGULAR, EHL_ETIMEOUT = range(8)
+
+# every symbol the header declares; the CPU tests check the library exports them
+SYMBOLS = {
+    "ehl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ehl_version": (ctypes.c_int, []),
+    "ehl_paqif_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+    "ehl_paqif_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+class EhlError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)}")
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load (building first if needed) and return the ctypes library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"EHL CUDA library not found at {path}; run paper_2008_03276_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SYMBOLS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(code):
+    return load().ehl_status_string(int(code)).decode()
+
+
+def check(code, where):
+    if code != EHL_OK:
+        raise EhlError(code, where)

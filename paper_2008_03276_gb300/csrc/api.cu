@@ -1,0 +1,82 @@
+// api.cu -- the extern "C" entry points of include/ehl.h: argument checks,
+// workspace carving and kernel launches.  No compute happens on the host.
+#include <cuda_runtime.h>
+
+#include "ehl_internal.h"
+
+using namespace ehl;
+
+extern "C" const char* ehl_status_string(ehl_status s) {
+  switch (s) {
+    case EHL_OK: return "EHL_OK";
+    case EHL_EINVAL: return "EHL_EINVAL: invalid argument";
+    case EHL_ENOMEM: return "EHL_ENOMEM: device allocation failed";
+    case EHL_ECUDA: return "EHL_ECUDA: CUDA runtime error";
+    case EHL_ENOCONV: return "EHL_ENOCONV: iteration limit reached";
+    case EHL_ENONFINITE: return "EHL_ENONFINITE: NaN or Inf";
+    case EHL_ESINGULAR: return "EHL_ESINGULAR: singular 2x2 pivot";
+    case EHL_ETIMEOUT: return "EHL_ETIMEOUT: bounded device wait expired";
+  }
+  return "EHL_?: unknown status";
+}
+
+extern "C" int ehl_version(void) { return 100; }
+
+static bool paqif_args_ok(int n_sys, int n, int beta, int mode) {
+  return n_sys >= 1 && n_sys <= (1 << 24) && n >= 1 && n <= (1 << 24) && beta >= 1 && beta <= 8 && mode >= 0 &&
+         mode <= 2;
+}
+
+static size_t paqif_act_bytes(int n_sys, int n) { return (size_t)n_sys * (size_t)n * sizeof(int); }
+
+extern "C" ehl_status ehl_paqif_workspace_size(int n_sys, int n, int beta, int mode, size_t* bytes) {
+  if (!bytes || !paqif_args_ok(n_sys, n, beta, mode)) return EHL_EINVAL;
+  *bytes = align_up(paqif_stack_bytes(n_sys, n, beta), kWorkspaceAlign) +
+           align_up(paqif_act_bytes(n_sys, n), kWorkspaceAlign);
+  return EHL_OK;
+}
+
+extern "C" ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* band, const double* rhs,
+                                      const uint8_t* active, int mode, double* x, int* iters, int* info,
+                                      void* workspace, size_t workspace_bytes, void* stream) {
+  if (!band || !rhs || !x || !paqif_args_ok(n_sys, n, beta, mode)) return EHL_EINVAL;
+  if ((const void*)x == (const void*)band || (const void*)x == (const void*)rhs) return EHL_EINVAL;
+  size_t need = 0;
+  ehl_paqif_workspace_size(n_sys, n, beta, mode, &need);
+  cudaStream_t st = (cudaStream_t)stream;
+  bool owned = false;
+  if (workspace) {
+    if (workspace_bytes < need || ((uintptr_t)workspace % kWorkspaceAlign) != 0) return EHL_EINVAL;
+  } else {
+    if (cudaMallocAsync(&workspace, need, st) != cudaSuccess) {
+      cudaGetLastError();
+      return EHL_ENOMEM;
+    }
+    owned = true;
+  }
+  unsigned char* ws = (unsigned char*)workspace;
+  PaqifLaunch L;
+  L.n_sys = n_sys;
+  L.n = n;
+  L.beta = beta;
+  L.mode = mode;
+  L.band = band;
+  L.rhs = rhs;
+  L.stack = ws;
+  L.act = nullptr;
+  L.x = x;
+  L.iters = iters;
+  L.info = info;
+  cudaError_t e = cudaSuccess;
+  if (active || mode == 2) {
+    L.act = (int*)(ws + align_up(paqif_stack_bytes(n_sys, n, beta), kWorkspaceAlign));
+    e = launch_expand_active(active, L.act, (size_t)n_sys * (size_t)n, st);
+  }
+  if (e == cudaSuccess) e = launch_paqif(L, st);
+  if (owned) cudaFreeAsync(workspace, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return EHL_ECUDA;
+  }
+  return EHL_OK;
+}

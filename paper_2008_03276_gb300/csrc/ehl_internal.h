@@ -1,0 +1,33 @@
+// ehl_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/ehl.h"
+
+namespace ehl {
+
+constexpr int kPaqifWarpsPerCta = 4;
+constexpr int kPaqifMaxActiveSetSteps = 64;
+constexpr size_t kWorkspaceAlign = 256;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct PaqifLaunch {
+  int n_sys, n, beta, mode;
+  const double* band;
+  const double* rhs;
+  int* act;     // int32 flags [n_sys][n] or nullptr
+  void* stack;  // paqif_stack_bytes() bytes, 16-byte aligned
+  double* x;
+  int* iters;
+  int* info;
+};
+
+// Bytes of the per-system Z-stack (padded to whole CTAs); 0 for a bad beta.
+size_t paqif_stack_bytes(int n_sys, int n, int beta);
+cudaError_t launch_paqif(const PaqifLaunch& L, cudaStream_t st);
+cudaError_t launch_expand_active(const uint8_t* in, int* out, size_t total, cudaStream_t st);
+
+}  // namespace ehl

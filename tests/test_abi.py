@@ -1,0 +1,49 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+function that include/ehl.h declares; host-side argument checks return
+EHL_EINVAL without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2008_03276_gb300 import _ffi
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ehl.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ehl_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_functions():
+    names = declared_functions()
+    assert "ehl_paqif_solve" in names and "ehl_status_string" in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _ffi.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _ffi.SYMBOLS, f"{name} has no ctypes signature"
+
+
+def test_status_strings():
+    for code in range(8):
+        assert _ffi.status_string(code).startswith("EHL_")
+    assert "unknown" in _ffi.status_string(99)
+
+
+def test_host_side_argument_checks():
+    lib = _ffi.load()
+    nb = ctypes.c_size_t(0)
+    assert lib.ehl_paqif_workspace_size(4, 16, 0, 0, ctypes.byref(nb)) == _ffi.EHL_EINVAL
+    assert lib.ehl_paqif_workspace_size(4, 16, 9, 0, ctypes.byref(nb)) == _ffi.EHL_EINVAL
+    assert lib.ehl_paqif_workspace_size(4, 16, 2, 3, ctypes.byref(nb)) == _ffi.EHL_EINVAL
+    assert lib.ehl_paqif_workspace_size(4, 16, 2, 0, ctypes.byref(nb)) == _ffi.EHL_OK and nb.value > 0
+    null = ctypes.c_void_p(0)
+    # NULL band / rhs / x are rejected before any CUDA call
+    assert lib.ehl_paqif_solve(4, 16, 2, null, null, null, 0, null, null, null, null, 0, null) == _ffi.EHL_EINVAL
+    assert lib.ehl_version() >= 100
