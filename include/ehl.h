@@ -100,6 +100,39 @@ ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* band, const
                            const uint8_t* active, int mode, double* x, int* iters, int* info,
                            void* workspace, size_t workspace_bytes, void* stream);
 
+/* ------------------------------------------------------------------------
+ * PAQIF without any allocation
+ * ------------------------------------------------------------------------
+ * The paper has no counterpart to this entry point: it exists for callers
+ * that cannot allocate device memory while they solve -- for example a host
+ * program whose own pool owns the whole GPU and forbids other allocations, a
+ * plug-in running inside another application's callback where allocation is
+ * not allowed, or a real-time loop that may neither wait on the allocator nor
+ * fail with out-of-memory halfway through a run.
+ *
+ * Same arguments, semantics and results as ehl_paqif_solve, without the
+ * workspace arguments: the scratch lives in one fixed device array of
+ * EHL_PAQIF_STATIC_SCRATCH_BYTES that the library reserves on every GPU that
+ * loads it, until the process exits.  The call allocates and frees nothing.
+ *
+ *  - Size limit: returns EHL_EINVAL when ehl_paqif_workspace_size() for the
+ *    batch exceeds EHL_PAQIF_STATIC_SCRATCH_BYTES (for example n_sys = 128,
+ *    n = 1024, beta = 4 needs about 10 MB and fits; 4096 such systems do not).
+ *  - Set-up: the first call on each device looks up the array's device
+ *    address (cudaGetSymbolAddress) with that device current and caches it;
+ *    make that first call before any stream capture.  A failed lookup returns
+ *    EHL_ECUDA.
+ *  - Sharing: all calls on a device use the same array and it keeps the last
+ *    call's contents.  Each call overwrites every scratch word it reads, so no
+ *    clearing is needed, but calls whose GPU work overlaps in time (different
+ *    streams, or other host threads) race on the array: serialise them.
+ */
+#define EHL_PAQIF_STATIC_SCRATCH_BYTES (16u << 20)
+
+ehl_status ehl_paqif_solve_static(int n_sys, int n, int beta, const double* band, const double* rhs,
+                                  const uint8_t* active, int mode, double* x, int* iters, int* info,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif
