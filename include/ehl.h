@@ -101,6 +101,95 @@ ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* band, const
                            void* workspace, size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * EHL problem: context, residual, band Jacobian, solve
+ * ------------------------------------------------------------------------
+ * The problem statement is the paper's: given load and lubricant parameters
+ * and a grid, find P >= 0 and the film H satisfying the Reynolds
+ * complementarity problem with force balance (Sec. 3.3, Examples 5 and 6;
+ * Sec. 3.3.4, Eq. eqn75).  Line contact (dim = 1), in Hertzian units:
+ *   H_i = H0 + X_i^2/2 - sum_k K_{|i-k|} P_k + rough_i,  K_d = G_d / pi with
+ *   the closed-form cell integral G_d of log|x - x'| (Sec. 3.3.1);
+ *   R_i = (F_{i+1/2} - F_{i-1/2})/h - [eps_{i+1/2}(P_{i+1}-P_i)
+ *         - eps_{i-1/2}(P_i-P_{i-1})]/h^2, F the limited face value of rho H
+ *   (Sec. 3.3.3), eps = rho H^3 / (eta lambda) with Roelands eta and
+ *   Dowson-Higginson rho;  P_i >= 0, R_i >= 0, P_i R_i = 0;  h sum P = pi/2.
+ * lambda and alpha_bar = alpha p_H come from the Moes parameters:
+ *   lambda = 3 pi^2 / (8 M^2), alpha_bar = L sqrt(M / (2 pi)).
+ *
+ * Arrays of one context with n_inst instances of nx nodes are [n_inst][nx]
+ * (nodal, including the two boundary nodes where P = 0), [n_inst] for H0.
+ */
+typedef struct ehl_ctx ehl_ctx;
+
+typedef struct {
+  int dim;              /* 1: line contact                                              */
+  int nx, ny;           /* nodes incl. boundary nodes (ny = 1 for line contact)         */
+  double xa, xb, ya, yb;/* domain                                                        */
+  double M, L;          /* Moes load and lubricant parameters                           */
+  double alpha;         /* pressure-viscosity coefficient [1/Pa] (1.7e-8)               */
+  double p0, z;         /* Roelands constants (1.98e8, 0.68)                            */
+  int compressible;     /* 1: Roelands + Dowson-Higginson; 0: rho = eta = 1             */
+  int elastic;          /* 1: elastic deformation; 0: rigid surfaces                    */
+  int limiter;          /* 0: minmod, 1: van Leer                                       */
+  int halfband;         /* half-bandwidth beta of the band Jacobian, 1..8               */
+  double switch_eps_h;  /* eps/h threshold of the hybrid splitting (0.6)                */
+  double dist_weight;   /* weighted-change share per neighbour (line 0.5)               */
+  double c_h0;          /* relaxation c of the force-balance H0 update (0.05)           */
+  double omega;         /* relaxation of the pressure change (1.0)                      */
+  int method;           /* 0: the paper's band Newton relaxation                        */
+                        /* 1: Newton-Krylov, PAQIF band preconditioner (default)         */
+  double tol;           /* converged when ||min(P,R)||_inf <= tol and |h sum P - pi/2| <= tol */
+  int max_iter;         /* cap on outer iterations                                      */
+  int krylov_dim;       /* GMRES basis size per Newton step (method 1)                  */
+  double h_init;        /* Hertzian start: H0 chosen so that min H = h_init             */
+} ehl_params;
+
+/* Fill *p with the defaults above for dimension `dim` (1). */
+void ehl_params_default(ehl_params* p, int dim);
+
+/* Create a context for n_inst instances.  `p` gives the shared settings; if
+ * per_inst is not NULL it gives per-instance parameters (n_inst entries; nx,
+ * dim, halfband and method must equal p's).  The context owns its device
+ * workspace (allocated here with cudaMalloc) and enqueues on `stream`.
+ * Returns EHL_EINVAL for invalid parameters (nx < 5 or > 65536, beta outside
+ * 1..8, M <= 0, xb <= xa, ...), EHL_ENOMEM, EHL_ECUDA. */
+ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_params* per_inst, void* stream, ehl_ctx** out);
+
+/* Release the context and its device memory (synchronises its stream). */
+ehl_status ehl_destroy(ehl_ctx* ctx);
+
+/* Residual at (P, H0): R [n_inst][nx] (0 at boundary nodes), H (nullable)
+ * [n_inst][nx] film thickness, comp_res (nullable) [n_inst][2] =
+ * (||min(P,R)||_inf over interior nodes, h sum P - pi/2).  rough nullable.
+ * Asynchronous. */
+ehl_status ehl_residual(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, double* R,
+                        double* H, double* comp_res);
+
+/* Band Jacobian at (P, H0), rows/columns = interior nodes (n = nx - 2),
+ * band [n_inst][n][2 beta + 1] in the PAQIF row-major layout, active
+ * [n_inst][n] uint8.
+ *  kind 0: the paper's limiter-based Newton matrix (Sec. 3.3.3-3.3.4):
+ *          eps, rho and the limiter factor frozen, the film change through
+ *          the kernel, the weighted-change distribution on the subregion
+ *          eps/h <= switch_eps_h, truncated to the band; cavitated rows
+ *          (P = 0, R > 0) are identity rows (active = 1).
+ *  kind 1: the band of the exact Jacobian dR/dP; rows with
+ *          P_i <= R_i / |dR_i/dP_i| are identity rows (active = 1).
+ * Asynchronous. */
+ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, int kind,
+                             double* band, uint8_t* active);
+
+/* Solve every instance.  init = 0: start from the Hertzian pressure with
+ * H0 chosen so that min H = h_init; init = 1: start from the given P, H0.
+ * On return P, H0 hold the last iterate, iters (nullable, [n_inst] int32)
+ * the outer iterations and final_res (nullable, [n_inst][2]) the residuals
+ * as in ehl_residual.  Synchronises the stream (to test convergence).
+ * Returns EHL_OK if every instance converged, EHL_ENOCONV if some reached
+ * max_iter, EHL_ENONFINITE if some produced NaN/Inf. */
+ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const double* rough, int init, int* iters,
+                     double* final_res);
+
+/* ------------------------------------------------------------------------
  * PAQIF without any allocation
  * ------------------------------------------------------------------------
  * The paper has no counterpart to this entry point: it exists for callers

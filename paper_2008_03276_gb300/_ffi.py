@@ -9,6 +9,20 @@ import os
 
 from . import build as _build
 
+class EhlParams(ctypes.Structure):
+    """Mirror of ``ehl_params`` in include/ehl.h (same field order and types)."""
+
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("xa", ctypes.c_double), ("xb", ctypes.c_double), ("ya", ctypes.c_double), ("yb", ctypes.c_double),
+                ("M", ctypes.c_double), ("L", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("p0", ctypes.c_double), ("z", ctypes.c_double),
+                ("compressible", ctypes.c_int), ("elastic", ctypes.c_int), ("limiter", ctypes.c_int),
+                ("halfband", ctypes.c_int), ("switch_eps_h", ctypes.c_double), ("dist_weight", ctypes.c_double),
+                ("c_h0", ctypes.c_double), ("omega", ctypes.c_double), ("method", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("krylov_dim", ctypes.c_int),
+                ("h_init", ctypes.c_double)]
+
+
 EHL_OK, EHL_EINVAL, EHL_ENOMEM, EHL_ECUDA, EHL_ENOCONV, EHL_ENONFINITE, EHL_ESINGULAR, EHL_ETIMEOUT = range(8)
 
 # every symbol the header declares; the CPU tests check the library exports them
@@ -20,6 +34,16 @@ SYMBOLS = {
     "ehl_paqif_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "ehl_params_default": (None, [ctypes.POINTER(EhlParams), ctypes.c_int]),
+    "ehl_create": (ctypes.c_int, [ctypes.POINTER(EhlParams), ctypes.c_int, ctypes.POINTER(EhlParams),
+                                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "ehl_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "ehl_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ehl_jacobian_band": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "ehl_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                 ctypes.c_void_p, ctypes.c_void_p]),
     "ehl_paqif_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),

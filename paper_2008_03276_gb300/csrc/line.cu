@@ -1,0 +1,556 @@
+// line.cu -- line-contact hot path (Sec. 3.3): closed-form kernel table,
+// double-float Toeplitz deformation, float64 lubricant model and TVD residual,
+// the band Jacobians, and the paper's limiter-based Newton-Raphson relaxation.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <vector>
+
+#include "df64.cuh"
+#include "ehl_internal.h"
+#include "line_kernels.cuh"
+#include "line.h"
+
+namespace ehl {
+
+constexpr int kDefTI = 64;    // outputs per deformation CTA
+constexpr int kDefSK = 128;   // sources per deformation CTA
+constexpr int kNodeBlock = 256;
+
+// max that keeps a NaN operand (fmax would drop it)
+__device__ __forceinline__ double nan_max(double a, double b) { return (a > b || a != a) ? a : b; }
+
+// ---------------------------------------------------------------- kernel table
+__global__ void k_line_gtab(const LineInst* __restrict__ inst, float2* __restrict__ gtab, int N) {
+  const int z = blockIdx.y;
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= N) return;
+  const double g = line_cell_integral(d, inst[z].h) / M_PI;
+  const df v = df_from_double(g);
+  gtab[(size_t)z * N + d] = make_float2(v.hi, v.lo);
+}
+
+// ---------------------------------------------------------------- deformation
+// partial[y][z][i] = sum_{k in chunk y} K_{|i-k|} V[z][k]   (double-float, Ogita-Rump-Oishi Dot2 sum)
+__global__ void __launch_bounds__(kDefTI) k_line_deform(const LineInst* __restrict__ inst,
+                                                        const float2* __restrict__ gtab,
+                                                        const double* __restrict__ V, int vstride,
+                                                        const int* __restrict__ skip, float2* __restrict__ partial,
+                                                        int n_inst, int N) {
+  const int z = blockIdx.z;
+  if (skip && skip[z]) return;
+  const int i0 = blockIdx.x * kDefTI, k0 = blockIdx.y * kDefSK;
+  const int tid = threadIdx.x;
+  float2* out = partial + ((size_t)blockIdx.y * n_inst + z) * N;
+  if (!inst[z].elastic) {
+    if (i0 + tid < N) out[i0 + tid] = make_float2(0.f, 0.f);
+    return;
+  }
+  __shared__ float2 Vs[kDefSK];
+  __shared__ float2 Gs[kDefTI + kDefSK - 1];
+  for (int t = tid; t < kDefSK; t += kDefTI) {
+    const int k = k0 + t;
+    df v = (k < N) ? df_from_double(V[(size_t)z * vstride + k]) : df_zero();
+    Vs[t] = make_float2(v.hi, v.lo);
+  }
+  const int base_d = i0 - (k0 + kDefSK - 1);
+  for (int m = tid; m < kDefTI + kDefSK - 1; m += kDefTI) {
+    int d = base_d + m;
+    d = d < 0 ? -d : d;
+    Gs[m] = (d < N) ? gtab[(size_t)z * N + d] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int i = i0 + tid;
+  if (i >= N) return;
+  float s = 0.f, c = 0.f;
+  const int kmax = min(kDefSK, N - k0);
+#pragma unroll 4
+  for (int k = 0; k < kmax; ++k) {
+    const float2 g = Gs[tid + kDefSK - 1 - k];
+    const float2 v = Vs[k];
+    const float p = __fmul_rn(g.x, v.x);
+    float e = __fmaf_rn(g.x, v.x, -p);
+    e = __fmaf_rn(g.x, v.y, e);
+    e = __fmaf_rn(g.y, v.x, e);
+    float t1, t2;
+    two_sum(s, p, t1, t2);
+    s = t1;
+    c = __fadd_rn(c, __fadd_rn(t2, e));
+  }
+  float hi, lo;
+  fast_two_sum(s, c, hi, lo);
+  out[i] = make_float2(hi, lo);
+}
+
+// mode 0: H = H0 + X^2/2 - D + rough;  mode 1: out = -D + dh0 (directional derivative of H)
+__global__ void k_line_film(const LineInst* __restrict__ inst, const float2* __restrict__ partial, int ksplit,
+                            const double* __restrict__ H0, const double* __restrict__ rough, int rstride,
+                            const int* __restrict__ skip, double* __restrict__ out, int n_inst, int N, int mode) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  df D = df_zero();
+  for (int y = 0; y < ksplit; ++y) {
+    const float2 p = partial[((size_t)y * n_inst + z) * N + i];
+    D = df_add(D, make_df(p.x, p.y));
+  }
+  const double Dd = df_to_double(D);
+  if (mode == 0) {
+    const double X = inst[z].xa + i * inst[z].h;
+    double H = H0[z] + 0.5 * X * X - Dd;
+    if (rough) H += rough[(size_t)z * rstride + i];
+    out[(size_t)z * N + i] = H;
+  } else {
+    out[(size_t)z * N + i] = -Dd + (H0 ? H0[z] : 0.0);
+  }
+}
+
+// ---------------------------------------------------------------- lubricant state
+__global__ void k_line_nodes(const LineInst* __restrict__ inst, const double* __restrict__ P,
+                             const double* __restrict__ H, const int* __restrict__ skip, double* __restrict__ rho,
+                             double* __restrict__ drho, double* __restrict__ deta_rel, double* __restrict__ eps,
+                             double* __restrict__ u, int N) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const LineInst q = inst[z];
+  const size_t o = (size_t)z * N + i;
+  double r, dr, ln_eta, de;
+  line_material(q, P[o], r, dr, ln_eta, de);
+  const double Hh = H[o];
+  rho[o] = r;
+  drho[o] = dr;
+  deta_rel[o] = de;
+  eps[o] = r * Hh * Hh * Hh / q.lam * exp(-ln_eta);
+  u[o] = r * Hh;
+}
+
+// faces j = 0..N-2: limited face value and limiter derivatives
+__global__ void k_line_faces(const LineInst* __restrict__ inst, const double* __restrict__ u,
+                             const int* __restrict__ skip, double* __restrict__ F, double* __restrict__ psi,
+                             double* __restrict__ psia, double* __restrict__ psib, int N) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N - 1) return;
+  const size_t o = (size_t)z * N + j;
+  double ps = 0.0, pa = 0.0, pb = 0.0;
+  if (j >= 1) line_limiter(inst[z].limiter, u[o] - u[o - 1], u[o + 1] - u[o], ps, pa, pb);
+  F[o] = u[o] + 0.5 * ps;
+  psi[o] = ps;
+  psia[o] = pa;
+  psib[o] = pb;
+}
+
+// residual at interior nodes; block partials of max|min(P,R)|, sum P and min H
+__global__ void __launch_bounds__(kNodeBlock) k_line_residual(const LineInst* __restrict__ inst,
+                                                              const double* __restrict__ P,
+                                                              const double* __restrict__ H,
+                                                              const double* __restrict__ eps,
+                                                              const double* __restrict__ F,
+                                                              const int* __restrict__ skip, double* __restrict__ R,
+                                                              double* __restrict__ blk, int nblk, int N) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double h = inst[z].h;
+  double cres = 0.0, sp = 0.0, hmin = INFINITY;
+  if (i < N) {
+    const size_t o = (size_t)z * N + i;
+    hmin = H[o];
+    if (i >= 1 && i <= N - 2) {
+      const double C = (F[o] - F[o - 1]) / h;
+      const double ef1 = 0.5 * (eps[o] + eps[o + 1]);
+      const double ef0 = 0.5 * (eps[o - 1] + eps[o]);
+      const double Q = (ef1 * (P[o + 1] - P[o]) - ef0 * (P[o] - P[o - 1])) / (h * h);
+      const double r = C - Q;
+      R[o] = r;
+      cres = fabs(P[o] < r ? P[o] : r);  // NaN in r propagates
+      sp = P[o];
+    } else {
+      R[o] = 0.0;
+    }
+  }
+  __shared__ double s_c[kNodeBlock], s_s[kNodeBlock], s_h[kNodeBlock];
+  s_c[threadIdx.x] = cres;
+  s_s[threadIdx.x] = sp;
+  s_h[threadIdx.x] = hmin;
+  __syncthreads();
+  for (int w = kNodeBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s_c[threadIdx.x] = nan_max(s_c[threadIdx.x], s_c[threadIdx.x + w]);
+      s_s[threadIdx.x] += s_s[threadIdx.x + w];
+      s_h[threadIdx.x] = fmin(s_h[threadIdx.x], s_h[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double* b = blk + ((size_t)z * nblk + blockIdx.x) * 4;
+    b[0] = s_c[0];
+    b[1] = s_s[0];
+    b[2] = s_h[0];
+  }
+}
+
+// red[z] = (max|min(P,R)|, h sum P - pi/2, sum P, min H); convergence flag and iteration count
+__global__ void k_line_finalize(const LineInst* __restrict__ inst, const double* __restrict__ blk, int nblk,
+                                double* __restrict__ red, int* __restrict__ done, int* __restrict__ iters,
+                                int n_inst) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= n_inst) return;
+  if (done && done[z]) return;
+  double c = 0.0, s = 0.0, hm = INFINITY;
+  for (int b = 0; b < nblk; ++b) {
+    const double* p = blk + ((size_t)z * nblk + b) * 4;
+    c = nan_max(c, p[0]);
+    s += p[1];
+    hm = fmin(hm, p[2]);
+  }
+  const double force = inst[z].h * s - 0.5 * M_PI;
+  red[z * 4 + 0] = c;
+  red[z * 4 + 1] = force;
+  red[z * 4 + 2] = s;
+  red[z * 4 + 3] = hm;
+  if (done) {
+    if (c <= inst[z].tol && fabs(force) <= inst[z].tol) {
+      done[z] = 1;
+    } else if (!(c == c) || !(force == force)) {
+      done[z] = 2;  // non-finite: stop this instance
+    } else if (iters) {
+      iters[z] += 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- band Jacobians
+struct LineRowCtx {
+  const double *rho, *drho, *deta_rel, *eps, *u, *H, *P, *psi, *psia, *psib;
+  const float2* gtab;
+  size_t base;  // z * N
+  int N;
+  double h;
+  __device__ double K(int d) const {
+    d = d < 0 ? -d : d;
+    if (d >= N) return 0.0;
+    const float2 g = gtab[base + d];
+    return (double)g.x + (double)g.y;
+  }
+  // frozen limiter factor phi_j = psi_j / (u_j - u_{j-1})
+  __device__ double phi(int j) const {
+    if (j < 1) return 0.0;
+    const double a = u[base + j] - u[base + j - 1];
+    return a != 0.0 ? psi[base + j] / a : 0.0;
+  }
+  // frozen face derivative dF_{j+1/2}/dP_m (rho, phi, eps frozen)
+  __device__ double dF_frozen(int j, int m) const {
+    if (j == 0) return -rho[base] * K(0 - m);
+    const double ph = phi(j);
+    return -rho[base + j] * (1.0 + 0.5 * ph) * K(j - m) + 0.5 * ph * rho[base + j - 1] * K(j - 1 - m);
+  }
+  __device__ double J_frozen(int i, int m, double ef0, double ef1) const {
+    double dC = (dF_frozen(i, m) - dF_frozen(i - 1, m)) / h;
+    double dQ = 0.0;
+    if (m == i + 1) dQ = ef1 / (h * h);
+    if (m == i) dQ = -(ef1 + ef0) / (h * h);
+    if (m == i - 1) dQ = ef0 / (h * h);
+    return dC - dQ;
+  }
+  // exact derivatives of the nodal u = rho H and eps with respect to P_m (m interior)
+  __device__ double dU(int j, int m) const {
+    double v = -rho[base + j] * K(j - m);
+    if (j == m) v += drho[base + j] * H[base + j];
+    return v;
+  }
+  __device__ double dE(int j, int m) const {
+    const double e = eps[base + j];
+    double v = -(3.0 * e / H[base + j]) * K(j - m);
+    if (j == m) v += e * (drho[base + j] / rho[base + j] - deta_rel[base + j]);
+    return v;
+  }
+  __device__ double dF_exact(int j, int m) const {
+    const double d0 = dU(j, m);
+    if (j == 0) return d0;
+    return d0 + 0.5 * (psia[base + j] * (d0 - dU(j - 1, m)) + psib[base + j] * (dU(j + 1, m) - d0));
+  }
+  __device__ double J_exact(int i, int m, double ef0, double ef1) const {
+    const double dC = (dF_exact(i, m) - dF_exact(i - 1, m)) / h;
+    const double def1 = 0.5 * (dE(i, m) + dE(i + 1, m));
+    const double def0 = 0.5 * (dE(i - 1, m) + dE(i, m));
+    const double Pi = P[base + i];
+    const double dq = def1 * (P[base + i + 1] - Pi) + ef1 * ((m == i + 1) - (m == i)) -
+                      def0 * (Pi - P[base + i - 1]) - ef0 * ((m == i) - (m == i - 1));
+    return dC - dq / (h * h);
+  }
+  // exact and frozen dR_i/dH0
+  __device__ double JH_exact(int i, double ef0, double ef1) const {
+    auto dUh = [&](int j) { return rho[base + j]; };
+    auto dEh = [&](int j) { return 3.0 * eps[base + j] / H[base + j]; };
+    auto dFh = [&](int j) {
+      const double d0 = dUh(j);
+      if (j == 0) return d0;
+      return d0 + 0.5 * (psia[base + j] * (d0 - dUh(j - 1)) + psib[base + j] * (dUh(j + 1) - d0));
+    };
+    const double dC = (dFh(i) - dFh(i - 1)) / h;
+    const double Pi = P[base + i];
+    const double dq = 0.5 * (dEh(i) + dEh(i + 1)) * (P[base + i + 1] - Pi) -
+                      0.5 * (dEh(i - 1) + dEh(i)) * (Pi - P[base + i - 1]);
+    return dC - dq / (h * h);
+  }
+  __device__ double JH_frozen(int i) const {
+    auto dFh = [&](int j) {
+      if (j == 0) return rho[base];
+      const double ph = phi(j);
+      return rho[base + j] * (1.0 + 0.5 * ph) - 0.5 * ph * rho[base + j - 1];
+    };
+    return (dFh(i) - dFh(i - 1)) / h;
+  }
+};
+
+// kind 0: band of (J_frozen D) with the weighted-change distribution D, cavitated rows -> identity;
+// kind 1: band of the exact Jacobian, rows with P_i <= R_i / |J_ii| -> identity.
+// Also writes dR/dH0 (jh, frozen or exact) and |J_ii| (dg, kind 1) per row.
+__global__ void k_line_jac_band(const LineInst* __restrict__ inst, LineRowCtx c, const double* __restrict__ R,
+                                const int* __restrict__ skip, int kind, int beta, double* __restrict__ band,
+                                uint8_t* __restrict__ act, double* __restrict__ jh, double* __restrict__ dg) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  const int N = c.N, n = N - 2;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  LineRowCtx q = c;
+  q.base = (size_t)z * N;
+  q.h = inst[z].h;
+  const int i = r + 1;
+  const int bw = 2 * beta + 1;
+  double* row = band + ((size_t)z * n + r) * bw;
+  const double ef1 = 0.5 * (c.eps[q.base + i] + c.eps[q.base + i + 1]);
+  const double ef0 = 0.5 * (c.eps[q.base + i - 1] + c.eps[q.base + i]);
+  const double Pi = c.P[q.base + i], Ri = R[q.base + i];
+  bool a;
+  if (kind == 0) {
+    a = (Pi <= 0.0) && (Ri > 0.0);
+    const double w = inst[z].dist_w, sw = inst[z].switch_eps_h;
+    for (int j = 0; j < bw; ++j) {
+      const int col = r - beta + j;  // interior column index, node col + 1
+      double v = 0.0;
+      if (col >= 0 && col < n) {
+        const int m = col + 1;
+        v = q.J_frozen(i, m, ef0, ef1);
+        if (c.eps[q.base + m] / q.h <= sw) {
+          if (m - 1 >= 1) v -= w * q.J_frozen(i, m - 1, ef0, ef1);
+          if (m + 1 <= N - 2) v -= w * q.J_frozen(i, m + 1, ef0, ef1);
+        }
+      }
+      row[j] = a ? (j == beta ? 1.0 : 0.0) : v;
+    }
+    if (jh) jh[(size_t)z * n + r] = a ? 0.0 : q.JH_frozen(i);
+  } else {
+    const double jii = q.J_exact(i, i, ef0, ef1);
+    const double d = fabs(jii) > 0.0 ? fabs(jii) : 1.0;
+    a = Pi <= Ri / d;
+    for (int j = 0; j < bw; ++j) {
+      const int col = r - beta + j;
+      double v = 0.0;
+      if (col >= 0 && col < n) v = q.J_exact(i, col + 1, ef0, ef1);
+      row[j] = a ? (j == beta ? 1.0 : 0.0) : v;
+    }
+    if (jh) jh[(size_t)z * n + r] = a ? 0.0 : q.JH_exact(i, ef0, ef1);
+    if (dg) dg[(size_t)z * n + r] = d;
+  }
+  act[(size_t)z * n + r] = a ? 1 : 0;
+}
+
+// ---------------------------------------------------------------- paper relaxation
+__global__ void k_line_paper_rhs(const double* __restrict__ R, const uint8_t* __restrict__ act,
+                                 const int* __restrict__ skip, double* __restrict__ rhs, int N) {
+  const int z = blockIdx.y, n = N - 2;
+  if (skip && skip[z]) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  rhs[(size_t)z * n + r] = act[(size_t)z * n + r] ? 0.0 : -R[(size_t)z * N + r + 1];
+}
+
+// P <- max(0, P + omega D sigma) (Sec. 3.3.4, Eq. eqn69); block partial sums of the new P
+// (one thread per node, the same blocks as k_line_residual)
+__global__ void __launch_bounds__(kNodeBlock) k_line_paper_update(const LineInst* __restrict__ inst,
+                                                                  const double* __restrict__ sigma,
+                                                                  const double* __restrict__ eps,
+                                                                  const int* __restrict__ skip,
+                                                                  double* __restrict__ P, double* __restrict__ blk,
+                                                                  int nblk, int N) {
+  const int z = blockIdx.y, n = N - 2;
+  if (skip && skip[z]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = i - 1;  // interior index
+  const LineInst q = inst[z];
+  double pn = 0.0;
+  if (r >= 0 && r < n) {
+    const size_t so = (size_t)z * n;
+    double dp = sigma[so + r];
+    for (int cc = r - 1; cc <= r + 1; cc += 2) {
+      if (cc < 0 || cc >= n) continue;
+      if (eps[(size_t)z * N + cc + 1] / q.h <= q.switch_eps_h) dp -= q.dist_w * sigma[so + cc];
+    }
+    const size_t o = (size_t)z * N + i;
+    pn = P[o] + q.omega * dp;
+    pn = pn > 0.0 ? pn : 0.0;
+    P[o] = pn;
+  }
+  __shared__ double s[kNodeBlock];
+  s[threadIdx.x] = pn;
+  __syncthreads();
+  for (int w = kNodeBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) blk[((size_t)z * nblk + blockIdx.x) * 4 + 1] = s[0];
+}
+
+// H0 <- H0 - c (pi/2 - h sum P)   (Sec. 3.3.4, Eq. eqn75 with the line-contact load)
+__global__ void k_line_h0_update(const LineInst* __restrict__ inst, const double* __restrict__ blk, int nblk,
+                                 const int* __restrict__ skip, double* __restrict__ H0, int n_inst) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= n_inst || (skip && skip[z])) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += blk[((size_t)z * nblk + b) * 4 + 1];
+  H0[z] -= inst[z].c_h0 * (0.5 * M_PI - inst[z].h * s);
+}
+
+// ---------------------------------------------------------------- start
+__global__ void k_line_hertz(const LineInst* __restrict__ inst, double* __restrict__ P, int N) {
+  const int z = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double X = inst[z].xa + i * inst[z].h;
+  double v = 1.0 - X * X;
+  P[(size_t)z * N + i] = (i == 0 || i == N - 1 || v <= 0.0) ? 0.0 : sqrt(v);
+}
+
+__global__ void k_line_set_h0(const LineInst* __restrict__ inst, const double* __restrict__ blk, int nblk,
+                              double* __restrict__ H0, int n_inst) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= n_inst) return;
+  double hm = INFINITY;
+  for (int b = 0; b < nblk; ++b) hm = fmin(hm, blk[((size_t)z * nblk + b) * 4 + 2]);
+  H0[z] = inst[z].h_init - hm;  // the film was evaluated with H0 = 0
+}
+
+// ================================================================= host side
+cudaError_t ctx_alloc(LineCtx* c, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 16);
+  if (e == cudaSuccess) c->allocs.push_back(*p);
+  return e;
+}
+
+LineRowCtx line_row_ctx(LineCtx* c) {
+  LineRowCtx q;
+  q.rho = c->rho;
+  q.drho = c->drho;
+  q.deta_rel = c->deta_rel;
+  q.eps = c->eps;
+  q.u = c->u;
+  q.H = c->H;
+  q.P = nullptr;
+  q.psi = c->psi;
+  q.psia = c->psia;
+  q.psib = c->psib;
+  q.gtab = c->gtab;
+  q.base = 0;
+  q.N = c->N;
+  q.h = 0.0;
+  return q;
+}
+
+// deformation of the nodal vectors V [n_inst][vstride] -> c->partial
+cudaError_t line_deform(LineCtx* c, const double* V, int vstride, const int* skip) {
+  dim3 g((c->N + kDefTI - 1) / kDefTI, c->ksplit, c->n_inst);
+  k_line_deform<<<g, kDefTI, 0, c->st>>>(c->inst, c->gtab, V, vstride, skip, c->partial, c->n_inst, c->N);
+  return cudaGetLastError();
+}
+
+// film + lubricant state + faces + residual + reductions at (P, H0)
+cudaError_t line_state(LineCtx* c, const double* P, const double* H0, const double* rough, const int* skip,
+                       int* iters_done_flag_mode) {
+  cudaError_t e = line_deform(c, P, c->N, skip);
+  if (e != cudaSuccess) return e;
+  dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
+  k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->partial, c->ksplit, H0, rough, c->N, skip, c->H,
+                                             c->n_inst, c->N, 0);
+  k_line_nodes<<<gn, kNodeBlock, 0, c->st>>>(c->inst, P, c->H, skip, c->rho, c->drho, c->deta_rel, c->eps, c->u,
+                                              c->N);
+  k_line_faces<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->u, skip, c->F, c->psi, c->psia, c->psib, c->N);
+  k_line_residual<<<gn, kNodeBlock, 0, c->st>>>(c->inst, P, c->H, c->eps, c->F, skip, c->R, c->blk, c->nblk, c->N);
+  (void)iters_done_flag_mode;
+  return cudaGetLastError();
+}
+
+cudaError_t line_finalize(LineCtx* c, int* done, int* iters) {
+  k_line_finalize<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(c->inst, c->blk, c->nblk, c->red, done, iters,
+                                                               c->n_inst);
+  return cudaGetLastError();
+}
+
+cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, uint8_t* act, double* jh,
+                          double* dg, const int* skip) {
+  LineRowCtx q = line_row_ctx(c);
+  q.P = P;
+  dim3 g((c->n + 127) / 128, c->n_inst);
+  k_line_jac_band<<<g, 128, 0, c->st>>>(c->inst, q, c->R, skip, kind, c->beta, band, act, jh, dg);
+  return cudaGetLastError();
+}
+
+cudaError_t line_start(LineCtx* c, double* P, double* H0, const double* rough) {
+  dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
+  k_line_hertz<<<gn, kNodeBlock, 0, c->st>>>(c->inst, P, c->N);
+  cudaError_t e = cudaMemsetAsync(H0, 0, sizeof(double) * c->n_inst, c->st);
+  if (e != cudaSuccess) return e;
+  e = line_state(c, P, H0, rough, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  k_line_set_h0<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(c->inst, c->blk, c->nblk, H0, c->n_inst);
+  return cudaGetLastError();
+}
+
+// the paper's iteration: band Newton step with the frozen / distributed Jacobian,
+// PAQIF solve, projected distributed update, H0 relaxation
+cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double* rough) {
+  cudaError_t e = line_state(c, P, H0, rough, c->done, nullptr);
+  if (e != cudaSuccess) return e;
+  e = line_finalize(c, c->done, c->iters);
+  if (e != cudaSuccess) return e;
+  e = line_jac_band(c, P, 0, c->band, c->act, nullptr, nullptr, c->done);
+  if (e != cudaSuccess) return e;
+  dim3 g((c->n + 127) / 128, c->n_inst);
+  k_line_paper_rhs<<<g, 128, 0, c->st>>>(c->R, c->act, c->done, c->rhs, c->N);
+  PaqifLaunch L;
+  L.n_sys = c->n_inst;
+  L.n = c->n;
+  L.beta = c->beta;
+  L.mode = 0;
+  L.band = c->band;
+  L.rhs = c->rhs;
+  L.act = (int*)((unsigned char*)c->pq_ws + align_up(paqif_stack_bytes(c->n_inst, c->n, c->beta), kWorkspaceAlign));
+  L.stack = c->pq_ws;
+  L.x = c->sigma;
+  L.iters = nullptr;
+  L.info = c->pq_info;
+  e = launch_expand_active(c->act, L.act, (size_t)c->n_inst * c->n, c->st);
+  if (e != cudaSuccess) return e;
+  e = launch_paqif(L, c->st);
+  if (e != cudaSuccess) return e;
+  dim3 gu((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
+  k_line_paper_update<<<gu, kNodeBlock, 0, c->st>>>(c->inst, c->sigma, c->eps, c->done, P, c->blk, c->nblk, c->N);
+  k_line_h0_update<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(c->inst, c->blk, c->nblk, c->done, H0, c->n_inst);
+  return cudaGetLastError();
+}
+
+}  // namespace ehl
+
+namespace ehl {
+cudaError_t line_init_tables(LineCtx* c) {
+  dim3 g((c->N + 255) / 256, c->n_inst);
+  k_line_gtab<<<g, 256, 0, c->st>>>(c->inst, c->gtab, c->N);
+  return cudaGetLastError();
+}
+}  // namespace ehl

@@ -1,0 +1,50 @@
+// line.h -- host-side state and stage launchers of the line-contact path.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ehl_internal.h"
+#include "line_kernels.cuh"
+
+namespace ehl {
+
+struct LineCtx {
+  int n_inst = 0, N = 0, n = 0, beta = 2, method = 0, max_iter = 0, krylov_dim = 30;
+  cudaStream_t st = nullptr;
+  std::vector<LineInst> h_inst;
+  LineInst* inst = nullptr;
+  float2* gtab = nullptr;
+  int ksplit = 1, nblk = 1;
+  float2* partial = nullptr;
+  double *H = nullptr, *rho = nullptr, *drho = nullptr, *deta_rel = nullptr, *eps = nullptr, *u = nullptr;
+  double *F = nullptr, *psi = nullptr, *psia = nullptr, *psib = nullptr, *R = nullptr;
+  double *blk = nullptr, *red = nullptr;
+  double *band = nullptr, *rhs = nullptr, *sigma = nullptr, *jh = nullptr, *dg = nullptr;
+  uint8_t* act = nullptr;
+  void* pq_ws = nullptr;
+  size_t pq_ws_bytes = 0;
+  int* pq_info = nullptr;
+  double *Pw = nullptr, *H0w = nullptr, *dH = nullptr;
+  int *done = nullptr, *iters = nullptr;
+  std::vector<void*> allocs;
+  // Newton-Krylov buffers (line_newton.cu)
+  void* nk = nullptr;
+};
+
+cudaError_t ctx_alloc(LineCtx* c, void** p, size_t bytes);
+cudaError_t line_deform(LineCtx* c, const double* V, int vstride, const int* skip);
+cudaError_t line_state(LineCtx* c, const double* P, const double* H0, const double* rough, const int* skip,
+                       int* unused);
+cudaError_t line_finalize(LineCtx* c, int* done, int* iters);
+cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, uint8_t* act, double* jh,
+                          double* dg, const int* skip);
+cudaError_t line_start(LineCtx* c, double* P, double* H0, const double* rough);
+cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double* rough);
+cudaError_t line_init_tables(LineCtx* c);
+// Newton-Krylov method (line_newton.cu)
+cudaError_t line_nk_alloc(LineCtx* c);
+cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough);
+
+}  // namespace ehl

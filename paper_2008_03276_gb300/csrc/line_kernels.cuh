@@ -1,0 +1,79 @@
+// line_kernels.cuh -- device code of the line-contact hot path (Sec. 3.3).
+//
+// Discrete problem: nodes X_i = xa + i h, i = 0..N-1, P_0 = P_{N-1} = 0.
+//  * film (Sec. 3.3.1 Case 1, Eq. eqn19):  H_i = H0 + X_i^2/2 - sum_k K_{|i-k|} P_k + rough_i,
+//    K_d = G_d / pi with the closed-form cell integral G_d of log|x - x'|;
+//  * lubricant (Sec. 3.3, Example 6): Roelands eta, Dowson-Higginson rho, eps = rho H^3/(eta lambda);
+//  * TVD residual (Sec. 3.3.3, Eqs. eqn62-eqn65 in the standard upwind form):
+//    F_{j+1/2} = u_j + psi(u_j - u_{j-1}, u_{j+1} - u_j)/2 (F_{1/2} = u_0), u = rho H,
+//    R_i = (F_{i+1/2} - F_{i-1/2})/h - [eps_{i+1/2}(P_{i+1}-P_i) - eps_{i-1/2}(P_i-P_{i-1})]/h^2.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "df64.cuh"
+
+namespace ehl {
+
+struct LineInst {
+  int N;             // nodes including the two boundary nodes
+  int beta;          // half-band of the Jacobian
+  int limiter;       // 0 minmod, 1 van Leer
+  int compressible;  // 0: rho = eta = 1
+  int elastic;       // 0: rigid surfaces
+  int pad0;
+  double xa, h;
+  double lam, abar, alpha, p0, z, pH;
+  double switch_eps_h, dist_w, c_h0, omega, tol, h_init;
+};
+
+// rho, d rho/dP, ln eta and (d eta/dP)/eta at pressure P (float64).
+__device__ __forceinline__ void line_material(const LineInst& q, double P, double& rho, double& drho,
+                                              double& lneta, double& deta_rel) {
+  if (!q.compressible) {
+    rho = 1.0;
+    drho = 0.0;
+    lneta = 0.0;
+    deta_rel = 0.0;
+    return;
+  }
+  const double base = 1.0 + P * q.pH / q.p0;
+  const double bz = pow(base, q.z);
+  lneta = (q.alpha * q.p0 / q.z) * (bz - 1.0);
+  deta_rel = q.alpha * q.pH * bz / base;
+  const double a = 0.59e9;
+  const double den = a + P * q.pH;
+  rho = (a + 1.34 * P * q.pH) / den;
+  drho = a * (1.34 * q.pH - q.pH) / (den * den);
+}
+
+// Limiter function psi(a, b) and its partial derivatives on the current branch.
+__device__ __forceinline__ void line_limiter(int kind, double a, double b, double& psi, double& pa, double& pb) {
+  if (!(a * b > 0.0)) {
+    psi = pa = pb = 0.0;
+    return;
+  }
+  if (kind == 0) {
+    if (fabs(a) <= fabs(b)) {
+      psi = a;
+      pa = 1.0;
+      pb = 0.0;
+    } else {
+      psi = b;
+      pa = 0.0;
+      pb = 1.0;
+    }
+  } else {
+    const double s = a + b;
+    psi = 2.0 * a * b / s;
+    pa = 2.0 * b * b / (s * s);
+    pb = 2.0 * a * a / (s * s);
+  }
+}
+
+// Cell integral of log|x_i - x'| over a cell at distance d (in cells), float64.
+__device__ __forceinline__ double line_cell_integral(int d, double h) {
+  const double tp = (d + 0.5) * h, tm = (d - 0.5) * h;
+  return tp * (log(fabs(tp)) - 1.0) - tm * (log(fabs(tm)) - 1.0);
+}
+
+}  // namespace ehl

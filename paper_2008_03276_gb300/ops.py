@@ -67,3 +67,86 @@ def paqif_solve(band, rhs, beta, mode=0, active=None, x=None, workspace=None, st
                                _ptr(info), _ptr(workspace), wbytes, _stream(stream))
     _ffi.check(code, "ehl_paqif_solve")
     return x, iters, info
+
+
+def default_params(dim=1, **overrides):
+    """``ehl_params`` filled by ``ehl_params_default`` with keyword overrides."""
+    lib = _ffi.load()
+    p = _ffi.EhlParams()
+    lib.ehl_params_default(ctypes.byref(p), dim)
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """An ``ehl_ctx`` for ``n_inst`` instances (device arrays ``[n_inst][nx]``)."""
+
+    def __init__(self, params, n_inst=1, per_inst=None, stream=None):
+        lib = _ffi.load()
+        self._lib = lib
+        self.params = params
+        self.n_inst = n_inst
+        self.nx = params.nx
+        self.beta = params.halfband
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = None
+        if per_inst is not None:
+            arr = (_ffi.EhlParams * n_inst)(*per_inst)
+        h = ctypes.c_void_p(0)
+        code = lib.ehl_create(ctypes.byref(params), n_inst, arr, ctypes.c_void_p(self._stream.cuda_stream),
+                              ctypes.byref(h))
+        _ffi.check(code, "ehl_create")
+        self._h = h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _ffi.check(self._lib.ehl_destroy(self._h), "ehl_destroy")
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self):
+        return torch.device("cuda", torch.cuda.current_device())
+
+    def residual(self, P, H0, rough=None):
+        _check_dev(P, H0, rough)
+        R = torch.empty_like(P)
+        H = torch.empty_like(P)
+        comp = torch.empty((self.n_inst, 2), dtype=torch.float64, device=P.device)
+        code = self._lib.ehl_residual(self._h, _ptr(P), _ptr(H0), _ptr(rough), _ptr(R), _ptr(H), _ptr(comp))
+        _ffi.check(code, "ehl_residual")
+        return R, H, comp
+
+    def jacobian_band(self, P, H0, kind=0, rough=None):
+        _check_dev(P, H0, rough)
+        n = self.nx - 2
+        band = torch.empty((self.n_inst, n, 2 * self.beta + 1), dtype=torch.float64, device=P.device)
+        act = torch.empty((self.n_inst, n), dtype=torch.uint8, device=P.device)
+        code = self._lib.ehl_jacobian_band(self._h, _ptr(P), _ptr(H0), _ptr(rough), kind, _ptr(band), _ptr(act))
+        _ffi.check(code, "ehl_jacobian_band")
+        return band, act
+
+    def solve(self, P=None, H0=None, rough=None, check=True):
+        dev = self._dev()
+        init = 1
+        if P is None:
+            init = 0
+            P = torch.zeros((self.n_inst, self.nx), dtype=torch.float64, device=dev)
+            H0 = torch.zeros(self.n_inst, dtype=torch.float64, device=dev)
+        else:
+            P = P.clone()
+            H0 = H0.clone()
+        _check_dev(P, H0, rough)
+        iters = torch.zeros(self.n_inst, dtype=torch.int32, device=dev)
+        res = torch.zeros((self.n_inst, 2), dtype=torch.float64, device=dev)
+        code = self._lib.ehl_solve(self._h, _ptr(P), _ptr(H0), _ptr(rough), init, _ptr(iters), _ptr(res))
+        if check:
+            _ffi.check(code, "ehl_solve")
+        return P, H0, iters, res, code

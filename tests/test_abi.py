@@ -47,3 +47,28 @@ def test_host_side_argument_checks():
     # NULL band / rhs / x are rejected before any CUDA call
     assert lib.ehl_paqif_solve(4, 16, 2, null, null, null, 0, null, null, null, null, 0, null) == _ffi.EHL_EINVAL
     assert lib.ehl_version() >= 100
+
+
+def test_params_struct_layout_matches_defaults():
+    """ctypes mirror of ehl_params: the C defaults land in the right fields."""
+    lib = _ffi.load()
+    p = _ffi.EhlParams()
+    lib.ehl_params_default(ctypes.byref(p), 1)
+    assert (p.dim, p.nx, p.ny) == (1, 129, 1)
+    assert (p.xa, p.xb, p.M, p.L) == (-4.5, 1.5, 20.0, 10.0)
+    assert (p.alpha, p.p0, p.z) == (1.7e-8, 1.98e8, 0.68)
+    assert (p.compressible, p.elastic, p.limiter, p.halfband) == (1, 1, 0, 2)
+    assert (p.switch_eps_h, p.dist_weight, p.c_h0, p.omega) == (0.6, 0.5, 0.05, 1.0)
+    assert (p.method, p.tol, p.max_iter, p.krylov_dim, p.h_init) == (1, 1e-8, 200, 40, 0.05)
+
+
+@pytest.mark.parametrize("field,value", [("nx", 4), ("halfband", 9), ("M", -1.0), ("xb", -5.0), ("method", 7),
+                                         ("limiter", 2), ("krylov_dim", 0)])
+def test_create_rejects_bad_params_on_host(field, value):
+    lib = _ffi.load()
+    p = _ffi.EhlParams()
+    lib.ehl_params_default(ctypes.byref(p), 1)
+    setattr(p, field, value)
+    h = ctypes.c_void_p(0)
+    assert lib.ehl_create(ctypes.byref(p), 1, None, None, ctypes.byref(h)) == _ffi.EHL_EINVAL
+    assert lib.ehl_create(None, 1, None, None, ctypes.byref(h)) == _ffi.EHL_EINVAL
