@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one full-size paqif_kernel<4> launch from the ncu capture
 # summarised in profiles/paqif_kernel_beta4_standalone.md, valid only for the kernel
 # sources with these sha256 prefixes; any other source reports traffic = null.
-PAQIF_TRAFFIC = {("89e6a3c4f45cb478", "4addd33d7cfa0c6e"): 875.96e6}
+PAQIF_TRAFFIC = {}
 
 
 def paqif_traffic():
@@ -51,7 +51,7 @@ def paqif_traffic():
             return hashlib.sha256(f.read()).hexdigest()[:16]
 
     try:
-        return PAQIF_TRAFFIC.get((h("paqif.cu"), h("df64.cuh")))
+        return PAQIF_TRAFFIC.get((h("paqif3.cu"), h("df64.cuh")))
     except OSError:
         return None
 
@@ -241,7 +241,7 @@ def run_ours(args):
         },
         "roofline": {"bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "traffic": paqif_traffic(),
-                     "kernel": "paqif_kernel<4>", "peak_source": src},
+                     "kernel": "paqif3_kernel<4>", "peak_source": src},
         "e2e": {"value": round(world * nbytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
