@@ -179,6 +179,16 @@ ehl_status ehl_residual(ehl_ctx* ctx, const double* P, const double* H0, const d
 ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, int kind,
                              double* band, uint8_t* active);
 
+/* Exact directional derivative of the residual at (P, H0):
+ *   out = (dR/dP) v + (dR/dH0) v_h0,
+ * every dependence on P included (the film through the kernel, rho, eta and
+ * eps, the limiter on its current branch).  v [n_inst][nx] nodal with zeros
+ * at the boundary nodes, v_h0 [n_inst], out [n_inst][nx] (0 at the boundary).
+ * This is the operator the Newton-Krylov method (method 1) iterates on.
+ * Asynchronous. */
+ehl_status ehl_jacobian_apply(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, const double* v,
+                              const double* v_h0, double* out);
+
 /* Solve every instance.  init = 0: start from the Hertzian pressure with
  * H0 chosen so that min H = h_init; init = 1: start from the given P, H0.
  * On return P, H0 hold the last iterate, iters (nullable, [n_inst] int32)

@@ -42,6 +42,7 @@ SYMBOLS = {
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "ehl_jacobian_band": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "ehl_jacobian_apply": (ctypes.c_int, [ctypes.c_void_p] * 7),
     "ehl_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                  ctypes.c_void_p, ctypes.c_void_p]),
     "ehl_paqif_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,

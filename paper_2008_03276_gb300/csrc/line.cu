@@ -548,6 +548,13 @@ cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double
 }  // namespace ehl
 
 namespace ehl {
+cudaError_t line_film_dir(LineCtx* c, const double* zh0, const int* skip) {
+  dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
+  k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->partial, c->ksplit, zh0, nullptr, c->N, skip, c->dH,
+                                             c->n_inst, c->N, 1);
+  return cudaGetLastError();
+}
+
 cudaError_t line_init_tables(LineCtx* c) {
   dim3 g((c->N + 255) / 256, c->n_inst);
   k_line_gtab<<<g, 256, 0, c->st>>>(c->inst, c->gtab, c->N);

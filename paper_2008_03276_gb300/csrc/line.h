@@ -43,8 +43,14 @@ cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, u
 cudaError_t line_start(LineCtx* c, double* P, double* H0, const double* rough);
 cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double* rough);
 cudaError_t line_init_tables(LineCtx* c);
+// dH = -K v + zh0: the film's directional derivative (v in c->partial from line_deform)
+cudaError_t line_film_dir(LineCtx* c, const double* zh0, const int* skip);
+// (dR/dP) v + (dR/dH0) v_h0 at (P, H0); v nodal (zero at the boundary nodes)
+cudaError_t line_jacobian_apply(LineCtx* c, const double* P, const double* H0, const double* rough, const double* v,
+                                const double* v_h0, double* out);
 // Newton-Krylov method (line_newton.cu)
 cudaError_t line_nk_alloc(LineCtx* c);
+void line_nk_free(LineCtx* c);
 cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough);
 
 }  // namespace ehl

@@ -81,6 +81,7 @@ static LineInst make_inst(const ehl_params& p) {
 static void free_all(LineCtx* c) {
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
+  if (c->nk) line_nk_free(c);
 }
 
 extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_params* per_inst, void* stream,
@@ -199,6 +200,12 @@ extern "C" ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const dou
   cudaError_t e = line_state(c, P, H0, rough, nullptr, nullptr);
   if (e == cudaSuccess) e = line_jac_band(c, P, kind, band, active, nullptr, nullptr, nullptr);
   return cuda_status(e);
+}
+
+extern "C" ehl_status ehl_jacobian_apply(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
+                                         const double* v, const double* v_h0, double* out) {
+  if (!ctx || !P || !H0 || !v || !v_h0 || !out) return EHL_EINVAL;
+  return cuda_status(line_jacobian_apply(&ctx->line, P, H0, rough, v, v_h0, out));
 }
 
 extern "C" ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const double* rough, int init, int* iters,

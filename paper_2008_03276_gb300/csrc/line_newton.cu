@@ -1,18 +1,482 @@
-// line_newton.cu -- Newton-Krylov method for line contact (method 1).
+// line_newton.cu -- Newton-Krylov method for line contact (ehl_params.method = 1).
+//
+// The fixed point is the paper's discrete problem (Sec. 3.3, Example 6): the
+// TVD residual R with P >= 0, R >= 0, P R = 0 and the force balance.  The
+// paper's banded Newton relaxation (method 0) diverges at high loads; this
+// method keeps its three hot-path parts -- the TVD residual, the deformation
+// integral and PAQIF on a band Jacobian -- and uses them in an inexact
+// semismooth Newton iteration:
+//   Phi_i = min(P_i, R_i / d_i)   (d_i = |dR_i/dP_i|, a row scaling),
+//   Phi_n = h sum P - pi/2,
+// each step solving J_Phi dz = -Phi by GMRES on the exact Jacobian (J v from
+// one deformation of v and a local directional derivative), right-
+// preconditioned by PAQIF on the band of the scaled exact Jacobian bordered
+// with the dR/dH0 column and the force row (one extra PAQIF solve per step
+// for the border), followed by a backtracking line search on ||Phi||_2.
 #include <cuda_runtime.h>
+#include <math.h>
 
+#include <vector>
+
+#include "ehl_internal.h"
 #include "line.h"
 
 namespace ehl {
+
+constexpr int kNkBlock = 256;
+
+struct NkBuf {
+  int m = 0, n1 = 0;
+  double *V = nullptr, *Z = nullptr, *Hh = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr;
+  double *phi = nullptr, *phinorm = nullptr, *zH = nullptr, *den = nullptr, *delta = nullptr;
+  double *Pt = nullptr, *H0t = nullptr, *tstep = nullptr, *rtol = nullptr, *beta0 = nullptr;
+  double *znode = nullptr, *zh0 = nullptr, *w = nullptr;
+  int *gm_k = nullptr, *gm_conv = nullptr, *lsdone = nullptr, *skip = nullptr;
+};
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kNkBlock / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// skip[z] = done[z] | other[z]
+__global__ void k_nk_skip(const int* __restrict__ done, const int* __restrict__ other, int* __restrict__ skip,
+                          int n_inst) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z < n_inst) skip[z] = (done[z] != 0) || (other && other[z] != 0);
+}
+
+// Scale the exact band rows by 1/d, form Phi, v_0 = -Phi/||Phi||, the border rhs.
+__global__ void __launch_bounds__(kNkBlock) k_nk_setup(const LineInst* __restrict__ inst, NkBuf b,
+                                                       const double* __restrict__ P, const double* __restrict__ R,
+                                                       const double* __restrict__ red, const uint8_t* __restrict__ act,
+                                                       const double* __restrict__ dg, const double* __restrict__ jh,
+                                                       const int* __restrict__ done, double* __restrict__ band,
+                                                       double* __restrict__ rhs, int N, int beta) {
+  const int z = blockIdx.x;
+  if (done[z]) return;
+  __shared__ double sh[kNkBlock];
+  const int n = N - 2, n1 = n + 1, bw = 2 * beta + 1;
+  double* phi = b.phi + (size_t)z * n1;
+  double ss = 0.0;
+  for (int r = threadIdx.x; r < n; r += kNkBlock) {
+    const size_t o = (size_t)z * n + r;
+    const double d = dg[o];
+    const double Pi = P[(size_t)z * N + r + 1], Ri = R[(size_t)z * N + r + 1];
+    double ph;
+    if (act[o]) {
+      ph = Pi;
+      rhs[o] = 0.0;
+    } else {
+      ph = Ri / d;
+      double* row = band + o * bw;
+      for (int j = 0; j < bw; ++j) row[j] /= d;
+      rhs[o] = jh[o] / d;
+    }
+    phi[r] = ph;
+    ss += ph * ph;
+  }
+  const double f = red[z * 4 + 1];
+  if (threadIdx.x == 0) phi[n] = f;
+  ss = block_sum(ss, sh) + f * f;
+  const double nrm = sqrt(ss);
+  double* v0 = b.V + (size_t)z * (b.m + 1) * n1;
+  for (int r = threadIdx.x; r < n1; r += kNkBlock) v0[r] = nrm > 0.0 ? -phi[r] / nrm : 0.0;
+  if (threadIdx.x == 0) {
+    b.phinorm[z] = nrm;
+    b.beta0[z] = nrm;
+    b.g[(size_t)z * (b.m + 1)] = nrm;
+    b.gm_k[z] = 0;
+    b.gm_conv[z] = nrm > 0.0 ? 0 : 1;
+    const double rc = red[z * 4 + 0];
+    b.rtol[z] = fmin(1e-3, fmax(1e-6, 1e-2 * rc));
+  }
+}
+
+// zH = sigma (the PAQIF solve of the border column), den = h sum zH
+__global__ void __launch_bounds__(kNkBlock) k_nk_border(const LineInst* __restrict__ inst, NkBuf b,
+                                                        const double* __restrict__ sigma,
+                                                        const int* __restrict__ done, double* __restrict__ rhs,
+                                                        int N) {
+  const int z = blockIdx.x;
+  if (done[z]) return;
+  __shared__ double sh[kNkBlock];
+  const int n = N - 2, n1 = n + 1;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n; r += kNkBlock) {
+    const double v = sigma[(size_t)z * n + r];
+    b.zH[(size_t)z * n + r] = v;
+    s += v;
+  }
+  s = block_sum(s, sh) * inst[z].h;
+  if (threadIdx.x == 0) b.den[z] = fabs(s) > 1e-300 ? s : 1e-300;
+  // the first preconditioner input: v_0[0:n]
+  const double* v0 = b.V + (size_t)z * (b.m + 1) * n1;
+  for (int r = threadIdx.x; r < n; r += kNkBlock) rhs[(size_t)z * n + r] = v0[r];
+}
+
+// z_j = M^-1 v_j from z1 = Jb^-1 v_j[0:n]: xi = (h sum z1 - v_j[n]) / den, z = z1 - xi zH
+__global__ void __launch_bounds__(kNkBlock) k_nk_prec(const LineInst* __restrict__ inst, NkBuf b, int j,
+                                                      const double* __restrict__ sigma, const int* __restrict__ skip,
+                                                      int N) {
+  const int z = blockIdx.x;
+  if (skip[z]) return;
+  __shared__ double sh[kNkBlock];
+  const int n = N - 2, n1 = n + 1;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n; r += kNkBlock) s += sigma[(size_t)z * n + r];
+  s = block_sum(s, sh) * inst[z].h;
+  const double* vj = b.V + ((size_t)z * (b.m + 1) + j) * n1;
+  const double xi = (s - vj[n]) / b.den[z];
+  double* Zj = b.Z + ((size_t)z * b.m + j) * n1;
+  double* zn = b.znode + (size_t)z * N;
+  for (int r = threadIdx.x; r < n; r += kNkBlock) {
+    const double v = sigma[(size_t)z * n + r] - xi * b.zH[(size_t)z * n + r];
+    Zj[r] = v;
+    zn[r + 1] = v;
+  }
+  if (threadIdx.x == 0) {
+    Zj[n] = xi;
+    zn[0] = 0.0;
+    zn[N - 1] = 0.0;
+    b.zh0[z] = xi;
+  }
+}
+
+// Exact directional derivative of R_i: (dR/dP) v + (dR/dH0) v_H0, given the
+// nodal direction zn (zero at the boundary nodes) and the film's directional
+// derivative dH = -K v + v_H0.
+struct JvArgs {
+  const double *P, *H, *rho, *drho, *deta_rel, *eps, *psia, *psib, *dH, *zn;
+};
+__device__ __forceinline__ double line_jv_row(const JvArgs& q, size_t base, int i, double h) {
+  auto dU = [&](int j) { return q.rho[base + j] * q.dH[base + j] + q.drho[base + j] * q.H[base + j] * q.zn[base + j]; };
+  auto dE = [&](int j) {
+    const double e = q.eps[base + j];
+    return (3.0 * e / q.H[base + j]) * q.dH[base + j] +
+           e * (q.drho[base + j] / q.rho[base + j] - q.deta_rel[base + j]) * q.zn[base + j];
+  };
+  auto dF = [&](int j) {
+    const double d0 = dU(j);
+    if (j == 0) return d0;
+    return d0 + 0.5 * (q.psia[base + j] * (d0 - dU(j - 1)) + q.psib[base + j] * (dU(j + 1) - d0));
+  };
+  const double dC = (dF(i) - dF(i - 1)) / h;
+  const double ef1 = 0.5 * (q.eps[base + i] + q.eps[base + i + 1]);
+  const double ef0 = 0.5 * (q.eps[base + i - 1] + q.eps[base + i]);
+  const double Pi = q.P[base + i];
+  const double* zn = q.zn + base;
+  const double dq = 0.5 * (dE(i) + dE(i + 1)) * (q.P[base + i + 1] - Pi) + ef1 * (zn[i + 1] - zn[i]) -
+                    0.5 * (dE(i - 1) + dE(i)) * (Pi - q.P[base + i - 1]) - ef0 * (zn[i] - zn[i - 1]);
+  return dC - dq / (h * h);
+}
+
+// w = J_Phi z for the interior rows (the force row is added in k_nk_arnoldi)
+__global__ void k_nk_jv(const LineInst* __restrict__ inst, NkBuf b, JvArgs q, const uint8_t* __restrict__ act,
+                        const double* __restrict__ dg, const int* __restrict__ skip, int N) {
+  const int z = blockIdx.y;
+  if (skip[z]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;  // interior node
+  if (i > N - 2) return;
+  const int n = N - 2, n1 = n + 1;
+  const size_t base = (size_t)z * N;
+  const double jv = line_jv_row(q, base, i, inst[z].h);
+  const size_t o = (size_t)z * n + (i - 1);
+  b.w[(size_t)z * n1 + (i - 1)] = act[o] ? q.zn[base + i] : jv / dg[o];
+}
+
+// out[z][i] = (dR_i/dP) v + (dR_i/dH0) v_H0 at interior nodes, 0 at the boundary
+__global__ void k_line_jv_raw(const LineInst* __restrict__ inst, JvArgs q, double* __restrict__ out, int N) {
+  const int z = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const size_t base = (size_t)z * N;
+  out[base + i] = (i >= 1 && i <= N - 2) ? line_jv_row(q, base, i, inst[z].h) : 0.0;
+}
+
+// Arnoldi step j with modified Gram-Schmidt, Givens update, convergence test
+__global__ void __launch_bounds__(kNkBlock) k_nk_arnoldi(const LineInst* __restrict__ inst, NkBuf b, int j,
+                                                         const int* __restrict__ skip, double* __restrict__ rhs,
+                                                         int N) {
+  const int z = blockIdx.x;
+  if (skip[z]) return;
+  __shared__ double sh[kNkBlock];
+  const int n = N - 2, n1 = n + 1, m = b.m;
+  double* w = b.w + (size_t)z * n1;
+  const double* Zj = b.Z + ((size_t)z * m + j) * n1;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n; r += kNkBlock) s += Zj[r];
+  s = block_sum(s, sh) * inst[z].h;
+  if (threadIdx.x == 0) w[n] = s;
+  __syncthreads();
+  double* H = b.Hh + (size_t)z * (m + 1) * m;  // H[i + j*(m+1)]
+  for (int i = 0; i <= j; ++i) {
+    const double* Vi = b.V + ((size_t)z * (m + 1) + i) * n1;
+    double d = 0.0;
+    for (int r = threadIdx.x; r < n1; r += kNkBlock) d += w[r] * Vi[r];
+    d = block_sum(d, sh);
+    for (int r = threadIdx.x; r < n1; r += kNkBlock) w[r] -= d * Vi[r];
+    if (threadIdx.x == 0) H[i + (size_t)j * (m + 1)] = d;
+    __syncthreads();
+  }
+  double nn = 0.0;
+  for (int r = threadIdx.x; r < n1; r += kNkBlock) nn += w[r] * w[r];
+  nn = sqrt(block_sum(nn, sh));
+  double* Vn = b.V + ((size_t)z * (m + 1) + j + 1) * n1;
+  const double inv = nn > 0.0 ? 1.0 / nn : 0.0;
+  for (int r = threadIdx.x; r < n1; r += kNkBlock) {
+    const double v = w[r] * inv;
+    Vn[r] = v;
+    if (r < n) rhs[(size_t)z * n + r] = v;
+  }
+  if (threadIdx.x == 0) {
+    double* col = H + (size_t)j * (m + 1);
+    col[j + 1] = nn;
+    double* cs = b.cs + (size_t)z * m;
+    double* sn = b.sn + (size_t)z * m;
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+      col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+      col[i] = t;
+    }
+    const double a = col[j], c = col[j + 1];
+    const double r = hypot(a, c);
+    const double cj = r > 0.0 ? a / r : 1.0, sj = r > 0.0 ? c / r : 0.0;
+    cs[j] = cj;
+    sn[j] = sj;
+    col[j] = r;
+    col[j + 1] = 0.0;
+    double* g = b.g + (size_t)z * (m + 1);
+    g[j + 1] = -sj * g[j];
+    g[j] = cj * g[j];
+    b.gm_k[z] = j + 1;
+    if (fabs(g[j + 1]) <= b.rtol[z] * b.beta0[z] || j + 1 == m || nn == 0.0) b.gm_conv[z] = 1;
+  }
+}
+
+// y = R^-1 g over the k Arnoldi steps, delta = sum y_j z_j
+__global__ void __launch_bounds__(kNkBlock) k_nk_update(const LineInst* __restrict__ inst, NkBuf b,
+                                                        const int* __restrict__ done, int N) {
+  const int z = blockIdx.x;
+  if (done[z]) return;
+  const int n = N - 2, n1 = n + 1, m = b.m;
+  const int k = b.gm_k[z];
+  __shared__ double y[256];
+  if (threadIdx.x == 0) {
+    const double* H = b.Hh + (size_t)z * (m + 1) * m;
+    const double* g = b.g + (size_t)z * (m + 1);
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int q = i + 1; q < k; ++q) s -= H[i + (size_t)q * (m + 1)] * y[q];
+      const double dgl = H[i + (size_t)i * (m + 1)];
+      y[i] = dgl != 0.0 ? s / dgl : 0.0;
+    }
+  }
+  __syncthreads();
+  double* dl = b.delta + (size_t)z * n1;
+  for (int r = threadIdx.x; r < n1; r += kNkBlock) {
+    double s = 0.0;
+    for (int q = 0; q < k; ++q) s += y[q] * b.Z[((size_t)z * m + q) * n1 + r];
+    dl[r] = s;
+  }
+  if (threadIdx.x == 0) {
+    b.tstep[z] = 1.0;
+    b.lsdone[z] = 0;
+  }
+}
+
+// trial point P_t = max(0, P + t dP), H0_t = H0 + t dH0
+__global__ void k_nk_trial(NkBuf b, const double* __restrict__ P, const double* __restrict__ H0,
+                           const int* __restrict__ skip, int N) {
+  const int z = blockIdx.y;
+  if (skip[z]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int n1 = N - 1;
+  const double t = b.tstep[z];
+  double v = 0.0;
+  if (i >= 1 && i <= N - 2) {
+    v = P[(size_t)z * N + i] + t * b.delta[(size_t)z * n1 + (i - 1)];
+    v = v > 0.0 ? v : 0.0;
+  }
+  b.Pt[(size_t)z * N + i] = v;
+  if (i == 0) b.H0t[z] = H0[z] + t * b.delta[(size_t)z * n1 + (N - 2)];
+}
+
+// merit of the trial point; accept (copy into P, H0) or halve the step
+__global__ void __launch_bounds__(kNkBlock) k_nk_merit(const LineInst* __restrict__ inst, NkBuf b,
+                                                       const double* __restrict__ R, const double* __restrict__ red,
+                                                       const double* __restrict__ dg, const int* __restrict__ skip,
+                                                       double* __restrict__ P, double* __restrict__ H0, int N) {
+  const int z = blockIdx.x;
+  if (skip[z]) return;
+  __shared__ double sh[kNkBlock];
+  __shared__ int accept;
+  const int n = N - 2;
+  double ss = 0.0;
+  bool finite = true;
+  for (int r = threadIdx.x; r < n; r += kNkBlock) {
+    const double pt = b.Pt[(size_t)z * N + r + 1];
+    const double rt = R[(size_t)z * N + r + 1] / dg[(size_t)z * n + r];
+    const double ph = pt < rt ? pt : rt;
+    if (!(ph == ph) || isinf(ph)) finite = false;
+    ss += ph * ph;
+  }
+  ss = block_sum(ss, sh);
+  const int nf = __syncthreads_or(finite ? 0 : 1);
+  const double f = red[z * 4 + 1];
+  const double nrm = sqrt(ss + f * f);
+  const double t = b.tstep[z];
+  if (threadIdx.x == 0) accept = (!nf && nrm == nrm && nrm <= (1.0 - 1e-4 * t) * b.phinorm[z]) || t < 1e-10;
+  __syncthreads();
+  if (accept) {
+    for (int i = threadIdx.x; i < N; i += kNkBlock) P[(size_t)z * N + i] = b.Pt[(size_t)z * N + i];
+    if (threadIdx.x == 0) {
+      H0[z] = b.H0t[z];
+      b.lsdone[z] = 1;
+    }
+  } else if (threadIdx.x == 0) {
+    b.tstep[z] = 0.5 * t;
+  }
+}
+
+// ----------------------------------------------------------------- host side
+cudaError_t line_jacobian_apply(LineCtx* c, const double* P, const double* H0, const double* rough, const double* v,
+                                const double* v_h0, double* out) {
+  cudaError_t e = line_state(c, P, H0, rough, nullptr, nullptr);
+  if (e == cudaSuccess) e = line_deform(c, v, c->N, nullptr);
+  if (e == cudaSuccess) e = line_film_dir(c, v_h0, nullptr);
+  if (e != cudaSuccess) return e;
+  JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, v};
+  const dim3 gn((c->N + 255) / 256, c->n_inst);
+  k_line_jv_raw<<<gn, 256, 0, c->st>>>(c->inst, q, out, c->N);
+  return cudaGetLastError();
+}
+
+void line_nk_free(LineCtx* c) {
+  delete (NkBuf*)c->nk;
+  c->nk = nullptr;
+}
+
 cudaError_t line_nk_alloc(LineCtx* c) {
-  (void)c;
+  NkBuf* b = new NkBuf();
+  c->nk = b;
+  const int m = c->krylov_dim, n1 = c->n + 1, ni = c->n_inst;
+  b->m = m;
+  b->n1 = n1;
+  const size_t NN = (size_t)ni * c->N;
+  struct A {
+    void** p;
+    size_t bytes;
+  } al[] = {{(void**)&b->V, sizeof(double) * ni * (m + 1) * (size_t)n1},
+            {(void**)&b->Z, sizeof(double) * ni * (size_t)m * n1},
+            {(void**)&b->Hh, sizeof(double) * ni * (m + 1) * (size_t)m},
+            {(void**)&b->cs, sizeof(double) * ni * (size_t)m},
+            {(void**)&b->sn, sizeof(double) * ni * (size_t)m},
+            {(void**)&b->g, sizeof(double) * ni * (size_t)(m + 1)},
+            {(void**)&b->phi, sizeof(double) * ni * (size_t)n1},
+            {(void**)&b->phinorm, sizeof(double) * ni},
+            {(void**)&b->zH, sizeof(double) * ni * (size_t)c->n},
+            {(void**)&b->den, sizeof(double) * ni},
+            {(void**)&b->delta, sizeof(double) * ni * (size_t)n1},
+            {(void**)&b->Pt, sizeof(double) * NN},
+            {(void**)&b->H0t, sizeof(double) * ni},
+            {(void**)&b->tstep, sizeof(double) * ni},
+            {(void**)&b->rtol, sizeof(double) * ni},
+            {(void**)&b->beta0, sizeof(double) * ni},
+            {(void**)&b->znode, sizeof(double) * NN},
+            {(void**)&b->zh0, sizeof(double) * ni},
+            {(void**)&b->w, sizeof(double) * ni * (size_t)n1},
+            {(void**)&b->gm_k, sizeof(int) * ni},
+            {(void**)&b->gm_conv, sizeof(int) * ni},
+            {(void**)&b->lsdone, sizeof(int) * ni},
+            {(void**)&b->skip, sizeof(int) * ni}};
+  for (auto& x : al) {
+    cudaError_t e = ctx_alloc(c, x.p, x.bytes);
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
-cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough) {
-  (void)c;
-  (void)P;
-  (void)H0;
-  (void)rough;
-  return cudaErrorNotSupported;
+
+// PAQIF on the scaled band.  Its cavitated rows are already identity rows, and
+// the preconditioner must return v_i on them, so no active mask is passed (a
+// mask would pin those unknowns to zero).
+static cudaError_t paqif_on(LineCtx* c, const double* rhs, double* x) {
+  PaqifLaunch L;
+  L.n_sys = c->n_inst;
+  L.n = c->n;
+  L.beta = c->beta;
+  L.mode = 0;
+  L.band = c->band;
+  L.rhs = rhs;
+  L.act = nullptr;
+  L.stack = c->pq_ws;
+  L.x = x;
+  L.iters = nullptr;
+  L.info = c->pq_info;
+  return launch_paqif(L, c->st);
 }
+
+static bool all_set(LineCtx* c, const int* a, const int* b2, cudaError_t& e) {
+  std::vector<int> ha(c->n_inst), hb(c->n_inst);
+  e = cudaMemcpyAsync(ha.data(), a, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), b2, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  for (int k = 0; k < c->n_inst; ++k)
+    if (!ha[k] && !hb[k]) return false;
+  return true;
+}
+
+// One Newton step for every instance that is not done.
+cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough) {
+  NkBuf& b = *(NkBuf*)c->nk;
+  const int ni = c->n_inst, N = c->N;
+  cudaError_t e = line_state(c, P, H0, rough, c->done, nullptr);
+  if (e == cudaSuccess) e = line_finalize(c, c->done, c->iters);
+  if (e == cudaSuccess) e = line_jac_band(c, P, 1, c->band, c->act, c->jh, c->dg, c->done);
+  if (e != cudaSuccess) return e;
+  k_nk_setup<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, P, c->R, c->red, c->act, c->dg, c->jh, c->done, c->band,
+                                         c->rhs, N, c->beta);
+  e = paqif_on(c, c->rhs, c->sigma);  // border column
+  if (e != cudaSuccess) return e;
+  k_nk_border<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->sigma, c->done, c->rhs, N);
+  const dim3 gn((N + 255) / 256, ni);
+  for (int j = 0; j < b.m; ++j) {
+    k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.gm_conv, b.skip, ni);
+    e = paqif_on(c, c->rhs, c->sigma);
+    if (e != cudaSuccess) return e;
+    k_nk_prec<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, b.skip, N);
+    e = line_deform(c, b.znode, N, b.skip);
+    if (e != cudaSuccess) return e;
+    e = line_film_dir(c, b.zh0, b.skip);
+    if (e != cudaSuccess) return e;
+    JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, b.znode};
+    k_nk_jv<<<gn, 256, 0, c->st>>>(c->inst, b, q, c->act, c->dg, b.skip, N);
+    k_nk_arnoldi<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, b.skip, c->rhs, N);
+    if ((j + 1) % 8 == 0 && j + 1 < b.m) {
+      if (all_set(c, c->done, b.gm_conv, e)) break;
+      if (e != cudaSuccess) return e;
+    }
+  }
+  k_nk_update<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->done, N);
+  for (int trial = 0; trial < 40; ++trial) {
+    k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.lsdone, b.skip, ni);
+    k_nk_trial<<<gn, 256, 0, c->st>>>(b, P, H0, b.skip, N);
+    e = line_state(c, b.Pt, b.H0t, rough, b.skip, nullptr);
+    if (e == cudaSuccess) e = line_finalize(c, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    k_nk_merit<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->R, c->red, c->dg, b.skip, P, H0, N);
+    if (all_set(c, c->done, b.lsdone, e)) break;
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace ehl

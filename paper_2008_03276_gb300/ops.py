@@ -133,6 +133,13 @@ class Context:
         _ffi.check(code, "ehl_jacobian_band")
         return band, act
 
+    def jacobian_apply(self, P, H0, v, v_h0, rough=None):
+        _check_dev(P, H0, v, v_h0, rough)
+        out = torch.empty_like(P)
+        code = self._lib.ehl_jacobian_apply(self._h, _ptr(P), _ptr(H0), _ptr(rough), _ptr(v), _ptr(v_h0), _ptr(out))
+        _ffi.check(code, "ehl_jacobian_apply")
+        return out
+
     def solve(self, P=None, H0=None, rough=None, check=True):
         dev = self._dev()
         init = 1

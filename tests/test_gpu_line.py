@@ -185,3 +185,25 @@ def test_paper_method_batch_of_instances():
         assert info["converged"]
         assert np.max(np.abs(P[k, 1:-1] - Pr)) <= 1e-8 * np.max(Pr)
         assert abs(H0[k] - H0r) <= 1e-8 * abs(H0r)
+
+
+@pytest.mark.parametrize("limiter", [0, 1])
+@pytest.mark.parametrize("N,M", [(129, 20.0), (513, 200.0)])
+def test_jacobian_apply_matches_oracle(limiter, N, M):
+    pb = oracle_problem(N, M=M, limiter=limiter)
+    ctx, _ = make(N, M=M, limiter=limiter)
+    rng = np.random.default_rng(N)
+    P = pb.hertz() * (1 + 0.05 * rng.standard_normal(pb.n)).clip(0)
+    H0 = pb.h0_for_min_film(P, 0.05)
+    J, JH = lr.jacobian_exact(pb, P, H0)
+    v = rng.standard_normal(pb.n)
+    vh = 0.3
+    ref = J @ v + JH * vh
+    Pd, H0d, vd, vhd = to_dev(pb.full(P)[None], np.array([H0]), pb.full(v)[None], np.array([vh]))
+    out = ctx.jacobian_apply(Pd, H0d, vd, vhd)
+    torch.cuda.synchronize()
+    out = out.cpu().numpy()[0]
+    scale = np.abs(J) @ np.abs(v) + np.abs(JH) * abs(vh)
+    cond = limiter_conditioning(pb, P, H0)
+    assert out[0] == 0 and out[-1] == 0
+    assert np.all(np.abs(out[1:-1] - ref) <= (1e-12 + 50 * cond) * scale + 1e-300)
