@@ -28,6 +28,11 @@ struct PaqifLaunch {
 // Bytes of the per-system Z-stack (padded to whole CTAs); 0 for a bad beta.
 size_t paqif_stack_bytes(int n_sys, int n, int beta);
 cudaError_t launch_paqif(const PaqifLaunch& L, cudaStream_t st);
+// Factor once (also solving for L.rhs), then resolve for new right-hand sides
+// with the same band: the stack (L.stack) and the factor store are kept.
+size_t paqif_factor_store_bytes(int n_sys, int n, int beta);
+cudaError_t launch_paqif_factor(const PaqifLaunch& L, void* fstore, cudaStream_t st);
+cudaError_t launch_paqif_resolve(const PaqifLaunch& L, void* fstore, cudaStream_t st);
 cudaError_t launch_expand_active(const uint8_t* in, int* out, size_t total, cudaStream_t st);
 
 }  // namespace ehl

@@ -32,6 +32,7 @@ struct NkBuf {
   double *Pt = nullptr, *H0t = nullptr, *tstep = nullptr, *rtol = nullptr, *beta0 = nullptr;
   double *znode = nullptr, *zh0 = nullptr, *w = nullptr;
   int *gm_k = nullptr, *gm_conv = nullptr, *lsdone = nullptr, *skip = nullptr;
+  void* fstore = nullptr;  // PAQIF factor store of the current preconditioner
 };
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -397,7 +398,8 @@ cudaError_t line_nk_alloc(LineCtx* c) {
             {(void**)&b->gm_k, sizeof(int) * ni},
             {(void**)&b->gm_conv, sizeof(int) * ni},
             {(void**)&b->lsdone, sizeof(int) * ni},
-            {(void**)&b->skip, sizeof(int) * ni}};
+            {(void**)&b->skip, sizeof(int) * ni},
+            {(void**)&b->fstore, paqif_factor_store_bytes(ni, c->n, c->beta)}};
   for (auto& x : al) {
     cudaError_t e = ctx_alloc(c, x.p, x.bytes);
     if (e != cudaSuccess) return e;
@@ -407,8 +409,11 @@ cudaError_t line_nk_alloc(LineCtx* c) {
 
 // PAQIF on the scaled band.  Its cavitated rows are already identity rows, and
 // the preconditioner must return v_i on them, so no active mask is passed (a
-// mask would pin those unknowns to zero).
-static cudaError_t paqif_on(LineCtx* c, const double* rhs, double* x) {
+// mask would pin those unknowns to zero).  factor = true factors the band once
+// per Newton step (solving for rhs as well); otherwise the stored factors are
+// reused for a new right-hand side.
+static cudaError_t paqif_on(LineCtx* c, const double* rhs, double* x, bool factor) {
+  NkBuf& b = *(NkBuf*)c->nk;
   PaqifLaunch L;
   L.n_sys = c->n_inst;
   L.n = c->n;
@@ -421,7 +426,7 @@ static cudaError_t paqif_on(LineCtx* c, const double* rhs, double* x) {
   L.x = x;
   L.iters = nullptr;
   L.info = c->pq_info;
-  return launch_paqif(L, c->st);
+  return factor ? launch_paqif_factor(L, b.fstore, c->st) : launch_paqif_resolve(L, b.fstore, c->st);
 }
 
 static bool all_set(LineCtx* c, const int* a, const int* b2, cudaError_t& e) {
@@ -444,13 +449,13 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
   if (e != cudaSuccess) return e;
   k_nk_setup<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, P, c->R, c->red, c->act, c->dg, c->jh, c->done, c->band,
                                          c->rhs, N, c->beta);
-  e = paqif_on(c, c->rhs, c->sigma);  // border column
+  e = paqif_on(c, c->rhs, c->sigma, true);  // factor, solving for the border column
   if (e != cudaSuccess) return e;
   k_nk_border<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->sigma, c->done, c->rhs, N);
   const dim3 gn((N + 255) / 256, ni);
   for (int j = 0; j < b.m; ++j) {
     k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.gm_conv, b.skip, ni);
-    e = paqif_on(c, c->rhs, c->sigma);
+    e = paqif_on(c, c->rhs, c->sigma, false);
     if (e != cudaSuccess) return e;
     k_nk_prec<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, b.skip, N);
     e = line_deform(c, b.znode, N, b.skip);

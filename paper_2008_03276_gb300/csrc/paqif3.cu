@@ -48,6 +48,7 @@ struct C3 {
   static constexpr int RB = 32;          // ring rows per side
   static constexpr int CH = 8;           // rows per chunk
   static constexpr int SL = NOC;         // float4 per stack level: (Mp, Mq) per outer column
+  static constexpr int FL = NO + 2;      // float4 per factor-store level: (w_p, w_q) per outer row, Pi^-1
   static constexpr int NT1 = NO + NOC;   // multiplier + folded-column tasks
   static constexpr int R1 = (NT1 + LS - 1) / LS;
   static constexpr int NUP = NO * NOC;   // update entries
@@ -68,6 +69,7 @@ struct __align__(16) Sm3 {
   union {
     double ring[2][C::RB][C::BW];  // band rows: float64 as copied, double-float after conversion
     float4 stk[C::RB][C::SL];      // phase 2: stack levels
+    float4 fr[C::RB][C::FL];       // solve-only W0 sweep: factor-store levels
   } u;
   double rrhs[2][C::RB];
   int ract[2][C::RB];
@@ -78,7 +80,8 @@ struct Paqif3Args {
   const double* band;
   const double* rhs;
   int* act;
-  float4* stack;  // [pad_sys][s][SL]
+  float4* stack;   // [pad_sys][s][SL]
+  float4* fstore;  // [pad_sys][s][FL]: outer-row multipliers and Pi^-1 (factor once, solve many), or null
   double* x;
   int* iters;
   int* info;
@@ -187,6 +190,7 @@ struct P3 {
   static __device__ void factor(Sm3<B>& sm, const Paqif3Args& a, int dsys, int ssys, int u, int& flag) {
     const int s = a.s, n = a.n;
     float4* stk = a.stack + (size_t)ssys * s * C::SL;
+    float4* fst = a.fstore ? a.fstore + (size_t)ssys * s * C::FL : nullptr;
     // prologue: chunks 0..3 issued, 0 and 1 converted; afterwards chunks
     // [0, conv) are double-float and chunks up to conv+1 are issued
     chunk<false>(sm, a, dsys, 0, u);
@@ -237,6 +241,12 @@ struct P3 {
         if (!(fabsf(det.hi) > 0.f)) det = make_df(1e-30f, 0.f);
       }
       const df inv = df_rcp(det);
+      if (fst && u == 0) {  // Pi^-1 = inv [[d, -b], [-c, a]]
+        const df i00 = df_mul(pd, inv), i01 = df_neg(df_mul(pb, inv));
+        const df i10 = df_neg(df_mul(pc, inv)), i11 = df_mul(pa, inv);
+        fst[(size_t)k * C::FL + C::NO] = make_float4(i00.hi, i00.lo, i01.hi, i01.lo);
+        fst[(size_t)k * C::FL + C::NO + 1] = make_float4(i10.hi, i10.lo, i11.hi, i11.lo);
+      }
       // tasks t < 2b: multipliers of outer row t, [w_ip, w_iq] = [l_ip, l_iq] Pi^-1;
       //       t >= 2b: folded outer column o = t - 2b, Pi^-1 [z_p,o; z_q,o].
       // All loads first, then the arithmetic, then the stores (no shared-memory
@@ -265,6 +275,7 @@ struct P3 {
         if (t < C::NO) {
           sm.w[t][0] = df2f(tr1[m]);
           sm.w[t][1] = df2f(tr2[m]);
+          if (fst) fst[(size_t)k * C::FL + t] = make_float4(tr1[m].hi, tr1[m].lo, tr2[m].hi, tr2[m].lo);
         } else if (t < C::NT1) {
           stk[(size_t)k * C::SL + (t - C::NO)] = make_float4(tr1[m].hi, tr1[m].lo, tr2[m].hi, tr2[m].lo);
         }
@@ -358,6 +369,112 @@ struct P3 {
           sm.kind[sq] = kind_r;
         }
       }
+      __syncwarp();
+      base = wrap(base + 1);
+    }
+    cpa_wait<0>();
+    __threadfence_block();
+    __syncwarp();
+  }
+
+
+  // ---------------------------------------------------------------- solve only
+  // W0 Y = F for a new right-hand side with the multipliers of a stored
+  // factorization: middle-out, y_p,q are read off the pivot slots, the outer
+  // rows take F_o -= w_o,p y_p + w_o,q y_q, and Pi^-1 (y_p, y_q) replaces the
+  // folded rhs column of the stack level for the Z0 sweep.
+  static __device__ void w_sweep(Sm3<B>& sm, const Paqif3Args& a, int dsys, int ssys, int u) {
+    const int s = a.s, n = a.n;
+    float4* stk = a.stack + (size_t)ssys * s * C::SL;
+    const float4* fst = a.fstore + (size_t)ssys * s * C::FL;
+    const double* rsys = a.rhs + (size_t)dsys * n;
+    // rhs and flags by chunk of 8 stream indices per side, staged in rrhs/ract;
+    // factor-store levels staged in the (unused) band ring as float4 [RB][FL]
+    float4 (*fring)[C::FL] = sm.u.fr;
+    auto issue = [&](int c) {
+      const int t0 = c * C::CH;
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        int r_lo = side ? s + t0 : s - 1 - (t0 + C::CH - 1);
+        int r_hi = side ? s + t0 + C::CH - 1 : s - 1 - t0;
+        r_lo = max(r_lo, 0);
+        r_hi = min(r_hi, n - 1);
+        for (int r = r_lo + u; r <= r_hi; r += C::LS)
+          cpa8(&sm.rrhs[side][(side ? r - s : s - 1 - r) & (C::RB - 1)], rsys + r);
+      }
+      const int k0 = t0, k1 = min(t0 + C::CH, s);
+      for (int e = u; e < (k1 - k0) * C::FL; e += C::LS) {
+        const int lvl = k0 + e / C::FL, off = e % C::FL;
+        if (lvl < s) cpa16cg(&fring[lvl & (C::RB - 1)][off], fst + (size_t)lvl * C::FL + off);
+      }
+    };
+    auto convert = [&](int c) {
+      const int t0 = c * C::CH;
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        int r_lo = side ? s + t0 : s - 1 - (t0 + C::CH - 1);
+        int r_hi = side ? s + t0 + C::CH - 1 : s - 1 - t0;
+        r_lo = max(r_lo, 0);
+        r_hi = min(r_hi, n - 1);
+        for (int r = r_lo + u; r <= r_hi; r += C::LS) {
+          const int t = (side ? r - s : s - 1 - r) & (C::RB - 1);
+          double* dst = &sm.rrhs[side][t];
+          const df v = df_from_double(*dst);
+          *reinterpret_cast<float2*>(dst) = make_float2(v.hi, v.lo);
+          sm.ract[side][t] = a.act ? __ldcg(a.act + (size_t)dsys * n + r) : 0;
+        }
+      }
+    };
+    // chunk c = rhs of stream indices [8c, 8c+8) and factor-store levels [8c, 8c+8).
+    // Level k reads levels of chunk k/8 and rhs up to stream k + b + 1 <= k + 9,
+    // so at k = 8c chunks c..c+2 must be complete and chunk c-1 is free.
+    issue(0);
+    cpa_commit();
+    issue(1);
+    cpa_commit();
+    issue(2);
+    cpa_commit();
+    issue(3);
+    cpa_commit();
+    cpa_wait<1>();
+    convert(0);
+    convert(1);
+    convert(2);
+    __syncwarp();
+    float2* F = &sm.S[0][C::NS];  // reuse the window's rhs column, stride NC
+    for (int e = u; e < C::NS; e += C::LS) {
+      const int side = e / C::W, t = e % C::W;
+      F[e * C::NC] = rhs_of(sm, side, t, row_kind(sm, side, t, s, n));
+    }
+    __syncwarp();
+    int base = 1;
+    for (int k = 0; k < s; ++k) {
+      const int pslot = base == 0 ? C::W - 1 : base - 1;
+      const int sp = pslot, sq = C::W + pslot;
+      const int tn = k + B + 1;
+      if ((k & 7) == 0 && k > 0) {
+        // issue chunk c+3 into the slots of chunk c-1, then all but the newest
+        // group are complete: chunk c+2 can be converted
+        issue((k >> 3) + 3);
+        cpa_commit();
+        cpa_wait<1>();
+        convert((k >> 3) + 2);
+        __syncwarp();
+      }
+      const df yp = f2df(F[sp * C::NC]), yq = f2df(F[sq * C::NC]);
+      const float4* lv = fring[k & (C::RB - 1)];
+      if (u < C::NO) {
+        const int so = u < B ? wrap(base + u) : C::W + wrap(base + u - B);
+        const float4 wv = lv[u];
+        F[so * C::NC] = df2f(df_sub_two_prods(f2df(F[so * C::NC]), make_df(wv.x, wv.y), yp, make_df(wv.z, wv.w), yq));
+      } else if (u == C::NO) {
+        const float4 r0 = lv[C::NO], r1 = lv[C::NO + 1];
+        const df cp = df_sub_two_prods(df_zero(), df_neg(make_df(r0.x, r0.y)), yp, df_neg(make_df(r0.z, r0.w)), yq);
+        const df cq = df_sub_two_prods(df_zero(), df_neg(make_df(r1.x, r1.y)), yp, df_neg(make_df(r1.z, r1.w)), yq);
+        stk[(size_t)k * C::SL + C::NO] = make_float4(cp.hi, cp.lo, cq.hi, cq.lo);
+      }
+      __syncwarp();
+      if (u < 2) F[(u ? sq : sp) * C::NC] = rhs_of(sm, u, tn, row_kind(sm, u, tn, s, n));
       __syncwarp();
       base = wrap(base + 1);
     }
@@ -523,6 +640,31 @@ __global__ void __launch_bounds__(32 * C3<B>::WARPS, 4) paqif3_kernel(Paqif3Args
   }
 }
 
+// Solve only, with the factorization stored by a factor launch (same systems,
+// same band): the W0 sweep for the new rhs, then the Z0 sweep.
+template <int B>
+__global__ void __launch_bounds__(32 * C3<B>::WARPS, 4) paqif3_solve_kernel(Paqif3Args a) {
+  using C = C3<B>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / C::LS, u = lane % C::LS;
+  Sm3<B>& sm = reinterpret_cast<Sm3<B>*>(smem_raw)[warp * C::G + grp];
+  const int ssys = (blockIdx.x * C::WARPS + warp) * C::G + grp;
+  const bool real = ssys < a.n_sys;
+  const int dsys = real ? ssys : a.n_sys - 1;
+  if (__all_sync(0xffffffffu, !real)) return;
+  int flag = 0;
+  P3<B>::w_sweep(sm, a, dsys, ssys, u);
+  P3<B>::z_solve(sm, a, dsys, ssys, real, u, flag);
+  int f = flag;
+#pragma unroll
+  for (int off = C::LS / 2; off > 0; off >>= 1) {
+    const int o = __shfl_xor_sync(0xffffffffu, f, off, C::LS);
+    if (f == 0) f = o;
+  }
+  if (real && u == 0 && a.info && f != 0) a.info[dsys] = f;
+}
+
 template <int B>
 static size_t p3_smem() {
   return sizeof(Sm3<B>) * (size_t)(C3<B>::WARPS * C3<B>::G);
@@ -551,7 +693,30 @@ size_t paqif_stack_bytes(int n_sys, int n, int beta) {
 }
 
 template <int B>
-static cudaError_t launch3(const PaqifLaunch& L, cudaStream_t st) {
+static int p3_fl() {
+  return C3<B>::FL;
+}
+
+size_t paqif_factor_store_bytes(int n_sys, int n, int beta) {
+  const int s = (n + 1) / 2;
+  int per = 0, fl = 0;
+  switch (beta) {
+#define EHL_CASE(BB)          \
+  case BB:                    \
+    per = p3_per_cta<BB>();   \
+    fl = p3_fl<BB>();         \
+    break;
+    EHL_CASE(1) EHL_CASE(2) EHL_CASE(3) EHL_CASE(4) EHL_CASE(5) EHL_CASE(6) EHL_CASE(7) EHL_CASE(8)
+#undef EHL_CASE
+    default:
+      return 0;
+  }
+  const size_t padded = (size_t)((n_sys + per - 1) / per) * per;
+  return padded * (size_t)s * (size_t)fl * sizeof(float4);
+}
+
+template <int B>
+static cudaError_t launch3(const PaqifLaunch& L, cudaStream_t st, void* fstore, bool solve_only) {
   Paqif3Args a;
   a.n_sys = L.n_sys;
   a.n = L.n;
@@ -561,15 +726,23 @@ static cudaError_t launch3(const PaqifLaunch& L, cudaStream_t st) {
   a.rhs = L.rhs;
   a.act = L.act;
   a.stack = reinterpret_cast<float4*>(L.stack);
+  a.fstore = reinterpret_cast<float4*>(fstore);
   a.x = L.x;
   a.iters = L.iters;
   a.info = L.info;
   const size_t smem = p3_smem<B>();
-  cudaError_t e = cudaFuncSetAttribute(paqif3_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const int per = p3_per_cta<B>();
   const int grid = (L.n_sys + per - 1) / per;
-  paqif3_kernel<B><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
+  cudaError_t e;
+  if (solve_only) {
+    e = cudaFuncSetAttribute(paqif3_solve_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    paqif3_solve_kernel<B><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(paqif3_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    paqif3_kernel<B><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -588,18 +761,30 @@ cudaError_t launch_expand_active(const uint8_t* in, int* out, size_t total, cuda
   return cudaGetLastError();
 }
 
-cudaError_t launch_paqif(const PaqifLaunch& L, cudaStream_t st) {
+static cudaError_t dispatch3(const PaqifLaunch& L, cudaStream_t st, void* fstore, bool solve_only) {
   switch (L.beta) {
-    case 1: return launch3<1>(L, st);
-    case 2: return launch3<2>(L, st);
-    case 3: return launch3<3>(L, st);
-    case 4: return launch3<4>(L, st);
-    case 5: return launch3<5>(L, st);
-    case 6: return launch3<6>(L, st);
-    case 7: return launch3<7>(L, st);
-    case 8: return launch3<8>(L, st);
+    case 1: return launch3<1>(L, st, fstore, solve_only);
+    case 2: return launch3<2>(L, st, fstore, solve_only);
+    case 3: return launch3<3>(L, st, fstore, solve_only);
+    case 4: return launch3<4>(L, st, fstore, solve_only);
+    case 5: return launch3<5>(L, st, fstore, solve_only);
+    case 6: return launch3<6>(L, st, fstore, solve_only);
+    case 7: return launch3<7>(L, st, fstore, solve_only);
+    case 8: return launch3<8>(L, st, fstore, solve_only);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_paqif(const PaqifLaunch& L, cudaStream_t st) { return dispatch3(L, st, nullptr, false); }
+
+cudaError_t launch_paqif_factor(const PaqifLaunch& L, void* fstore, cudaStream_t st) {
+  if (L.mode == 2 || !fstore) return cudaErrorInvalidValue;
+  return dispatch3(L, st, fstore, false);
+}
+
+cudaError_t launch_paqif_resolve(const PaqifLaunch& L, void* fstore, cudaStream_t st) {
+  if (L.mode == 2 || !fstore) return cudaErrorInvalidValue;
+  return dispatch3(L, st, fstore, true);
 }
 
 }  // namespace ehl
