@@ -3,20 +3,26 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Workload: the high-load line-contact configuration -- converged line-contact
-solves (N = 1025, M = 200, L = 10, van Leer, band half-width 8) together with
-the standalone PAQIF batch of that configuration (4096 strictly diagonally
-dominant banded float64 systems, n = 1024, half-width 4, off-diagonals
-U(-1,1), diagonal 1.5 x row abs-sum, rhs U(-1,1), solved with projection onto
-x >= 0).  All inputs are synthetic and seeded.
+Workload: the high-load line-contact configuration.  One step is
+  (A) the standalone PAQIF batch of that configuration: 4096 strictly
+      diagonally dominant banded float64 systems, n = 1024, half-width 4,
+      off-diagonals U(-1,1), diagonal 1.5 x row abs-sum, rhs U(-1,1), solved
+      with projection onto x >= 0 (one kernel launch), and
+  (B) a batch of converged line-contact solves: N = 1025 nodes, M = 200,
+      L = 10, van Leer limiter, Roelands/Dowson-Higginson lubricant, band
+      half-width 8, Newton-Krylov with the PAQIF band preconditioner, from
+      the Hertzian start to ||min(P,R)||_inf <= 1e-8 and |h sum P - pi/2| <= 1e-8.
+`value` is converged solves per second of leg B; leg A's GB/s and its HBM
+roofline are reported under "paqif" and "roofline".  All inputs are
+synthetic; nothing is read from disk.
 
-One step = one pass of every hot-path stage over one batch.  The timed region
-is bracketed by a barrier and torch.cuda.synchronize(); device time is taken
-with CUDA events on the launching stream; the inputs of the PAQIF batch
-(369 MB moved per step) exceed the 129 MB L2, so no flush is needed.
+Timing: a barrier and torch.cuda.synchronize() bracket the K timed steps;
+each leg is timed with CUDA events on the launching stream.  Leg A moves
+369 MB per step, more than the 129 MB L2, so no flush is needed; leg B's
+working set is small but each step starts again from the Hertzian pressure.
 
 `--impl reference` times the plain float64 CPU oracle on the same workload
-(bounded sample per step) on the host cores.
+(a bounded sample per step) on the host cores.
 """
 import argparse
 import json
@@ -25,7 +31,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -35,11 +40,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "converged EHL solves/s at residual<1e-8; PAQIF solve GB/s vs HBM peak"
 PAQIF_NSYS, PAQIF_N, PAQIF_BETA, PAQIF_MODE = 4096, 1024, 4, 1
+EHL = dict(N=1025, M=200.0, L=10.0, limiter=1, beta=8, tol=1e-8)
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes (read + write) of one full-size paqif_kernel<4> launch from the ncu capture
-# summarised in profiles/paqif_kernel_beta4_standalone.md, valid only for the kernel
-# sources with these sha256 prefixes; any other source reports traffic = null.
+# DRAM bytes (read + write) of one full-size paqif3_kernel<4> launch from the ncu
+# capture summarised in profiles/, valid only for the kernel sources with these
+# sha256 prefixes; any other source reports traffic = null.
 PAQIF_TRAFFIC = {}
 
 
@@ -131,6 +137,11 @@ def dist_env():
     return world, rank, local
 
 
+def ehl_params(ops):
+    return ops.default_params(1, nx=EHL["N"], M=EHL["M"], L=EHL["L"], limiter=EHL["limiter"], halfband=EHL["beta"],
+                              method=1, tol=EHL["tol"], max_iter=60, krylov_dim=40)
+
+
 # --------------------------------------------------------------------------- ours
 def run_ours(args):
     import torch
@@ -143,86 +154,112 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    global PAQIF_NSYS
-    PAQIF_NSYS = args.paqif_nsys
-    band_h, rhs_h = inputs.dd_band_systems(PAQIF_NSYS, PAQIF_N, PAQIF_BETA, seed=rank)
+    n_sys = args.paqif_nsys
+    band_h, rhs_h = inputs.dd_band_systems(n_sys, PAQIF_N, PAQIF_BETA, seed=rank)
     band = torch.from_numpy(band_h).to(dev)
     rhs = torch.from_numpy(rhs_h).to(dev)
     x = torch.empty_like(rhs)
-    ws = torch.empty(ops.paqif_workspace_size(PAQIF_NSYS, PAQIF_N, PAQIF_BETA, PAQIF_MODE), dtype=torch.uint8,
-                     device=dev)
+    ws = torch.empty(ops.paqif_workspace_size(n_sys, PAQIF_N, PAQIF_BETA, PAQIF_MODE), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    B = args.ehl_batch
+    ctx = ops.Context(ehl_params(ops), n_inst=B) if B > 0 else None
+    sol = {}
 
-    def step():
+    def leg_a():
         ops.paqif_solve(band, rhs, PAQIF_BETA, PAQIF_MODE, x=x, workspace=ws)
 
+    def leg_b():
+        if ctx is not None:
+            sol["P"], sol["H0"], sol["iters"], sol["res"], sol["code"] = ctx.solve(check=False)
+
     for _ in range(args.warmup):
-        step()
+        leg_a()
+        leg_b()
     torch.cuda.synchronize()
     _, _, info = ops.paqif_solve(band, rhs, PAQIF_BETA, PAQIF_MODE, x=x, workspace=ws)
-    ok = bool((info == 0).all().item())
+    paqif_ok = bool((info == 0).all().item())
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
+    n0 = ops.kernel_launches()
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
         t0 = time.perf_counter()
-        evs[0].record(stream)
         for k in range(args.steps):
-            step()
-            evs[k + 1].record(stream)
+            ev[k][0].record(stream)
+            leg_a()
+            ev[k][1].record(stream)
+            leg_b()
+            ev[k][2].record(stream)
         torch.cuda.synchronize()
         barrier()
         wall = time.perf_counter() - t0
-    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    ms = sum(per) / len(per)
+    launches = ops.kernel_launches() - n0
+    ta = [e[0].elapsed_time(e[1]) for e in ev]
+    tb = [e[1].elapsed_time(e[2]) for e in ev]
+    ms_a, ms_b = sum(ta) / len(ta), sum(tb) / len(tb)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
+        t = torch.tensor([ms_a, ms_b], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    nbytes = paqif_bytes(PAQIF_NSYS, PAQIF_N, PAQIF_BETA)
-    gbs = nbytes / (ms * 1e-3) / 1e9
+        ms_a, ms_b = float(t[0]), float(t[1])
+    ms = ms_a + ms_b
+    nbytes = paqif_bytes(n_sys, PAQIF_N, PAQIF_BETA)
+    gbs = nbytes / (ms_a * 1e-3) / 1e9
     hbm, src = peaks()
+    ehl_ok, ehl_iters, ehl_res = None, None, None
+    if ctx is not None:
+        ehl_ok = int(sol["code"]) == 0
+        it = sol["iters"].cpu().numpy()
+        rs = sol["res"].cpu().numpy()
+        ehl_iters = [int(it.min()), int(it.max())]
+        ehl_res = float(np.max(np.abs(rs)))
 
-    # end to end through the public API with host buffers (pinned), copies inside
+    # end to end through the public API with pinned host buffers, copies inside the timed region
+    e2e_b = None
+    if ctx is not None:
+        P_p = torch.empty((B, EHL["N"]), dtype=torch.float64).pin_memory()
+        H0_p = torch.empty(B, dtype=torch.float64).pin_memory()
+        it_p = torch.empty(B, dtype=torch.int32).pin_memory()
+        res_p = torch.empty((B, 2), dtype=torch.float64).pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            P, H0, iters, res, _ = ctx.solve(check=False)
+            P_p.copy_(P, non_blocking=True)
+            H0_p.copy_(H0, non_blocking=True)
+            it_p.copy_(iters, non_blocking=True)
+            res_p.copy_(res, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_b = e0.elapsed_time(e1) / args.steps
     band_p = torch.from_numpy(band_h).pin_memory()
     rhs_p = torch.from_numpy(rhs_h).pin_memory()
     x_p = torch.empty(rhs_p.shape, dtype=torch.float64).pin_memory()
-    band_d = torch.empty_like(band)
-    rhs_d = torch.empty_like(rhs)
-
-    def e2e_step():
+    band_d, rhs_d = torch.empty_like(band), torch.empty_like(rhs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
         band_d.copy_(band_p, non_blocking=True)
         rhs_d.copy_(rhs_p, non_blocking=True)
         ops.paqif_solve(band_d, rhs_d, PAQIF_BETA, PAQIF_MODE, x=x, workspace=ws)
         x_p.copy_(x, non_blocking=True)
-
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    h2d = band_h.nbytes + rhs_h.nbytes
-    d2h = rhs_h.nbytes
+    e2e_a = e0.elapsed_time(e1) / args.steps
 
     if rank != 0:
         return None
-    total = world * nbytes / (ms * 1e-3) / 1e9
+    solves = world * B / (ms_b * 1e-3) if B > 0 else None
     line = {
         "metric": METRIC,
-        "value": round(total, 2),
-        "unit": "GB/s",
+        "value": round(solves, 3) if solves is not None else None,
+        "unit": "converged solves/s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
@@ -230,21 +267,28 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 (double-float f32 pairs inside the kernel)",
+        "dtype": "f64 (double-float f32 pairs in the O(N^2) and O(N beta^2) kernels)",
         "data": "synthetic (seeded)",
         "config": {
-            "workload": "standalone PAQIF of the high-load line-contact config: 4096 systems, n=1024, beta=4, "
-                        "diagonal 1.5x row abs-sum, mode 1 (solve + projection)",
-            "n_sys": PAQIF_NSYS, "n": PAQIF_N, "beta": PAQIF_BETA, "mode": PAQIF_MODE,
-            "l2": "inputs larger than L2 (369 MB per step)", "parity_ok": ok,
+            "workload": "high-load line contact: batch of converged solves N=1025, M=200, L=10, van Leer, "
+                        "beta=8, tol 1e-8, plus the standalone PAQIF batch (4096 x n=1024, beta=4, mode 1)",
+            "ehl_batch": B, "ehl_N": EHL["N"], "ehl_M": EHL["M"], "ehl_L": EHL["L"], "ehl_beta": EHL["beta"],
+            "ehl_ms": round(ms_b, 3), "ehl_newton_iters_min_max": ehl_iters, "ehl_max_final_residual": ehl_res,
+            "ehl_all_converged": ehl_ok,
+            "paqif_n_sys": n_sys, "paqif_n": PAQIF_N, "paqif_beta": PAQIF_BETA, "paqif_mode": PAQIF_MODE,
+            "paqif_parity_ok": paqif_ok,
+            "l2": "PAQIF leg inputs larger than L2 (369 MB per step)",
             "parallelism": f"{world} independent replica batch(es)",
         },
+        "paqif": {"gbs": round(gbs, 2), "ms": round(ms_a, 4), "frac_of_measured_hbm": round(gbs / hbm, 4)},
         "roofline": {"bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "traffic": paqif_traffic(),
-                     "kernel": "paqif3_kernel<4>", "peak_source": src},
-        "e2e": {"value": round(world * nbytes / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps,
+                     "kernel": "paqif3_kernel<4> (leg A)", "peak_source": src},
+        "e2e": {"value": round(world * B / (e2e_b * 1e-3), 3) if e2e_b else None, "unit": "converged solves/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": B * (EHL["N"] + 1 + 2) * 8 + B * 4,
+                "paqif_gbs": round(world * nbytes / (e2e_a * 1e-3) / 1e9, 2),
+                "paqif_h2d_bytes_per_step": band_h.nbytes + rhs_h.nbytes, "paqif_d2h_bytes_per_step": rhs_h.nbytes},
+        "gpu_launches": launches,
         "clocks": clk.summary(),
         "wall_s": round(wall, 3),
     }
@@ -254,19 +298,36 @@ def run_ours(args):
 
 
 # --------------------------------------------------------------------------- oracle
+def oracle_ehl_solve():
+    from oracle import line_ref as lr
+
+    pb = lr.LineProblem(EHL["N"], EHL["M"], EHL["L"], limiter=("minmod", "vanleer")[EHL["limiter"]])
+    P, H0, info = lr.solve(pb, tol=EHL["tol"])
+    return info["converged"]
+
+
 def cpu_baseline(band_h, rhs_h, budget_s=12.0):
-    """The oracle (dense float64 LU per system) on a bounded sample of the batch."""
+    """The oracle (dense semismooth Newton; dense LU per PAQIF system) on a bounded sample."""
     from oracle import paqif_ref as pr
 
-    done, t0 = 0, time.perf_counter()
-    while done < band_h.shape[0] and (time.perf_counter() - t0) < budget_s:
-        pr.paqif_reference(band_h[done:done + 1], rhs_h[done:done + 1], PAQIF_BETA, PAQIF_MODE)
+    t0 = time.perf_counter()
+    done = 0
+    while done < 1 or (time.perf_counter() - t0) < 0.7 * budget_s:
+        oracle_ehl_solve()
         done += 1
+        if done >= 8:
+            break
     dt = time.perf_counter() - t0
-    nbytes = paqif_bytes(done, PAQIF_N, PAQIF_BETA)
-    return {"value": round(nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{done} of {band_h.shape[0]} systems (dense LU per system, numpy BLAS default threads), "
-                      f"{dt:.1f} s"}
+    sps = done / dt
+    t1, nsys = time.perf_counter(), 0
+    while nsys < band_h.shape[0] and (time.perf_counter() - t1) < 0.3 * budget_s:
+        pr.paqif_reference(band_h[nsys:nsys + 1], rhs_h[nsys:nsys + 1], PAQIF_BETA, PAQIF_MODE)
+        nsys += 1
+    dt2 = time.perf_counter() - t1
+    return {"value": round(sps, 5), "unit": "converged solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} line-contact solve(s) of the leg-B instance ({dt:.1f} s, numpy BLAS default "
+                      f"threads); PAQIF leg: {nsys} systems by dense LU ({dt2:.1f} s) = "
+                      f"{paqif_bytes(nsys, PAQIF_N, PAQIF_BETA) / dt2 / 1e9:.5f} GB/s"}
 
 
 def run_reference(args):
@@ -275,39 +336,45 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return None
-    band_h, rhs_h = inputs.dd_band_systems(PAQIF_NSYS, PAQIF_N, PAQIF_BETA, seed=0)
     from oracle import paqif_ref as pr
 
-    per_step = max(1, int(args.ref_systems))
+    band_h, rhs_h = inputs.dd_band_systems(args.ref_systems, PAQIF_N, PAQIF_BETA, seed=0)
     for _ in range(args.warmup):
         pr.paqif_reference(band_h[:1], rhs_h[:1], PAQIF_BETA, PAQIF_MODE)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        lo = (k * per_step) % PAQIF_NSYS
-        pr.paqif_reference(band_h[lo:lo + per_step], rhs_h[lo:lo + per_step], PAQIF_BETA, PAQIF_MODE)
+    ta = 0.0
+    for _ in range(args.steps):
+        a0 = time.perf_counter()
+        pr.paqif_reference(band_h, rhs_h, PAQIF_BETA, PAQIF_MODE)
+        ta += time.perf_counter() - a0
+        oracle_ehl_solve()
     dt = (time.perf_counter() - t0) / args.steps
-    val = paqif_bytes(per_step, PAQIF_N, PAQIF_BETA) / dt / 1e9
+    tb = dt - ta / args.steps
+    val = 1.0 / tb
     return {
-        "impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "GB/s", "n_gpus": world,
+        "impl": "reference", "metric": METRIC, "value": round(val, 5), "unit": "converged solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-        "config": {"workload": "standalone PAQIF of the high-load line-contact config (oracle: dense LU)",
-                   "n_sys": PAQIF_NSYS, "n": PAQIF_N, "beta": PAQIF_BETA, "mode": PAQIF_MODE},
-        "cpu_baseline": {"value": round(val, 6), "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"{per_step} systems per step"},
-        "e2e": {"value": round(val, 6), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": "high-load line contact (oracle): one converged solve N=1025, M=200, L=10, van Leer "
+                               f"per step, plus {args.ref_systems} PAQIF systems by dense LU"},
+        "paqif": {"gbs": round(paqif_bytes(args.ref_systems, PAQIF_N, PAQIF_BETA) / (ta / args.steps) / 1e9, 6)},
+        "cpu_baseline": {"value": round(val, 5), "unit": "converged solves/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": f"1 solve + {args.ref_systems} PAQIF systems per step"},
+        "e2e": {"value": round(val, 5), "unit": "converged solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
     }
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-systems", type=int, default=8)
+    ap.add_argument("--ref-systems", type=int, default=4)
+    ap.add_argument("--ehl-batch", type=int, default=512, help="line-contact instances solved per step")
     ap.add_argument("--paqif-nsys", type=int, default=PAQIF_NSYS,
                     help="systems in the PAQIF batch (smaller only for profiling captures)")
     args = ap.parse_args()

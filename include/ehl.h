@@ -53,6 +53,10 @@ const char* ehl_status_string(ehl_status s);
 /* Library version as major*10000 + minor*100 + patch. */
 int ehl_version(void);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all devices, all streams; a monotone counter for instrumentation). */
+unsigned long long ehl_kernel_launches(void);
+
 /* ------------------------------------------------------------------------
  * PAQIF: batched projected alternate quadrant interlocking factorization
  * ------------------------------------------------------------------------

@@ -29,6 +29,7 @@ EHL_OK, EHL_EINVAL, EHL_ENOMEM, EHL_ECUDA, EHL_ENOCONV, EHL_ENONFINITE, EHL_ESIN
 SYMBOLS = {
     "ehl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ehl_version": (ctypes.c_int, []),
+    "ehl_kernel_launches": (ctypes.c_ulonglong, []),
     "ehl_paqif_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_size_t)]),
     "ehl_paqif_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,

@@ -2,7 +2,14 @@
 // workspace carving and kernel launches.  No compute happens on the host.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "ehl_internal.h"
+
+namespace ehl {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace ehl
 
 using namespace ehl;
 
@@ -21,6 +28,8 @@ extern "C" const char* ehl_status_string(ehl_status s) {
 }
 
 extern "C" int ehl_version(void) { return 100; }
+
+extern "C" unsigned long long ehl_kernel_launches(void) { return ehl::g_launches.load(std::memory_order_relaxed); }
 
 static bool paqif_args_ok(int n_sys, int n, int beta, int mode) {
   return n_sys >= 1 && n_sys <= (1 << 24) && n >= 1 && n <= (1 << 24) && beta >= 1 && beta <= 8 && mode >= 0 &&

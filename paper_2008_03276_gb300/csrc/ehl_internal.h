@@ -14,6 +14,9 @@ constexpr size_t kWorkspaceAlign = 256;
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Count of kernels this library has launched (observability; see ehl_kernel_launches).
+void note_launch();
+
 struct PaqifLaunch {
   int n_sys, n, beta, mode;
   const double* band;

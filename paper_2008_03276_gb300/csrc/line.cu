@@ -467,6 +467,7 @@ LineRowCtx line_row_ctx(LineCtx* c) {
 cudaError_t line_deform(LineCtx* c, const double* V, int vstride, const int* skip) {
   dim3 g((c->N + kDefTI - 1) / kDefTI, c->ksplit, c->n_inst);
   k_line_deform<<<g, kDefTI, 0, c->st>>>(c->inst, c->gtab, V, vstride, skip, c->partial, c->n_inst, c->N);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -478,10 +479,14 @@ cudaError_t line_state(LineCtx* c, const double* P, const double* H0, const doub
   dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
   k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->partial, c->ksplit, H0, rough, c->N, skip, c->H,
                                              c->n_inst, c->N, 0);
+  note_launch();
   k_line_nodes<<<gn, kNodeBlock, 0, c->st>>>(c->inst, P, c->H, skip, c->rho, c->drho, c->deta_rel, c->eps, c->u,
                                               c->N);
+  note_launch();
   k_line_faces<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->u, skip, c->F, c->psi, c->psia, c->psib, c->N);
+  note_launch();
   k_line_residual<<<gn, kNodeBlock, 0, c->st>>>(c->inst, P, c->H, c->eps, c->F, skip, c->R, c->blk, c->nblk, c->N);
+  note_launch();
   (void)iters_done_flag_mode;
   return cudaGetLastError();
 }
@@ -489,6 +494,7 @@ cudaError_t line_state(LineCtx* c, const double* P, const double* H0, const doub
 cudaError_t line_finalize(LineCtx* c, int* done, int* iters) {
   k_line_finalize<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(c->inst, c->blk, c->nblk, c->red, done, iters,
                                                                c->n_inst);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -498,17 +504,20 @@ cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, u
   q.P = P;
   dim3 g((c->n + 127) / 128, c->n_inst);
   k_line_jac_band<<<g, 128, 0, c->st>>>(c->inst, q, c->R, skip, kind, c->beta, band, act, jh, dg);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t line_start(LineCtx* c, double* P, double* H0, const double* rough) {
   dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
   k_line_hertz<<<gn, kNodeBlock, 0, c->st>>>(c->inst, P, c->N);
+  note_launch();
   cudaError_t e = cudaMemsetAsync(H0, 0, sizeof(double) * c->n_inst, c->st);
   if (e != cudaSuccess) return e;
   e = line_state(c, P, H0, rough, nullptr, nullptr);
   if (e != cudaSuccess) return e;
   k_line_set_h0<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(c->inst, c->blk, c->nblk, H0, c->n_inst);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -523,6 +532,7 @@ cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double
   if (e != cudaSuccess) return e;
   dim3 g((c->n + 127) / 128, c->n_inst);
   k_line_paper_rhs<<<g, 128, 0, c->st>>>(c->R, c->act, c->done, c->rhs, c->N);
+  note_launch();
   PaqifLaunch L;
   L.n_sys = c->n_inst;
   L.n = c->n;
@@ -541,7 +551,9 @@ cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double
   if (e != cudaSuccess) return e;
   dim3 gu((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
   k_line_paper_update<<<gu, kNodeBlock, 0, c->st>>>(c->inst, c->sigma, c->eps, c->done, P, c->blk, c->nblk, c->N);
+  note_launch();
   k_line_h0_update<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(c->inst, c->blk, c->nblk, c->done, H0, c->n_inst);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -552,12 +564,14 @@ cudaError_t line_film_dir(LineCtx* c, const double* zh0, const int* skip) {
   dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
   k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->partial, c->ksplit, zh0, nullptr, c->N, skip, c->dH,
                                              c->n_inst, c->N, 1);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t line_init_tables(LineCtx* c) {
   dim3 g((c->N + 255) / 256, c->n_inst);
   k_line_gtab<<<g, 256, 0, c->st>>>(c->inst, c->gtab, c->N);
+  note_launch();
   return cudaGetLastError();
 }
 }  // namespace ehl

@@ -358,6 +358,7 @@ cudaError_t line_jacobian_apply(LineCtx* c, const double* P, const double* H0, c
   JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, v};
   const dim3 gn((c->N + 255) / 256, c->n_inst);
   k_line_jv_raw<<<gn, 256, 0, c->st>>>(c->inst, q, out, c->N);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -449,35 +450,45 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
   if (e != cudaSuccess) return e;
   k_nk_setup<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, P, c->R, c->red, c->act, c->dg, c->jh, c->done, c->band,
                                          c->rhs, N, c->beta);
+  note_launch();
   e = paqif_on(c, c->rhs, c->sigma, true);  // factor, solving for the border column
   if (e != cudaSuccess) return e;
   k_nk_border<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->sigma, c->done, c->rhs, N);
+  note_launch();
   const dim3 gn((N + 255) / 256, ni);
   for (int j = 0; j < b.m; ++j) {
     k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.gm_conv, b.skip, ni);
+    note_launch();
     e = paqif_on(c, c->rhs, c->sigma, false);
     if (e != cudaSuccess) return e;
     k_nk_prec<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, b.skip, N);
+    note_launch();
     e = line_deform(c, b.znode, N, b.skip);
     if (e != cudaSuccess) return e;
     e = line_film_dir(c, b.zh0, b.skip);
     if (e != cudaSuccess) return e;
     JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, b.znode};
     k_nk_jv<<<gn, 256, 0, c->st>>>(c->inst, b, q, c->act, c->dg, b.skip, N);
+    note_launch();
     k_nk_arnoldi<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, b.skip, c->rhs, N);
+    note_launch();
     if ((j + 1) % 8 == 0 && j + 1 < b.m) {
       if (all_set(c, c->done, b.gm_conv, e)) break;
       if (e != cudaSuccess) return e;
     }
   }
   k_nk_update<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->done, N);
+  note_launch();
   for (int trial = 0; trial < 40; ++trial) {
     k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.lsdone, b.skip, ni);
+    note_launch();
     k_nk_trial<<<gn, 256, 0, c->st>>>(b, P, H0, b.skip, N);
+    note_launch();
     e = line_state(c, b.Pt, b.H0t, rough, b.skip, nullptr);
     if (e == cudaSuccess) e = line_finalize(c, nullptr, nullptr);
     if (e != cudaSuccess) return e;
     k_nk_merit<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->R, c->red, c->dg, b.skip, P, H0, N);
+    note_launch();
     if (all_set(c, c->done, b.lsdone, e)) break;
     if (e != cudaSuccess) return e;
   }

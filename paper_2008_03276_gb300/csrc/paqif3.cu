@@ -738,10 +738,12 @@ static cudaError_t launch3(const PaqifLaunch& L, cudaStream_t st, void* fstore, 
     e = cudaFuncSetAttribute(paqif3_solve_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     paqif3_solve_kernel<B><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
+    note_launch();
   } else {
     e = cudaFuncSetAttribute(paqif3_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     paqif3_kernel<B><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
+    note_launch();
   }
   return cudaGetLastError();
 }
@@ -758,6 +760,7 @@ cudaError_t launch_expand_active(const uint8_t* in, int* out, size_t total, cuda
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   expand_active3_kernel<<<blocks, 256, 0, st>>>(in, out, total);
+  note_launch();
   return cudaGetLastError();
 }
 

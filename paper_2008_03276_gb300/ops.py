@@ -28,6 +28,11 @@ def _check_dev(*ts):
             raise ValueError("tensors must be contiguous CUDA tensors")
 
 
+def kernel_launches():
+    """Kernels the CUDA library has launched in this process."""
+    return int(_ffi.load().ehl_kernel_launches())
+
+
 def paqif_workspace_size(n_sys, n, beta, mode):
     lib = _ffi.load()
     out = ctypes.c_size_t(0)
