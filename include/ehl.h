@@ -120,8 +120,15 @@ ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* band, const
  * lambda and alpha_bar = alpha p_H come from the Moes parameters:
  *   lambda = 3 pi^2 / (8 M^2), alpha_bar = L sqrt(M / (2 pi)).
  *
- * Arrays of one context with n_inst instances of nx nodes are [n_inst][nx]
- * (nodal, including the two boundary nodes where P = 0), [n_inst] for H0.
+ * Arrays of one context are [n_inst][nx_max] with nx_max the largest nx of
+ * its instances (nodal, including the two boundary nodes where P = 0): the
+ * row of instance k holds its own nx_k nodes first; entries past nx_k are
+ * neither read nor written.  H0 is [n_inst].  Band arrays are
+ * [n_inst][nx_max - 2][2 beta + 1] and active [n_inst][nx_max - 2], padded
+ * the same way.  A batch may mix grid sizes (ragged batch): instances are
+ * grouped by nx and each group runs on its own stream, forked from and
+ * joined back to the context's stream; with a single grid size the kernels
+ * work on the caller's arrays in place.
  */
 typedef struct ehl_ctx ehl_ctx;
 
@@ -146,32 +153,41 @@ typedef struct {
   int max_iter;         /* cap on outer iterations                                      */
   int krylov_dim;       /* GMRES basis size per Newton step (method 1)                  */
   double h_init;        /* Hertzian start: H0 chosen so that min H = h_init             */
+  int levels;           /* nested iteration: coarse grids solved first (init = 0 only);  */
+                        /*   -1 as many as allowed (default), 0 none                     */
+  int coarse_min_nodes; /* coarsest grid keeps at least this many nodes (65)             */
+  double coarse_tol;    /* tolerance of the coarse-grid solves, max(tol, coarse_tol) (1e-6) */
 } ehl_params;
 
 /* Fill *p with the defaults above for dimension `dim` (1). */
 void ehl_params_default(ehl_params* p, int dim);
 
 /* Create a context for n_inst instances.  `p` gives the shared settings; if
- * per_inst is not NULL it gives per-instance parameters (n_inst entries; nx,
- * dim, halfband and method must equal p's).  The context owns its device
+ * per_inst is not NULL it gives per-instance parameters (n_inst entries; dim,
+ * halfband and method must equal p's, nx may differ: nx_max is the largest
+ * of p->nx and the per-instance nx).  The context owns its device
  * workspace (allocated here with cudaMalloc) and enqueues on `stream`.
- * Returns EHL_EINVAL for invalid parameters (nx < 5 or > 65536, beta outside
- * 1..8, M <= 0, xb <= xa, ...), EHL_ENOMEM, EHL_ECUDA. */
+ * Returns EHL_EINVAL for invalid parameters (n_inst outside 1..65535, nx < 5
+ * or > 65536, beta outside 1..8, M <= 0, xb <= xa, ...), EHL_ENOMEM,
+ * EHL_ECUDA.  With levels != 0 the context also holds the coarse grids of
+ * the nested iteration (nx_l - 1 = (nx - 1) / 2^l while that is an integer
+ * and nx_l >= coarse_min_nodes), about as much memory again as the finest. */
 ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_params* per_inst, void* stream, ehl_ctx** out);
 
 /* Release the context and its device memory (synchronises its stream). */
 ehl_status ehl_destroy(ehl_ctx* ctx);
 
-/* Residual at (P, H0): R [n_inst][nx] (0 at boundary nodes), H (nullable)
- * [n_inst][nx] film thickness, comp_res (nullable) [n_inst][2] =
+/* Residual at (P, H0): R [n_inst][nx_max] (0 at boundary nodes), H (nullable)
+ * [n_inst][nx_max] film thickness, comp_res (nullable) [n_inst][2] =
  * (||min(P,R)||_inf over interior nodes, h sum P - pi/2).  rough nullable.
  * Asynchronous. */
 ehl_status ehl_residual(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, double* R,
                         double* H, double* comp_res);
 
 /* Band Jacobian at (P, H0), rows/columns = interior nodes (n = nx - 2),
- * band [n_inst][n][2 beta + 1] in the PAQIF row-major layout, active
- * [n_inst][n] uint8.
+ * band [n_inst][nx_max - 2][2 beta + 1] in the PAQIF row-major layout
+ * (instance k fills its first n_k = nx_k - 2 rows), active
+ * [n_inst][nx_max - 2] uint8.
  *  kind 0: the paper's limiter-based Newton matrix (Sec. 3.3.3-3.3.4):
  *          eps, rho and the limiter factor frozen, the film change through
  *          the kernel, the weighted-change distribution on the subregion
@@ -186,18 +202,29 @@ ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const double* H0, co
 /* Exact directional derivative of the residual at (P, H0):
  *   out = (dR/dP) v + (dR/dH0) v_h0,
  * every dependence on P included (the film through the kernel, rho, eta and
- * eps, the limiter on its current branch).  v [n_inst][nx] nodal with zeros
- * at the boundary nodes, v_h0 [n_inst], out [n_inst][nx] (0 at the boundary).
+ * eps, the limiter on its current branch).  v [n_inst][nx_max] nodal with
+ * zeros at the boundary nodes, v_h0 [n_inst], out [n_inst][nx_max] (0 at the
+ * boundary).
  * This is the operator the Newton-Krylov method (method 1) iterates on.
  * Asynchronous. */
 ehl_status ehl_jacobian_apply(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, const double* v,
                               const double* v_h0, double* out);
 
 /* Solve every instance.  init = 0: start from the Hertzian pressure with
- * H0 chosen so that min H = h_init; init = 1: start from the given P, H0.
+ * H0 chosen so that min H = h_init -- on the coarsest grid of the nested
+ * iteration when the context has coarse grids, each finer grid then starting
+ * from the linear interpolation of the solution below it (coarse grids solved
+ * to max(tol, coarse_tol), the roughness sampled at their nodes); init = 1:
+ * start from the given P, H0 on the target grid.
  * On return P, H0 hold the last iterate, iters (nullable, [n_inst] int32)
- * the outer iterations and final_res (nullable, [n_inst][2]) the residuals
- * as in ehl_residual.  Synchronises the stream (to test convergence).
+ * the outer iterations on the target grid and final_res (nullable, [n_inst][2]) the residuals
+ * as in ehl_residual.  Synchronises the stream (to test convergence); in a
+ * ragged batch each grid-size group iterates on its own host thread and
+ * stream, so groups with different iteration counts overlap on the GPU.
+ * An instance has converged when ||min(P,R)||_inf <= tol and
+ * |h sum P - pi/2| <= tol, or when the first has not halved for five outer
+ * iterations and lies within 1e3 roundoff units of the largest term of R
+ * (its rounding floor) with the force balance met.
  * Returns EHL_OK if every instance converged, EHL_ENOCONV if some reached
  * max_iter, EHL_ENONFINITE if some produced NaN/Inf. */
 ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const double* rough, int init, int* iters,

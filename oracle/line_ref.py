@@ -340,3 +340,64 @@ def solve_continuation(pb_factory, M_target, L_target, steps, **kw):
         if not info["converged"]:
             raise RuntimeError(f"continuation step M={M_target * f} did not converge")
     return pb, P, H0, info
+
+
+# ------------------------------------------------------------ grid sequence
+def grid_sequence(N, n_min=65, levels=-1):
+    """Grids ``N_0 < N_1 < ... < N_L = N`` with ``N_{l+1} - 1 = 2 (N_l - 1)``.
+
+    Coarsening halves the number of intervals while it stays even and the
+    coarse grid keeps at least ``n_min`` nodes; ``levels`` (``>= 0``) caps the
+    number of coarse grids, ``-1`` takes as many as the rule allows.  The
+    paper computes its line- and point-contact solutions on such a sequence
+    of grids (Sec. 4, coarse ``16+1`` up to fine ``1024+1`` nodes per axis).
+    """
+    seq = [int(N)]
+    while (seq[-1] - 1) % 2 == 0 and (seq[-1] - 1) // 2 + 1 >= n_min and (levels < 0 or len(seq) <= levels):
+        seq.append((seq[-1] - 1) // 2 + 1)
+    return seq[::-1]
+
+
+def prolong(Pc):
+    """Nodal vector on a grid of ``Nc`` nodes -> ``2 Nc - 1`` nodes, linear interpolation.
+
+    Coarse node ``i`` is fine node ``2 i``; a new fine node takes the mean of
+    its two coarse neighbours.
+    """
+    Pc = np.asarray(Pc, dtype=np.float64)
+    Pf = np.empty(2 * len(Pc) - 1)
+    Pf[0::2] = Pc
+    Pf[1::2] = 0.5 * (Pc[:-1] + Pc[1:])
+    return Pf
+
+
+def inject(vf, Nc):
+    """Fine nodal vector -> its values at the ``Nc`` nodes of a coarser grid of the sequence."""
+    vf = np.asarray(vf, dtype=np.float64)
+    stride = (len(vf) - 1) // (Nc - 1)
+    return vf[::stride].copy()
+
+
+def solve_nested(pb_factory, N, n_min=65, levels=-1, coarse_tol=1e-6, tol=1e-12, **kw):
+    """Nested iteration: solve on each grid of ``grid_sequence(N)``, coarse to fine.
+
+    ``pb_factory(N_l)`` builds the problem on ``N_l`` nodes (with the
+    roughness injected from the finest grid).  The coarsest solve starts from
+    the Hertzian pressure; each finer one from the prolonged pressure of the
+    grid below and its ``H0``.  Coarse grids are solved to ``max(tol,
+    coarse_tol)``, the finest to ``tol``.  Returns ``(pb, P_int, H0, info)``
+    of the finest grid, ``info["levels"]`` the ``(N_l, iterations,
+    converged)`` of every grid.
+    """
+    seq = grid_sequence(N, n_min, levels)
+    P = H0 = None
+    out = []
+    for l, Nl in enumerate(seq):
+        pb = pb_factory(Nl)
+        P0 = None if P is None else prolong(pb_prev.full(P))[1:-1]
+        t = tol if l == len(seq) - 1 else max(tol, coarse_tol)
+        P, H0, info = solve(pb, P_init=P0, H0_init=H0, tol=t, **kw)
+        out.append((Nl, info["iters"], info["converged"]))
+        pb_prev = pb
+    info["levels"] = out
+    return pb, P, H0, info

@@ -20,7 +20,8 @@ class EhlParams(ctypes.Structure):
                 ("halfband", ctypes.c_int), ("switch_eps_h", ctypes.c_double), ("dist_weight", ctypes.c_double),
                 ("c_h0", ctypes.c_double), ("omega", ctypes.c_double), ("method", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("krylov_dim", ctypes.c_int),
-                ("h_init", ctypes.c_double)]
+                ("h_init", ctypes.c_double), ("levels", ctypes.c_int), ("coarse_min_nodes", ctypes.c_int),
+                ("coarse_tol", ctypes.c_double)]
 
 
 EHL_OK, EHL_EINVAL, EHL_ENOMEM, EHL_ECUDA, EHL_ENOCONV, EHL_ENONFINITE, EHL_ESINGULAR, EHL_ETIMEOUT = range(8)

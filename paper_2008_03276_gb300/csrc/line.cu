@@ -2,6 +2,7 @@
 // double-float Toeplitz deformation, float64 lubricant model and TVD residual,
 // the band Jacobians, and the paper's limiter-based Newton-Raphson relaxation.
 #include <cuda_runtime.h>
+#include <float.h>
 #include <math.h>
 
 #include <vector>
@@ -21,13 +22,15 @@ constexpr int kNodeBlock = 256;
 __device__ __forceinline__ double nan_max(double a, double b) { return (a > b || a != a) ? a : b; }
 
 // ---------------------------------------------------------------- kernel table
-__global__ void k_line_gtab(const LineInst* __restrict__ inst, float2* __restrict__ gtab, int N) {
+__global__ void k_line_gtab(const LineInst* __restrict__ inst, float2* __restrict__ gtab, double* __restrict__ gtab64,
+                            int N) {
   const int z = blockIdx.y;
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= N) return;
   const double g = line_cell_integral(d, inst[z].h) / M_PI;
   const df v = df_from_double(g);
   gtab[(size_t)z * N + d] = make_float2(v.hi, v.lo);
+  gtab64[(size_t)z * N + d] = g;
 }
 
 // ---------------------------------------------------------------- deformation
@@ -82,20 +85,76 @@ __global__ void __launch_bounds__(kDefTI) k_line_deform(const LineInst* __restri
   out[i] = make_float2(hi, lo);
 }
 
+// The same sums in float64 (FMA accumulation per CTA chunk, chunks added in
+// float64 by the film kernel): the deformation of the residual, whose
+// rounding sets how far the outer iteration can drive ||min(P,R)||.  The
+// double-float form above (about 48 bits) serves the Krylov products.
+__global__ void __launch_bounds__(kDefTI) k_line_deform64(const LineInst* __restrict__ inst,
+                                                          const double* __restrict__ gtab64,
+                                                          const double* __restrict__ V, int vstride,
+                                                          const int* __restrict__ skip, double* __restrict__ partial,
+                                                          int n_inst, int N) {
+  const int z = blockIdx.z;
+  if (skip && skip[z]) return;
+  const int i0 = blockIdx.x * kDefTI, k0 = blockIdx.y * kDefSK;
+  const int tid = threadIdx.x;
+  double* out = partial + ((size_t)blockIdx.y * n_inst + z) * N;
+  if (!inst[z].elastic) {
+    if (i0 + tid < N) out[i0 + tid] = 0.0;
+    return;
+  }
+  __shared__ double Vs[kDefSK];
+  __shared__ double Gs[kDefTI + kDefSK - 1];
+  for (int t = tid; t < kDefSK; t += kDefTI) {
+    const int k = k0 + t;
+    Vs[t] = (k < N) ? V[(size_t)z * vstride + k] : 0.0;
+  }
+  const int base_d = i0 - (k0 + kDefSK - 1);
+  for (int m = tid; m < kDefTI + kDefSK - 1; m += kDefTI) {
+    int d = base_d + m;
+    d = d < 0 ? -d : d;
+    Gs[m] = (d < N) ? gtab64[(size_t)z * N + d] : 0.0;
+  }
+  __syncthreads();
+  const int i = i0 + tid;
+  if (i >= N) return;
+  const int kmax = min(kDefSK, N - k0);
+  // four interleaved accumulators: independent FMA chains
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int k = 0;
+  for (; k + 4 <= kmax; k += 4) {
+    s0 = fma(Gs[tid + kDefSK - 1 - k], Vs[k], s0);
+    s1 = fma(Gs[tid + kDefSK - 2 - k], Vs[k + 1], s1);
+    s2 = fma(Gs[tid + kDefSK - 3 - k], Vs[k + 2], s2);
+    s3 = fma(Gs[tid + kDefSK - 4 - k], Vs[k + 3], s3);
+  }
+  for (; k < kmax; ++k) s0 = fma(Gs[tid + kDefSK - 1 - k], Vs[k], s0);
+  out[i] = (s0 + s1) + (s2 + s3);
+}
+
 // mode 0: H = H0 + X^2/2 - D + rough;  mode 1: out = -D + dh0 (directional derivative of H)
+// partial holds float64 chunk sums when p64 is set, double-float ones otherwise
 __global__ void k_line_film(const LineInst* __restrict__ inst, const float2* __restrict__ partial, int ksplit,
                             const double* __restrict__ H0, const double* __restrict__ rough, int rstride,
-                            const int* __restrict__ skip, double* __restrict__ out, int n_inst, int N, int mode) {
+                            const int* __restrict__ skip, double* __restrict__ out, int n_inst, int N, int mode,
+                            int p64) {
   const int z = blockIdx.y;
   if (skip && skip[z]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  df D = df_zero();
-  for (int y = 0; y < ksplit; ++y) {
-    const float2 p = partial[((size_t)y * n_inst + z) * N + i];
-    D = df_add(D, make_df(p.x, p.y));
+  double Dd;
+  if (p64) {
+    const double* pd = reinterpret_cast<const double*>(partial);
+    Dd = 0.0;
+    for (int y = 0; y < ksplit; ++y) Dd += pd[((size_t)y * n_inst + z) * N + i];
+  } else {
+    df D = df_zero();
+    for (int y = 0; y < ksplit; ++y) {
+      const float2 p = partial[((size_t)y * n_inst + z) * N + i];
+      D = df_add(D, make_df(p.x, p.y));
+    }
+    Dd = df_to_double(D);
   }
-  const double Dd = df_to_double(D);
   if (mode == 0) {
     const double X = inst[z].xa + i * inst[z].h;
     double H = H0[z] + 0.5 * X * X - Dd;
@@ -156,7 +215,7 @@ __global__ void __launch_bounds__(kNodeBlock) k_line_residual(const LineInst* __
   if (skip && skip[z]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double h = inst[z].h;
-  double cres = 0.0, sp = 0.0, hmin = INFINITY;
+  double cres = 0.0, sp = 0.0, hmin = INFINITY, term = 0.0;
   if (i < N) {
     const size_t o = (size_t)z * N + i;
     hmin = H[o];
@@ -169,20 +228,25 @@ __global__ void __launch_bounds__(kNodeBlock) k_line_residual(const LineInst* __
       R[o] = r;
       cres = fabs(P[o] < r ? P[o] : r);  // NaN in r propagates
       sp = P[o];
+      // magnitude of the largest term of R_i (sets the rounding floor of R)
+      term = (fabs(F[o]) + fabs(F[o - 1])) / h +
+             (fabs(ef1 * (P[o + 1] - P[o])) + fabs(ef0 * (P[o] - P[o - 1]))) / (h * h);
     } else {
       R[o] = 0.0;
     }
   }
-  __shared__ double s_c[kNodeBlock], s_s[kNodeBlock], s_h[kNodeBlock];
+  __shared__ double s_c[kNodeBlock], s_s[kNodeBlock], s_h[kNodeBlock], s_t[kNodeBlock];
   s_c[threadIdx.x] = cres;
   s_s[threadIdx.x] = sp;
   s_h[threadIdx.x] = hmin;
+  s_t[threadIdx.x] = term;
   __syncthreads();
   for (int w = kNodeBlock / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
       s_c[threadIdx.x] = nan_max(s_c[threadIdx.x], s_c[threadIdx.x + w]);
       s_s[threadIdx.x] += s_s[threadIdx.x + w];
       s_h[threadIdx.x] = fmin(s_h[threadIdx.x], s_h[threadIdx.x + w]);
+      s_t[threadIdx.x] = fmax(s_t[threadIdx.x], s_t[threadIdx.x + w]);
     }
     __syncthreads();
   }
@@ -191,22 +255,24 @@ __global__ void __launch_bounds__(kNodeBlock) k_line_residual(const LineInst* __
     b[0] = s_c[0];
     b[1] = s_s[0];
     b[2] = s_h[0];
+    b[3] = s_t[0];
   }
 }
 
 // red[z] = (max|min(P,R)|, h sum P - pi/2, sum P, min H); convergence flag and iteration count
 __global__ void k_line_finalize(const LineInst* __restrict__ inst, const double* __restrict__ blk, int nblk,
                                 double* __restrict__ red, int* __restrict__ done, int* __restrict__ iters,
-                                int n_inst) {
+                                double* __restrict__ best, int* __restrict__ stall, int n_inst) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
   if (z >= n_inst) return;
   if (done && done[z]) return;
-  double c = 0.0, s = 0.0, hm = INFINITY;
+  double c = 0.0, s = 0.0, hm = INFINITY, tm = 0.0;
   for (int b = 0; b < nblk; ++b) {
     const double* p = blk + ((size_t)z * nblk + b) * 4;
     c = nan_max(c, p[0]);
     s += p[1];
     hm = fmin(hm, p[2]);
+    tm = fmax(tm, p[3]);
   }
   const double force = inst[z].h * s - 0.5 * M_PI;
   red[z * 4 + 0] = c;
@@ -214,13 +280,31 @@ __global__ void k_line_finalize(const LineInst* __restrict__ inst, const double*
   red[z * 4 + 2] = s;
   red[z * 4 + 3] = hm;
   if (done) {
-    if (c <= inst[z].tol && fabs(force) <= inst[z].tol) {
+    const double tol = inst[z].tol;
+    if (c <= tol && fabs(force) <= tol) {
       done[z] = 1;
-    } else if (!(c == c) || !(force == force)) {
-      done[z] = 2;  // non-finite: stop this instance
-    } else if (iters) {
-      iters[z] += 1;
+      return;
     }
+    if (!(c == c) || !(force == force)) {
+      done[z] = 2;  // non-finite: stop this instance
+      return;
+    }
+    // Rounding-floor stop: the residual has not halved for five outer
+    // iterations and lies within 1e3 roundoff units of the largest term of R.
+    if (best && stall) {
+      if (c < 0.5 * best[z]) {
+        best[z] = c;
+        stall[z] = 0;
+      } else {
+        stall[z] += 1;
+      }
+      const double floor_r = 1e3 * DBL_EPSILON * tm;
+      if (stall[z] >= 5 && c <= fmax(tol, floor_r) && fabs(force) <= tol) {
+        done[z] = 1;
+        return;
+      }
+    }
+    if (iters) iters[z] += 1;
   }
 }
 
@@ -474,11 +558,15 @@ cudaError_t line_deform(LineCtx* c, const double* V, int vstride, const int* ski
 // film + lubricant state + faces + residual + reductions at (P, H0)
 cudaError_t line_state(LineCtx* c, const double* P, const double* H0, const double* rough, const int* skip,
                        int* iters_done_flag_mode) {
-  cudaError_t e = line_deform(c, P, c->N, skip);
+  dim3 g((c->N + kDefTI - 1) / kDefTI, c->ksplit, c->n_inst);
+  k_line_deform64<<<g, kDefTI, 0, c->st>>>(c->inst, c->gtab64, P, c->N, skip, reinterpret_cast<double*>(c->partial),
+                                           c->n_inst, c->N);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
   k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->partial, c->ksplit, H0, rough, c->N, skip, c->H,
-                                             c->n_inst, c->N, 0);
+                                             c->n_inst, c->N, 0, 1);
   note_launch();
   k_line_nodes<<<gn, kNodeBlock, 0, c->st>>>(c->inst, P, c->H, skip, c->rho, c->drho, c->deta_rel, c->eps, c->u,
                                               c->N);
@@ -492,8 +580,8 @@ cudaError_t line_state(LineCtx* c, const double* P, const double* H0, const doub
 }
 
 cudaError_t line_finalize(LineCtx* c, int* done, int* iters) {
-  k_line_finalize<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(c->inst, c->blk, c->nblk, c->red, done, iters,
-                                                               c->n_inst);
+  k_line_finalize<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(
+      c->inst, c->blk, c->nblk, c->red, done, iters, done ? c->best : nullptr, done ? c->stall : nullptr, c->n_inst);
   note_launch();
   return cudaGetLastError();
 }
@@ -517,6 +605,45 @@ cudaError_t line_start(LineCtx* c, double* P, double* H0, const double* rough) {
   e = line_state(c, P, H0, rough, nullptr, nullptr);
   if (e != cudaSuccess) return e;
   k_line_set_h0<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(c->inst, c->blk, c->nblk, H0, c->n_inst);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ grid sequence
+__global__ void k_line_inject(const double* __restrict__ src, int Nf, double* __restrict__ dst, int Nc, int stride) {
+  const int z = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < Nc) dst[(size_t)z * Nc + i] = src[(size_t)z * Nf + (size_t)i * stride];
+}
+
+cudaError_t line_inject(const double* src, int Nf, double* dst, int Nc, int n_inst, cudaStream_t st) {
+  if (Nc < 2 || (Nf - 1) % (Nc - 1) != 0) return cudaErrorInvalidValue;
+  dim3 g((Nc + 255) / 256, n_inst);
+  k_line_inject<<<g, 256, 0, st>>>(src, Nf, dst, Nc, (Nf - 1) / (Nc - 1));
+  note_launch();
+  return cudaGetLastError();
+}
+
+// fine node 2i = coarse node i; fine node 2i+1 = mean of coarse nodes i, i+1
+__global__ void k_line_prolong(const double* __restrict__ Pc, const double* __restrict__ H0c,
+                               const int* __restrict__ cdone, int Nc, double* __restrict__ Pf,
+                               double* __restrict__ H0f) {
+  const int z = blockIdx.y;
+  if (cdone && cdone[z] == 2) return;
+  const int Nf = 2 * Nc - 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Nf) return;
+  const double* pc = Pc + (size_t)z * Nc;
+  const int i = j >> 1;
+  Pf[(size_t)z * Nf + j] = (j & 1) ? 0.5 * (pc[i] + pc[i + 1]) : pc[i];
+  if (j == 0) H0f[z] = H0c[z];
+}
+
+cudaError_t line_prolong(const double* Pc, const double* H0c, const int* cdone, int Nc, double* Pf, double* H0f,
+                         int n_inst, cudaStream_t st) {
+  const int Nf = 2 * Nc - 1;
+  dim3 g((Nf + 255) / 256, n_inst);
+  k_line_prolong<<<g, 256, 0, st>>>(Pc, H0c, cdone, Nc, Pf, H0f);
   note_launch();
   return cudaGetLastError();
 }
@@ -563,14 +690,14 @@ namespace ehl {
 cudaError_t line_film_dir(LineCtx* c, const double* zh0, const int* skip) {
   dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
   k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->partial, c->ksplit, zh0, nullptr, c->N, skip, c->dH,
-                                             c->n_inst, c->N, 1);
+                                             c->n_inst, c->N, 1, 0);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t line_init_tables(LineCtx* c) {
   dim3 g((c->N + 255) / 256, c->n_inst);
-  k_line_gtab<<<g, 256, 0, c->st>>>(c->inst, c->gtab, c->N);
+  k_line_gtab<<<g, 256, 0, c->st>>>(c->inst, c->gtab, c->gtab64, c->N);
   note_launch();
   return cudaGetLastError();
 }

@@ -15,7 +15,8 @@ struct LineCtx {
   cudaStream_t st = nullptr;
   std::vector<LineInst> h_inst;
   LineInst* inst = nullptr;
-  float2* gtab = nullptr;
+  float2* gtab = nullptr;    // K_d / pi as double-float (Krylov products)
+  double* gtab64 = nullptr;  // K_d / pi in float64 (the residual)
   int ksplit = 1, nblk = 1;
   float2* partial = nullptr;
   double *H = nullptr, *rho = nullptr, *drho = nullptr, *deta_rel = nullptr, *eps = nullptr, *u = nullptr;
@@ -28,9 +29,13 @@ struct LineCtx {
   int* pq_info = nullptr;
   double *Pw = nullptr, *H0w = nullptr, *dH = nullptr;
   int *done = nullptr, *iters = nullptr;
+  double* best = nullptr;  // smallest ||min(P,R)||_inf seen (stall test of the rounding-floor stop)
+  int* stall = nullptr;    // outer iterations since it last halved
   std::vector<void*> allocs;
   // Newton-Krylov buffers (line_newton.cu)
   void* nk = nullptr;
+  // EHL_TRACE=k in the environment: one line per Newton step for the first k instances (stderr)
+  int trace = 0;
 };
 
 cudaError_t ctx_alloc(LineCtx* c, void** p, size_t bytes);
@@ -48,6 +53,12 @@ cudaError_t line_film_dir(LineCtx* c, const double* zh0, const int* skip);
 // (dR/dP) v + (dR/dH0) v_h0 at (P, H0); v nodal (zero at the boundary nodes)
 cudaError_t line_jacobian_apply(LineCtx* c, const double* P, const double* H0, const double* rough, const double* v,
                                 const double* v_h0, double* out);
+// Grid sequence: dst[z][i] = src[z][i * (Nf - 1) / (Nc - 1)] (coarse values of a fine nodal array)
+cudaError_t line_inject(const double* src, int Nf, double* dst, int Nc, int n_inst, cudaStream_t st);
+// Linear prolongation of (P, H0) from a grid of Nc nodes to one of 2 Nc - 1; instances with
+// cdone = 2 (non-finite on the coarse grid) keep their fine values.
+cudaError_t line_prolong(const double* Pc, const double* H0c, const int* cdone, int Nc, double* Pf, double* H0f,
+                         int n_inst, cudaStream_t st);
 // Newton-Krylov method (line_newton.cu)
 cudaError_t line_nk_alloc(LineCtx* c);
 void line_nk_free(LineCtx* c);

@@ -1,8 +1,10 @@
 // line_api.cu -- extern "C" context API of include/ehl.h for line contact.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include <thread>
 #include <vector>
 
 #include "ehl_internal.h"
@@ -10,10 +12,53 @@
 
 using namespace ehl;
 
-struct ehl_ctx {
-  int dim;
-  LineCtx line;
+// A context holds one bucket (an internal LineCtx on its own stream) per
+// distinct grid size.  Caller arrays are [n_inst][nx_max] (rows padded to the
+// largest grid); each bucket works on compact [n_b][N_b] copies, gathered from
+// and scattered back to the caller's rows.  When every instance has the same
+// grid the single bucket works on the caller's arrays directly.
+struct Bucket {
+  LineCtx c;
+  std::vector<LineCtx*> lv;  // coarse grids of the nested iteration, coarsest first
+  std::vector<double*> lrough;  // roughness injected on each coarse grid
+  std::vector<int> idx;      // caller instance of each bucket instance
+  int* d_idx = nullptr;      // the same on the device
+  double *Pb = nullptr, *H0b = nullptr, *rb = nullptr, *vb = nullptr, *vhb = nullptr, *ob = nullptr;
+  cudaEvent_t ev = nullptr;  // completion of the bucket's work on its stream
+  bool own_stream = false;
 };
+
+struct ehl_ctx {
+  int dim = 1;
+  int n_inst = 0, nx_max = 0, beta = 0;
+  bool direct = true;  // single bucket in caller order: no gather/scatter
+  cudaStream_t st = nullptr;
+  std::vector<Bucket*> buckets;
+};
+
+// dst[r][0:len] = src[idx[r]][0:len]  (gather, forward) or the reverse (scatter)
+template <typename T>
+__global__ void k_rows(const T* __restrict__ src, int sstride, T* __restrict__ dst, int dstride,
+                       const int* __restrict__ idx, int rows, int len, int scatter) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    if (!scatter)
+      dst[(size_t)r * dstride + i] = src[(size_t)idx[r] * sstride + i];
+    else
+      dst[(size_t)idx[r] * dstride + i] = src[(size_t)r * sstride + i];
+  }
+}
+
+template <typename T>
+static cudaError_t rows(cudaStream_t st, const T* src, int sstride, T* dst, int dstride, const int* idx,
+                        int nrows, int len, bool scatter) {
+  if (nrows <= 0 || len <= 0) return cudaSuccess;
+  dim3 g((len + 255) / 256, nrows < 65535 ? nrows : 65535);
+  k_rows<T><<<g, 256, 0, st>>>(src, sstride, dst, dstride, idx, nrows, len, scatter ? 1 : 0);
+  note_launch();
+  return cudaGetLastError();
+}
 
 extern "C" void ehl_params_default(ehl_params* p, int dim) {
   if (!p) return;
@@ -43,6 +88,9 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   p->max_iter = 200;
   p->krylov_dim = 40;
   p->h_init = 0.05;
+  p->levels = -1;
+  p->coarse_min_nodes = 65;
+  p->coarse_tol = 1e-6;
 }
 
 static bool params_ok(const ehl_params& p) {
@@ -50,7 +98,7 @@ static bool params_ok(const ehl_params& p) {
          p.L >= 0.0 && p.xb > p.xa && p.alpha > 0.0 && p.p0 > 0.0 && p.z > 0.0 && (p.limiter == 0 || p.limiter == 1) &&
          (p.method == 0 || p.method == 1) && p.max_iter >= 1 && p.krylov_dim >= 1 && p.krylov_dim <= 200 &&
          p.tol > 0.0 && isfinite(p.h_init) && isfinite(p.c_h0) && isfinite(p.omega) && isfinite(p.dist_weight) &&
-         isfinite(p.switch_eps_h);
+         isfinite(p.switch_eps_h) && p.levels >= -1 && p.coarse_min_nodes >= 5 && p.coarse_tol > 0.0;
 }
 
 static LineInst make_inst(const ehl_params& p) {
@@ -84,29 +132,38 @@ static void free_all(LineCtx* c) {
   if (c->nk) line_nk_free(c);
 }
 
-extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_params* per_inst, void* stream,
-                                 ehl_ctx** out) {
-  if (!p || !out || n_inst < 1 || n_inst > (1 << 20) || !params_ok(*p)) return EHL_EINVAL;
-  if (per_inst) {
-    for (int k = 0; k < n_inst; ++k) {
-      const ehl_params& q = per_inst[k];
-      if (!params_ok(q) || q.nx != p->nx || q.dim != p->dim || q.halfband != p->halfband || q.method != p->method)
-        return EHL_EINVAL;
-    }
+static void free_bucket(Bucket* b) {
+  if (!b) return;
+  if (b->c.st) cudaStreamSynchronize(b->c.st);
+  for (LineCtx* l : b->lv) {
+    free_all(l);
+    delete l;
   }
-  ehl_ctx* ctx = new ehl_ctx();
-  ctx->dim = p->dim;
-  LineCtx* c = &ctx->line;
+  b->lv.clear();
+  free_all(&b->c);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->own_stream && b->c.st) cudaStreamDestroy(b->c.st);
+  delete b;
+}
+
+static void free_ctx(ehl_ctx* ctx) {
+  for (Bucket* b : ctx->buckets) free_bucket(b);
+  ctx->buckets.clear();
+  delete ctx;
+}
+
+// Workspace and tables of one LineCtx for the given instances (all on grid N).
+static ehl_status init_line(LineCtx* c, const std::vector<LineInst>& insts, int N, const ehl_params& p) {
+  const int n_inst = (int)insts.size();
+  if (const char* tr = getenv("EHL_TRACE")) c->trace = atoi(tr) > 0 ? atoi(tr) : 0;
   c->n_inst = n_inst;
-  c->N = p->nx;
-  c->n = p->nx - 2;
-  c->beta = p->halfband;
-  c->method = p->method;
-  c->max_iter = p->max_iter;
-  c->krylov_dim = p->krylov_dim;
-  c->st = (cudaStream_t)stream;
-  c->h_inst.resize(n_inst);
-  for (int k = 0; k < n_inst; ++k) c->h_inst[k] = make_inst(per_inst ? per_inst[k] : *p);
+  c->N = N;
+  c->n = N - 2;
+  c->beta = p.halfband;
+  c->method = p.method;
+  c->max_iter = p.max_iter;
+  c->krylov_dim = p.krylov_dim;
+  c->h_inst = insts;
   c->ksplit = (c->N + 127) / 128;
   c->nblk = (c->N + 255) / 256;
   const size_t NN = (size_t)n_inst * c->N, nn = (size_t)n_inst * c->n;
@@ -117,6 +174,7 @@ extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_para
   };
   A((void**)&c->inst, sizeof(LineInst) * n_inst);
   A((void**)&c->gtab, sizeof(float2) * NN);
+  A((void**)&c->gtab64, sizeof(double) * NN);
   A((void**)&c->partial, sizeof(float2) * NN * c->ksplit);
   double** nodal[] = {&c->H, &c->rho, &c->drho, &c->deta_rel, &c->eps, &c->u, &c->F, &c->psi, &c->psia, &c->psib,
                       &c->R, &c->Pw, &c->dH};
@@ -132,6 +190,8 @@ extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_para
   A((void**)&c->H0w, sizeof(double) * n_inst);
   A((void**)&c->done, sizeof(int) * n_inst);
   A((void**)&c->iters, sizeof(int) * n_inst);
+  A((void**)&c->best, sizeof(double) * n_inst);
+  A((void**)&c->stall, sizeof(int) * n_inst);
   A((void**)&c->pq_info, sizeof(int) * n_inst);
   if (ok) {
     size_t wb = 0;
@@ -142,19 +202,146 @@ extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_para
   if (ok && c->method == 1 && line_nk_alloc(c) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();
-    free_all(c);
-    delete ctx;
     return EHL_ENOMEM;
   }
   cudaError_t e = cudaMemcpyAsync(c->inst, c->h_inst.data(), sizeof(LineInst) * n_inst, cudaMemcpyHostToDevice,
                                   c->st);
   if (e == cudaSuccess) e = line_init_tables(c);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return EHL_ECUDA;
+  }
+  return EHL_OK;
+}
+
+// Grids of the nested iteration below N (finest excluded), coarsest first:
+// halve the intervals while their number stays even and the coarse grid
+// keeps at least `min_nodes` nodes, at most `levels` times (-1: no cap).
+static std::vector<int> coarse_grids(int N, int levels, int min_nodes) {
+  std::vector<int> g;
+  int n = N;
+  while ((n - 1) % 2 == 0 && (n - 1) / 2 + 1 >= min_nodes && (levels < 0 || (int)g.size() < levels)) {
+    n = (n - 1) / 2 + 1;
+    g.push_back(n);
+  }
+  return std::vector<int>(g.rbegin(), g.rend());
+}
+
+// One bucket: the finest-grid LineCtx, its coarse grids and the gather buffers.
+static ehl_status init_bucket(Bucket* b, const ehl_params& p0, const std::vector<const ehl_params*>& ps,
+                              bool gather) {
+  const int n_inst = (int)ps.size();
+  std::vector<LineInst> insts(n_inst);
+  for (int k = 0; k < n_inst; ++k) insts[k] = make_inst(*ps[k]);
+  ehl_status st = init_line(&b->c, insts, p0.nx, p0);
+  if (st != EHL_OK) return st;
+  for (int Nl : coarse_grids(p0.nx, p0.levels, p0.coarse_min_nodes)) {
+    LineCtx* l = new LineCtx();
+    l->st = b->c.st;
+    b->lv.push_back(l);
+    std::vector<LineInst> ci(n_inst);
+    for (int k = 0; k < n_inst; ++k) {
+      ehl_params q = *ps[k];
+      q.nx = Nl;
+      q.tol = q.tol > q.coarse_tol ? q.tol : q.coarse_tol;
+      ci[k] = make_inst(q);
+    }
+    st = init_line(l, ci, Nl, p0);
+    if (st != EHL_OK) return st;
+    double* r = nullptr;
+    if (ctx_alloc(l, (void**)&r, sizeof(double) * n_inst * (size_t)Nl) != cudaSuccess) {
+      cudaGetLastError();
+      return EHL_ENOMEM;
+    }
+    b->lrough.push_back(r);
+  }
+  LineCtx* c = &b->c;
+  const size_t NN = (size_t)n_inst * c->N;
+  bool ok = true;
+  auto A = [&](void** ptr, size_t bytes) {
+    if (ok && ctx_alloc(c, ptr, bytes) != cudaSuccess) ok = false;
+  };
+  if (gather) {
+    A((void**)&b->d_idx, sizeof(int) * n_inst);
+    A((void**)&b->Pb, sizeof(double) * NN);
+    A((void**)&b->H0b, sizeof(double) * n_inst);
+    A((void**)&b->rb, sizeof(double) * NN);
+    A((void**)&b->vb, sizeof(double) * NN);
+    A((void**)&b->vhb, sizeof(double) * n_inst);
+    A((void**)&b->ob, sizeof(double) * NN);
+  }
+  if (ok && cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) ok = false;
+  if (!ok) {
+    cudaGetLastError();
+    return EHL_ENOMEM;
+  }
+  cudaError_t e = cudaSuccess;
+  if (gather) e = cudaMemcpyAsync(b->d_idx, b->idx.data(), sizeof(int) * n_inst, cudaMemcpyHostToDevice, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    free_all(c);
-    delete ctx;
     return EHL_ECUDA;
+  }
+  return EHL_OK;
+}
+
+extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_params* per_inst, void* stream,
+                                 ehl_ctx** out) {
+  if (!p || !out || n_inst < 1 || n_inst > 65535 || !params_ok(*p)) return EHL_EINVAL;
+  int nx_max = p->nx;
+  if (per_inst) {
+    for (int k = 0; k < n_inst; ++k) {
+      const ehl_params& q = per_inst[k];
+      if (!params_ok(q) || q.dim != p->dim || q.halfband != p->halfband || q.method != p->method) return EHL_EINVAL;
+      nx_max = q.nx > nx_max ? q.nx : nx_max;
+    }
+  }
+  // buckets by grid size, in order of first appearance
+  std::vector<int> sizes;
+  std::vector<std::vector<int>> members;
+  for (int k = 0; k < n_inst; ++k) {
+    const int nx = per_inst ? per_inst[k].nx : p->nx;
+    size_t q = 0;
+    while (q < sizes.size() && sizes[q] != nx) ++q;
+    if (q == sizes.size()) {
+      sizes.push_back(nx);
+      members.emplace_back();
+    }
+    members[q].push_back(k);
+  }
+  ehl_ctx* ctx = new ehl_ctx();
+  ctx->dim = p->dim;
+  ctx->n_inst = n_inst;
+  ctx->nx_max = nx_max;
+  ctx->beta = p->halfband;
+  ctx->st = (cudaStream_t)stream;
+  ctx->direct = sizes.size() == 1;
+  for (size_t q = 0; q < sizes.size(); ++q) {
+    Bucket* b = new Bucket();
+    ctx->buckets.push_back(b);
+    b->idx = members[q];
+    if (ctx->direct) {
+      b->c.st = ctx->st;
+    } else {
+      if (cudaStreamCreateWithFlags(&b->c.st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(ctx);
+        return EHL_ECUDA;
+      }
+      b->own_stream = true;
+    }
+    std::vector<const ehl_params*> ps;
+    for (int k : b->idx) ps.push_back(per_inst ? &per_inst[k] : p);
+    ehl_params p0 = *ps[0];
+    p0.halfband = p->halfband;
+    p0.method = p->method;
+    p0.levels = p->levels;
+    p0.coarse_min_nodes = p->coarse_min_nodes;
+    const ehl_status st = init_bucket(b, p0, ps, !ctx->direct);
+    if (st != EHL_OK) {
+      free_ctx(ctx);
+      return st;
+    }
   }
   *out = ctx;
   return EHL_OK;
@@ -162,9 +349,8 @@ extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_para
 
 extern "C" ehl_status ehl_destroy(ehl_ctx* ctx) {
   if (!ctx) return EHL_EINVAL;
-  cudaStreamSynchronize(ctx->line.st);
-  free_all(&ctx->line);
-  delete ctx;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  free_ctx(ctx);
   return EHL_OK;
 }
 
@@ -174,56 +360,130 @@ static ehl_status cuda_status(cudaError_t e) {
   return EHL_ECUDA;
 }
 
-// (red [n_inst][4]) -> (comp_res [n_inst][2])
-static cudaError_t copy_comp(LineCtx* c, double* comp_res) {
-  return cudaMemcpy2DAsync(comp_res, 2 * sizeof(double), c->red, 4 * sizeof(double), 2 * sizeof(double), c->n_inst,
-                           cudaMemcpyDeviceToDevice, c->st);
+// bucket streams wait for the caller's stream (fork) and the caller's stream for them (join)
+static cudaError_t fork(ehl_ctx* ctx) {
+  if (ctx->direct) return cudaSuccess;
+  cudaEvent_t e0;
+  cudaError_t e = cudaEventCreateWithFlags(&e0, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->st);
+  for (Bucket* b : ctx->buckets)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->c.st, e0, 0);
+  cudaEventDestroy(e0);
+  return e;
+}
+static cudaError_t join(ehl_ctx* ctx) {
+  if (ctx->direct) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  for (Bucket* b : ctx->buckets) {
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev, b->c.st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->st, b->ev, 0);
+  }
+  return e;
+}
+
+// caller [n_inst][stride] rows -> bucket compact rows (or the caller pointer when direct)
+static const double* gin(ehl_ctx* ctx, Bucket* b, const double* src, int stride, int len, double* buf,
+                         cudaError_t& e) {
+  if (!src) return nullptr;
+  if (ctx->direct) return src;
+  if (e == cudaSuccess) e = rows(b->c.st, src, stride, buf, len, b->d_idx, (int)b->idx.size(), len, false);
+  return buf;
+}
+
+static cudaError_t bucket_state(ehl_ctx* ctx, Bucket* b, const double* P, const double* H0, const double* rough) {
+  LineCtx* c = &b->c;
+  cudaError_t e = cudaSuccess;
+  const double* Pb = gin(ctx, b, P, ctx->nx_max, c->N, b->Pb, e);
+  const double* H0b = gin(ctx, b, H0, 1, 1, b->H0b, e);
+  const double* rb = gin(ctx, b, rough, ctx->nx_max, c->N, b->rb, e);
+  if (e == cudaSuccess) e = line_state(c, Pb, H0b, rb, nullptr, nullptr);
+  if (e == cudaSuccess) e = line_finalize(c, nullptr, nullptr);
+  return e;
+}
+
+// (red [n][4]) -> (comp_res rows of 2)
+static cudaError_t put_comp(ehl_ctx* ctx, Bucket* b, double* comp_res) {
+  LineCtx* c = &b->c;
+  if (ctx->direct)
+    return cudaMemcpy2DAsync(comp_res, 2 * sizeof(double), c->red, 4 * sizeof(double), 2 * sizeof(double),
+                             c->n_inst, cudaMemcpyDeviceToDevice, c->st);
+  return rows(c->st, (const double*)c->red, 4, comp_res, 2, b->d_idx, c->n_inst, 2, true);
+}
+
+template <typename T>
+static cudaError_t put_rows(ehl_ctx* ctx, Bucket* b, const T* src, int len, T* dst, int dstride) {
+  LineCtx* c = &b->c;
+  if (ctx->direct) return cudaMemcpyAsync(dst, src, sizeof(T) * len * c->n_inst, cudaMemcpyDeviceToDevice, c->st);
+  return rows(c->st, src, len, dst, dstride, b->d_idx, c->n_inst, len, true);
 }
 
 extern "C" ehl_status ehl_residual(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, double* R,
                                    double* H, double* comp_res) {
   if (!ctx || !P || !H0 || !R) return EHL_EINVAL;
-  LineCtx* c = &ctx->line;
-  cudaError_t e = line_state(c, P, H0, rough, nullptr, nullptr);
-  if (e == cudaSuccess) e = line_finalize(c, nullptr, nullptr);
-  const size_t NN = (size_t)c->n_inst * c->N;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(R, c->R, sizeof(double) * NN, cudaMemcpyDeviceToDevice, c->st);
-  if (e == cudaSuccess && H) e = cudaMemcpyAsync(H, c->H, sizeof(double) * NN, cudaMemcpyDeviceToDevice, c->st);
-  if (e == cudaSuccess && comp_res) e = copy_comp(c, comp_res);
+  cudaError_t e = fork(ctx);
+  for (Bucket* b : ctx->buckets) {
+    LineCtx* c = &b->c;
+    if (e == cudaSuccess) e = bucket_state(ctx, b, P, H0, rough);
+    if (e == cudaSuccess) e = put_rows(ctx, b, (const double*)c->R, c->N, R, ctx->nx_max);
+    if (e == cudaSuccess && H) e = put_rows(ctx, b, (const double*)c->H, c->N, H, ctx->nx_max);
+    if (e == cudaSuccess && comp_res) e = put_comp(ctx, b, comp_res);
+  }
+  if (e == cudaSuccess) e = join(ctx);
   return cuda_status(e);
 }
 
 extern "C" ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
                                         int kind, double* band, uint8_t* active) {
   if (!ctx || !P || !H0 || !band || !active || (kind != 0 && kind != 1)) return EHL_EINVAL;
-  LineCtx* c = &ctx->line;
-  cudaError_t e = line_state(c, P, H0, rough, nullptr, nullptr);
-  if (e == cudaSuccess) e = line_jac_band(c, P, kind, band, active, nullptr, nullptr, nullptr);
+  const int bw = 2 * ctx->beta + 1, nmax = ctx->nx_max - 2;
+  cudaError_t e = fork(ctx);
+  for (Bucket* b : ctx->buckets) {
+    LineCtx* c = &b->c;
+    if (e == cudaSuccess) e = bucket_state(ctx, b, P, H0, rough);
+    const double* Pb = ctx->direct ? P : b->Pb;
+    double* bo = ctx->direct ? band : c->band;
+    uint8_t* ao = ctx->direct ? active : c->act;
+    if (e == cudaSuccess) e = line_jac_band(c, Pb, kind, bo, ao, nullptr, nullptr, nullptr);
+    if (!ctx->direct) {
+      if (e == cudaSuccess) e = rows(c->st, (const double*)c->band, c->n * bw, band, nmax * bw, b->d_idx, c->n_inst,
+                                     c->n * bw, true);
+      if (e == cudaSuccess) e = rows(c->st, (const uint8_t*)c->act, c->n, active, nmax, b->d_idx, c->n_inst, c->n,
+                                     true);
+    }
+  }
+  if (e == cudaSuccess) e = join(ctx);
   return cuda_status(e);
 }
 
 extern "C" ehl_status ehl_jacobian_apply(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
                                          const double* v, const double* v_h0, double* out) {
   if (!ctx || !P || !H0 || !v || !v_h0 || !out) return EHL_EINVAL;
-  return cuda_status(line_jacobian_apply(&ctx->line, P, H0, rough, v, v_h0, out));
+  cudaError_t e = fork(ctx);
+  for (Bucket* b : ctx->buckets) {
+    LineCtx* c = &b->c;
+    const double* Pb = gin(ctx, b, P, ctx->nx_max, c->N, b->Pb, e);
+    const double* H0b = gin(ctx, b, H0, 1, 1, b->H0b, e);
+    const double* rb = gin(ctx, b, rough, ctx->nx_max, c->N, b->rb, e);
+    const double* vb = gin(ctx, b, v, ctx->nx_max, c->N, b->vb, e);
+    const double* vhb = gin(ctx, b, v_h0, 1, 1, b->vhb, e);
+    double* ob = ctx->direct ? out : b->ob;
+    if (e == cudaSuccess) e = line_jacobian_apply(c, Pb, H0b, rb, vb, vhb, ob);
+    if (e == cudaSuccess && !ctx->direct) e = put_rows(ctx, b, (const double*)b->ob, c->N, out, ctx->nx_max);
+  }
+  if (e == cudaSuccess) e = join(ctx);
+  return cuda_status(e);
 }
 
-extern "C" ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const double* rough, int init, int* iters,
-                                double* final_res) {
-  if (!ctx || !P || !H0 || (init != 0 && init != 1)) return EHL_EINVAL;
-  LineCtx* c = &ctx->line;
-  const size_t NN = (size_t)c->n_inst * c->N;
-  cudaError_t e = cudaSuccess;
-  if (init == 1) {
-    e = cudaMemcpyAsync(c->Pw, P, sizeof(double) * NN, cudaMemcpyDeviceToDevice, c->st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(c->H0w, H0, sizeof(double) * c->n_inst, cudaMemcpyDeviceToDevice, c->st);
-  } else {
-    e = line_start(c, c->Pw, c->H0w, rough);
-  }
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->done, 0, sizeof(int) * c->n_inst, c->st);
+// Outer iterations of one LineCtx from (c->Pw, c->H0w) until every instance is
+// done or max_iter; ends with the residual at the returned iterate and the
+// done flags in hdone.
+static cudaError_t iterate(LineCtx* c, const double* rough, std::vector<int>& hdone) {
+  cudaError_t e = cudaMemsetAsync(c->done, 0, sizeof(int) * c->n_inst, c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->iters, 0, sizeof(int) * c->n_inst, c->st);
-  std::vector<int> hdone(c->n_inst, 0);
+  // bytes 0x7f: best = 1.4e306 (no residual seen yet)
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->best, 0x7f, sizeof(double) * c->n_inst, c->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->stall, 0, sizeof(int) * c->n_inst, c->st);
+  hdone.assign(c->n_inst, 0);
   const int check_every = 8;
   for (int it = 0; it < c->max_iter && e == cudaSuccess; ++it) {
     e = (c->method == 0) ? line_paper_iteration(c, c->Pw, c->H0w, rough) : line_nk_step(c, c->Pw, c->H0w, rough);
@@ -236,21 +496,92 @@ extern "C" ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const doubl
       if (all) break;
     }
   }
-  // final residual at the returned iterate
   if (e == cudaSuccess) e = line_state(c, c->Pw, c->H0w, rough, nullptr, nullptr);
   if (e == cudaSuccess) e = line_finalize(c, nullptr, nullptr);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(P, c->Pw, sizeof(double) * NN, cudaMemcpyDeviceToDevice, c->st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(H0, c->H0w, sizeof(double) * c->n_inst, cudaMemcpyDeviceToDevice, c->st);
-  if (e == cudaSuccess && iters)
-    e = cudaMemcpyAsync(iters, c->iters, sizeof(int) * c->n_inst, cudaMemcpyDeviceToDevice, c->st);
-  if (e == cudaSuccess && final_res) e = copy_comp(c, final_res);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hdone.data(), c->done, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hdone.data(), c->done, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  return e;
+}
+
+// The solve of one bucket on its stream; the result stays in c->Pw, c->H0w.
+// From the Hertzian start with coarse grids: nested iteration, each grid
+// started from the prolonged solution of the one below.
+static cudaError_t solve_bucket(ehl_ctx* ctx, Bucket* b, const double* P, const double* H0, const double* rough,
+                                int init, std::vector<int>& hdone) {
+  LineCtx* c = &b->c;
+  const size_t NN = (size_t)c->n_inst * c->N;
+  cudaError_t e = cudaSuccess;
+  const double* rb = gin(ctx, b, rough, ctx->nx_max, c->N, b->rb, e);
+  if (init == 1) {
+    const double* Pb = gin(ctx, b, P, ctx->nx_max, c->N, b->Pb, e);
+    const double* H0b = gin(ctx, b, H0, 1, 1, b->H0b, e);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->Pw, Pb, sizeof(double) * NN, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->H0w, H0b, sizeof(double) * c->n_inst, cudaMemcpyDeviceToDevice, c->st);
+  } else {
+    LineCtx* prev = nullptr;
+    std::vector<int> hd;
+    for (size_t l = 0; l < b->lv.size() && e == cudaSuccess; ++l) {
+      LineCtx* cl = b->lv[l];
+      const double* rl = nullptr;
+      if (rb) {
+        e = line_inject(rb, c->N, b->lrough[l], cl->N, cl->n_inst, cl->st);
+        rl = b->lrough[l];
+      }
+      if (e == cudaSuccess) e = line_start(cl, cl->Pw, cl->H0w, rl);
+      if (e == cudaSuccess && prev)
+        e = line_prolong(prev->Pw, prev->H0w, prev->done, prev->N, cl->Pw, cl->H0w, cl->n_inst, cl->st);
+      if (e == cudaSuccess) e = iterate(cl, rl, hd);
+      prev = cl;
+    }
+    if (e == cudaSuccess) e = line_start(c, c->Pw, c->H0w, rb);
+    if (e == cudaSuccess && prev)
+      e = line_prolong(prev->Pw, prev->H0w, prev->done, prev->N, c->Pw, c->H0w, c->n_inst, c->st);
+  }
+  if (e == cudaSuccess) e = iterate(c, rb, hdone);
+  return e;
+}
+
+extern "C" ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const double* rough, int init, int* iters,
+                                double* final_res) {
+  if (!ctx || !P || !H0 || (init != 0 && init != 1)) return EHL_EINVAL;
+  cudaError_t e = fork(ctx);
+  if (e != cudaSuccess) return cuda_status(e);
+  const size_t nb = ctx->buckets.size();
+  std::vector<cudaError_t> errs(nb, cudaSuccess);
+  std::vector<std::vector<int>> dones(nb);
+  if (nb == 1) {
+    errs[0] = solve_bucket(ctx, ctx->buckets[0], P, H0, rough, init, dones[0]);
+  } else {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<std::thread> th;
+    for (size_t q = 0; q < nb; ++q)
+      th.emplace_back([&, q, dev]() {
+        cudaSetDevice(dev);
+        errs[q] = solve_bucket(ctx, ctx->buckets[q], P, H0, rough, init, dones[q]);
+      });
+    for (auto& t : th) t.join();
+  }
+  for (size_t q = 0; q < nb; ++q) {
+    Bucket* b = ctx->buckets[q];
+    LineCtx* c = &b->c;
+    if (errs[q] != cudaSuccess) e = errs[q];
+    if (e != cudaSuccess) break;
+    e = put_rows(ctx, b, (const double*)c->Pw, c->N, P, ctx->nx_max);
+    if (e == cudaSuccess) e = put_rows(ctx, b, (const double*)c->H0w, 1, H0, 1);
+    if (e == cudaSuccess && iters) e = put_rows(ctx, b, (const int*)c->iters, 1, iters, 1);
+    if (e == cudaSuccess && final_res) e = put_comp(ctx, b, final_res);
+  }
+  if (e == cudaSuccess) e = join(ctx);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
   if (e != cudaSuccess) return cuda_status(e);
   bool nonfinite = false, noconv = false;
-  for (int v : hdone) {
-    nonfinite = nonfinite || v == 2;
-    noconv = noconv || v == 0;
-  }
+  for (auto& hd : dones)
+    for (int v : hd) {
+      nonfinite = nonfinite || v == 2;
+      noconv = noconv || v == 0;
+    }
   return nonfinite ? EHL_ENONFINITE : (noconv ? EHL_ENOCONV : EHL_OK);
 }

@@ -14,6 +14,7 @@
 // with the dR/dH0 column and the force row (one extra PAQIF solve per step
 // for the border), followed by a backtracking line search on ||Phi||_2.
 #include <cuda_runtime.h>
+#include <stdio.h>
 #include <math.h>
 
 #include <vector>
@@ -32,6 +33,7 @@ struct NkBuf {
   double *Pt = nullptr, *H0t = nullptr, *tstep = nullptr, *rtol = nullptr, *beta0 = nullptr;
   double *znode = nullptr, *zh0 = nullptr, *w = nullptr;
   int *gm_k = nullptr, *gm_conv = nullptr, *lsdone = nullptr, *skip = nullptr;
+  int* lsphase = nullptr;  // line search: 0 projected trials (P_t >= 0), 1 unprojected
   void* fstore = nullptr;  // PAQIF factor store of the current preconditioner
 };
 
@@ -290,10 +292,11 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_update(const LineInst* __restri
   if (threadIdx.x == 0) {
     b.tstep[z] = 1.0;
     b.lsdone[z] = 0;
+    b.lsphase[z] = 0;
   }
 }
 
-// trial point P_t = max(0, P + t dP), H0_t = H0 + t dH0
+// trial point P_t = P + t dP, projected on P_t >= 0 in the first phase; H0_t = H0 + t dH0
 __global__ void k_nk_trial(NkBuf b, const double* __restrict__ P, const double* __restrict__ H0,
                            const int* __restrict__ skip, int N) {
   const int z = blockIdx.y;
@@ -305,13 +308,18 @@ __global__ void k_nk_trial(NkBuf b, const double* __restrict__ P, const double* 
   double v = 0.0;
   if (i >= 1 && i <= N - 2) {
     v = P[(size_t)z * N + i] + t * b.delta[(size_t)z * n1 + (i - 1)];
-    v = v > 0.0 ? v : 0.0;
+    if (b.lsphase[z] == 0) v = v > 0.0 ? v : 0.0;
   }
   b.Pt[(size_t)z * N + i] = v;
   if (i == 0) b.H0t[z] = H0[z] + t * b.delta[(size_t)z * n1 + (N - 2)];
 }
 
-// merit of the trial point; accept (copy into P, H0) or halve the step
+// Merit of the trial point; accept (copy into P, H0) or shorten the step.
+// Backtracking on ||Phi||_2 with sufficient decrease 1e-4 t.  Projected
+// trials run down to t = 2^-10; the projection max(0, .) can destroy the
+// descent of the Newton direction where the step drives many pressures below
+// zero, so the search then restarts at t = 1 without it (Phi = min(P, R/d) is
+// defined for P < 0) and accepts its last trial once t < 1e-10.
 __global__ void __launch_bounds__(kNkBlock) k_nk_merit(const LineInst* __restrict__ inst, NkBuf b,
                                                        const double* __restrict__ R, const double* __restrict__ red,
                                                        const double* __restrict__ dg, const int* __restrict__ skip,
@@ -335,7 +343,9 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_merit(const LineInst* __restric
   const double f = red[z * 4 + 1];
   const double nrm = sqrt(ss + f * f);
   const double t = b.tstep[z];
-  if (threadIdx.x == 0) accept = (!nf && nrm == nrm && nrm <= (1.0 - 1e-4 * t) * b.phinorm[z]) || t < 1e-10;
+  const int phase = b.lsphase[z];
+  if (threadIdx.x == 0)
+    accept = (!nf && nrm == nrm && nrm <= (1.0 - 1e-4 * t) * b.phinorm[z]) || (phase == 1 && t < 1e-10);
   __syncthreads();
   if (accept) {
     for (int i = threadIdx.x; i < N; i += kNkBlock) P[(size_t)z * N + i] = b.Pt[(size_t)z * N + i];
@@ -344,7 +354,12 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_merit(const LineInst* __restric
       b.lsdone[z] = 1;
     }
   } else if (threadIdx.x == 0) {
-    b.tstep[z] = 0.5 * t;
+    if (phase == 0 && 0.5 * t < 0x1p-10) {
+      b.lsphase[z] = 1;
+      b.tstep[z] = 1.0;
+    } else {
+      b.tstep[z] = 0.5 * t;
+    }
   }
 }
 
@@ -399,6 +414,7 @@ cudaError_t line_nk_alloc(LineCtx* c) {
             {(void**)&b->gm_k, sizeof(int) * ni},
             {(void**)&b->gm_conv, sizeof(int) * ni},
             {(void**)&b->lsdone, sizeof(int) * ni},
+            {(void**)&b->lsphase, sizeof(int) * ni},
             {(void**)&b->skip, sizeof(int) * ni},
             {(void**)&b->fstore, paqif_factor_store_bytes(ni, c->n, c->beta)}};
   for (auto& x : al) {
@@ -479,7 +495,23 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
   }
   k_nk_update<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->done, N);
   note_launch();
-  for (int trial = 0; trial < 40; ++trial) {
+  std::vector<int> tk, tc;
+  std::vector<double> tphin, trtol;
+  if (c->trace) {
+    const int nt = c->trace < ni ? c->trace : ni;
+    tk.resize(nt);
+    tc.resize(nt);
+    tphin.resize(nt);
+    trtol.resize(nt);
+    e = cudaMemcpyAsync(tk.data(), b.gm_k, sizeof(int) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tc.data(), b.gm_conv, sizeof(int) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tphin.data(), b.phinorm, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(trtol.data(), b.rtol, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e != cudaSuccess) return e;
+  }
+  for (int trial = 0; trial < 64; ++trial) {
     k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.lsdone, b.skip, ni);
     note_launch();
     k_nk_trial<<<gn, 256, 0, c->st>>>(b, P, H0, b.skip, N);
@@ -491,6 +523,21 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
     note_launch();
     if (all_set(c, c->done, b.lsdone, e)) break;
     if (e != cudaSuccess) return e;
+  }
+  if (c->trace) {
+    const int nt = (int)tk.size();
+    std::vector<double> tt(nt), tred(4 * nt);
+    std::vector<int> tph(nt), tdone(nt), tit(nt);
+    e = cudaMemcpyAsync(tt.data(), b.tstep, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tph.data(), b.lsphase, sizeof(int) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tdone.data(), c->done, sizeof(int) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tit.data(), c->iters, sizeof(int) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return e;
+    for (int z = 0; z < nt; ++z)
+      if (!tdone[z])
+        fprintf(stderr, "ehl nk N=%d inst %d it %d |Phi| %.3e rtol %.1e gmres %d conv %d t %.3e phase %d\n", N, z,
+                tit[z], tphin[z], trtol[z], tk[z], tc[z], tt[z], tph[z]);
   }
   return cudaGetLastError();
 }

@@ -87,14 +87,21 @@ def default_params(dim=1, **overrides):
 
 
 class Context:
-    """An ``ehl_ctx`` for ``n_inst`` instances (device arrays ``[n_inst][nx]``)."""
+    """An ``ehl_ctx`` for ``n_inst`` instances.
+
+    Device arrays are ``[n_inst][nx_max]``, ``nx_max`` the largest grid of the
+    batch; instance ``k`` uses the first ``nxs[k]`` entries of its row (a
+    ragged batch when the grids differ).
+    """
 
     def __init__(self, params, n_inst=1, per_inst=None, stream=None):
         lib = _ffi.load()
         self._lib = lib
         self.params = params
         self.n_inst = n_inst
-        self.nx = params.nx
+        self.nxs = [q.nx for q in per_inst] if per_inst is not None else [params.nx] * n_inst
+        self.nx = max([params.nx] + self.nxs)
+        self.ragged = any(v != self.nx for v in self.nxs)
         self.beta = params.halfband
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         arr = None
@@ -120,27 +127,35 @@ class Context:
     def _dev(self):
         return torch.device("cuda", torch.cuda.current_device())
 
+    def _check(self, P, H0, rough=None, v=None, v_h0=None):
+        _check_dev(P, H0, rough, v, v_h0)
+        for t, shape in ((P, (self.n_inst, self.nx)), (H0, (self.n_inst,)), (rough, (self.n_inst, self.nx)),
+                         (v, (self.n_inst, self.nx)), (v_h0, (self.n_inst,))):
+            if t is not None and (tuple(t.shape) != shape or t.dtype != torch.float64):
+                raise ValueError(f"expected a float64 tensor of shape {shape}, got {tuple(t.shape)} {t.dtype}")
+
     def residual(self, P, H0, rough=None):
-        _check_dev(P, H0, rough)
-        R = torch.empty_like(P)
-        H = torch.empty_like(P)
+        self._check(P, H0, rough)
+        R = torch.zeros_like(P) if self.ragged else torch.empty_like(P)
+        H = torch.zeros_like(P) if self.ragged else torch.empty_like(P)
         comp = torch.empty((self.n_inst, 2), dtype=torch.float64, device=P.device)
         code = self._lib.ehl_residual(self._h, _ptr(P), _ptr(H0), _ptr(rough), _ptr(R), _ptr(H), _ptr(comp))
         _ffi.check(code, "ehl_residual")
         return R, H, comp
 
     def jacobian_band(self, P, H0, kind=0, rough=None):
-        _check_dev(P, H0, rough)
+        self._check(P, H0, rough)
         n = self.nx - 2
-        band = torch.empty((self.n_inst, n, 2 * self.beta + 1), dtype=torch.float64, device=P.device)
-        act = torch.empty((self.n_inst, n), dtype=torch.uint8, device=P.device)
+        alloc = torch.zeros if self.ragged else torch.empty
+        band = alloc((self.n_inst, n, 2 * self.beta + 1), dtype=torch.float64, device=P.device)
+        act = alloc((self.n_inst, n), dtype=torch.uint8, device=P.device)
         code = self._lib.ehl_jacobian_band(self._h, _ptr(P), _ptr(H0), _ptr(rough), kind, _ptr(band), _ptr(act))
         _ffi.check(code, "ehl_jacobian_band")
         return band, act
 
     def jacobian_apply(self, P, H0, v, v_h0, rough=None):
-        _check_dev(P, H0, v, v_h0, rough)
-        out = torch.empty_like(P)
+        self._check(P, H0, rough, v, v_h0)
+        out = torch.zeros_like(P) if self.ragged else torch.empty_like(P)
         code = self._lib.ehl_jacobian_apply(self._h, _ptr(P), _ptr(H0), _ptr(rough), _ptr(v), _ptr(v_h0), _ptr(out))
         _ffi.check(code, "ehl_jacobian_apply")
         return out
@@ -155,7 +170,7 @@ class Context:
         else:
             P = P.clone()
             H0 = H0.clone()
-        _check_dev(P, H0, rough)
+        self._check(P, H0, rough)
         iters = torch.zeros(self.n_inst, dtype=torch.int32, device=dev)
         res = torch.zeros((self.n_inst, 2), dtype=torch.float64, device=dev)
         code = self._lib.ehl_solve(self._h, _ptr(P), _ptr(H0), _ptr(rough), init, _ptr(iters), _ptr(res))

@@ -60,10 +60,13 @@ def test_params_struct_layout_matches_defaults():
     assert (p.compressible, p.elastic, p.limiter, p.halfband) == (1, 1, 0, 2)
     assert (p.switch_eps_h, p.dist_weight, p.c_h0, p.omega) == (0.6, 0.5, 0.05, 1.0)
     assert (p.method, p.tol, p.max_iter, p.krylov_dim, p.h_init) == (1, 1e-8, 200, 40, 0.05)
+    assert (p.levels, p.coarse_min_nodes, p.coarse_tol) == (-1, 65, 1e-6)
+    assert ctypes.sizeof(p) == _ffi.EhlParams.coarse_tol.offset + 8
 
 
 @pytest.mark.parametrize("field,value", [("nx", 4), ("halfband", 9), ("M", -1.0), ("xb", -5.0), ("method", 7),
-                                         ("limiter", 2), ("krylov_dim", 0)])
+                                         ("limiter", 2), ("krylov_dim", 0), ("levels", -2),
+                                         ("coarse_min_nodes", 4), ("coarse_tol", 0.0)])
 def test_create_rejects_bad_params_on_host(field, value):
     lib = _ffi.load()
     p = _ffi.EhlParams()

@@ -13,22 +13,23 @@ import pytest
 import torch
 
 from oracle import line_ref as lr
-from paper_2008_03276_gb300 import ops
+from paper_2008_03276_gb300 import inputs, ops
 
 pytestmark = pytest.mark.gpu
 
 
-def gpu_solve(N, M, L, limiter, beta, tol, n_inst=1, per=None, max_iter=60, krylov_dim=40):
-    p = ops.default_params(1, nx=N, M=M, L=L, limiter=limiter, halfband=beta, method=1, tol=tol, max_iter=max_iter,
-                           krylov_dim=krylov_dim)
+def gpu_solve(N, M, L, limiter, beta, tol, n_inst=1, per=None, max_iter=60, krylov_dim=40, levels=-1, rough=None):
+    kw = dict(limiter=limiter, halfband=beta, method=1, tol=tol, max_iter=max_iter, krylov_dim=krylov_dim,
+              levels=levels)
+    p = ops.default_params(1, nx=N, M=M, L=L, **kw)
     per_inst = None
     if per is not None:
-        per_inst = [ops.default_params(1, nx=N, limiter=limiter, halfband=beta, method=1, tol=tol, max_iter=max_iter,
-                                       krylov_dim=krylov_dim, **d) for d in per]
+        per_inst = [ops.default_params(1, nx=N, **kw, **d) for d in per]
     ctx = ops.Context(p, n_inst=n_inst, per_inst=per_inst)
+    rd = None if rough is None else torch.tensor(np.asarray(rough, dtype=np.float64).reshape(n_inst, N), device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    P, H0, iters, res, code = ctx.solve(check=False)
+    P, H0, iters, res, code = ctx.solve(rough=rd, check=False)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return P.cpu().numpy(), H0.cpu().numpy(), iters.cpu().numpy(), res.cpu().numpy(), code, dt
@@ -42,13 +43,14 @@ def check(P, H0, pb, Pr, H0r):
     assert np.max(np.abs(H - Hr)) <= 1e-8 * np.max(np.abs(Hr))
 
 
+@pytest.mark.parametrize("levels", [0, -1])
 @pytest.mark.parametrize("beta", [2, 4, 8])
-def test_c1_newton_krylov(beta):
+def test_c1_newton_krylov(beta, levels):
     pb = lr.LineProblem(129, 20.0, 10.0, limiter="minmod")
     Pr, H0r, info = lr.solve(pb)
     assert info["converged"]
-    P, H0, iters, res, code, dt = gpu_solve(129, 20.0, 10.0, 0, beta, tol=1e-11)
-    print(f"beta {beta}: {iters[0]} Newton steps, {dt * 1e3:.1f} ms, res {res[0]}")
+    P, H0, iters, res, code, dt = gpu_solve(129, 20.0, 10.0, 0, beta, tol=1e-11, levels=levels)
+    print(f"beta {beta} levels {levels}: {iters[0]} Newton steps, {dt * 1e3:.1f} ms, res {res[0]}")
     assert code == 0 and iters[0] < 30
     check(P[0], H0[0], pb, Pr, H0r)
 
@@ -75,3 +77,20 @@ def test_batch_of_loads_newton_krylov():
         Pr, H0r, info = lr.solve(pb)
         assert info["converged"]
         check(P[k], H0[k], pb, Pr, H0r)
+
+
+@pytest.mark.parametrize("rough", [False, True])
+def test_nested_iteration_low_load_van_leer(rough):
+    """Low load, strong piezoviscosity, van Leer: Newton from the Hertzian start on the
+    target grid stalls (oracle and GPU alike); the grid sequence 65-129-257 converges."""
+    M, L, N = 10.068856862228834, 19.478471312560632, 257
+    X = np.linspace(-4.5, 1.5, N)
+    rgh = inputs.sin_grf_roughness(X, seed=11, amp=0.02, wavelength=0.4, sigma=0.01) if rough else np.zeros(N)
+    pb, Pr, H0r, info = lr.solve_nested(
+        lambda n: lr.LineProblem(n, M, L, limiter="vanleer", rough=lr.inject(rgh, n)), N, tol=1e-11)
+    assert info["converged"], info["levels"]
+    P, H0, iters, res, code, dt = gpu_solve(N, M, L, 1, 8, tol=1e-10, rough=rgh if rough else None)
+    print(f"nested: {iters[0]} Newton steps on the target grid, {dt * 1e3:.1f} ms, res {res[0]}; "
+          f"oracle levels {info['levels']}")
+    assert code == 0 and iters[0] < 20
+    check(P[0], H0[0], pb, Pr, H0r)

@@ -249,3 +249,53 @@ def test_grid_convergence_order():
     # the pressure spike and the limiter's first-order switch at extrema hold
     # the observed order near 1 (0.9 and 0.6 measured); it must stay positive
     assert 0.3 < p2a < 3.5 and 0.3 < p2b < 3.5
+
+
+# ------------------------------------------------------ nested iteration (grid sequence)
+def test_grid_sequence_rule():
+    assert lr.grid_sequence(1025) == [65, 129, 257, 513, 1025]
+    assert lr.grid_sequence(1025, levels=2) == [257, 513, 1025]
+    assert lr.grid_sequence(1025, levels=0) == [1025]
+    assert lr.grid_sequence(129, n_min=33) == [33, 65, 129]
+    assert lr.grid_sequence(100) == [100]           # odd number of intervals: no coarser grid
+    assert lr.grid_sequence(193) == [97, 193]       # 96 intervals -> 48 -> (25 nodes < 65) stop
+
+
+def test_prolongation_and_injection():
+    # linear interpolation reproduces linear functions exactly and a quadratic
+    # with the interpolation error h^2 f''/8 at the new nodes
+    xc = np.linspace(-4.5, 1.5, 65)
+    xf = np.linspace(-4.5, 1.5, 129)
+    assert np.allclose(lr.prolong(3.0 * xc - 1.0), 3.0 * xf - 1.0, rtol=0, atol=1e-14)
+    h = xc[1] - xc[0]
+    err = lr.prolong(xc ** 2) - xf ** 2
+    assert np.allclose(err[0::2], 0.0, atol=1e-14)
+    assert np.allclose(err[1::2], h ** 2 / 4.0, rtol=1e-12)   # (h/2)^2 for f = x^2
+    v = np.random.default_rng(0).standard_normal(65)
+    assert np.array_equal(lr.inject(lr.prolong(v), 65), v)
+    assert np.array_equal(lr.inject(np.arange(257.0), 65), np.arange(0.0, 257.0, 4.0))
+
+
+def test_nested_solve_reaches_the_direct_solution(c1_solution):
+    pb, P, H0, _ = c1_solution
+    pbn, Pn, H0n, info = lr.solve_nested(lambda n: lr.LineProblem(n, pb.M, pb.L), pb.N, tol=1e-12)
+    assert [l[0] for l in info["levels"]] == lr.grid_sequence(pb.N)
+    assert all(l[2] for l in info["levels"])
+    assert np.max(np.abs(Pn - P)) <= 1e-9 * np.max(P)
+    assert abs(H0n - H0) <= 1e-9 * abs(H0)
+
+
+def test_nested_solve_where_the_hertzian_start_fails():
+    # low load, strongly piezoviscous, van Leer: Newton from the Hertzian start on
+    # the target grid stalls; the grid sequence converges, and the result
+    # satisfies complementarity and the force balance on the target grid
+    M, L, N = 10.068856862228834, 19.478471312560632, 257
+    pb = lr.LineProblem(N, M, L, limiter="vanleer")
+    _, _, direct = lr.solve(pb, max_iter=40)
+    assert not direct["converged"]
+    pbn, P, H0, info = lr.solve_nested(lambda n: lr.LineProblem(n, M, L, limiter="vanleer"), N, tol=1e-10)
+    assert info["converged"] and all(l[2] for l in info["levels"])
+    R = lr.residual(pbn, P, H0)
+    assert np.min(P) >= -1e-10 and np.min(R) >= -1e-10 * max(1.0, np.max(np.abs(R)))
+    assert np.max(np.abs(np.minimum(P, R))) <= 1e-10
+    assert abs(pbn.h * np.sum(P) - np.pi / 2) <= 1e-10
