@@ -46,7 +46,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one full-size paqif3_kernel<4> launch from the ncu
 # capture summarised in profiles/, valid only for the kernel sources with these
 # sha256 prefixes; any other source reports traffic = null.
-PAQIF_TRAFFIC = {}
+PAQIF_TRAFFIC = {("03fe5598e85142b3", "4addd33d7cfa0c6e"): 601213440 + 328103680}
 
 
 def paqif_traffic():

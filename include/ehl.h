@@ -156,7 +156,7 @@ typedef struct {
   int levels;           /* nested iteration: coarse grids solved first (init = 0 only);  */
                         /*   -1 as many as allowed (default), 0 none                     */
   int coarse_min_nodes; /* coarsest grid keeps at least this many nodes (65)             */
-  double coarse_tol;    /* tolerance of the coarse-grid solves, max(tol, coarse_tol) (1e-6) */
+  double coarse_tol;    /* tolerance of the coarse-grid solves, max(tol, coarse_tol) (1e-4) */
 } ehl_params;
 
 /* Fill *p with the defaults above for dimension `dim` (1). */
@@ -229,6 +229,28 @@ ehl_status ehl_jacobian_apply(ehl_ctx* ctx, const double* P, const double* H0, c
  * max_iter, EHL_ENONFINITE if some produced NaN/Inf. */
 ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const double* rough, int init, int* iters,
                      double* final_res);
+
+/* Sensitivities of converged solutions (the paper stops at the solution;
+ * these follow from its discrete problem by the implicit-function theorem).
+ * At a converged (P, H0) -- as ehl_solve returns it -- for an objective
+ * J(P, H, H0) with partial derivatives gP, gH ([n_inst][nx_max], nullable
+ * = 0) and gH0 ([n_inst], nullable), P, H and H0 taken as independent:
+ *   grad_rough [n_inst][nx_max] (nullable)  dJ/d rough at every node,
+ *   grad_ML    [n_inst][2]      (nullable)  (dJ/dM, dJ/dL),
+ *   relres     [n_inst]         (nullable)  relative residual reached by
+ *              the transposed solve.
+ * The rows with P_i > R_i / |dR_i/dP_i| carry the equation R_i = 0, the
+ * others keep P_i = 0; the transposed bordered system of these equations is
+ * solved by GMRES (a basis of max(krylov_dim, 120) vectors, restarted up to
+ * max_cycles times) on the exact
+ * transposed Jacobian, preconditioned by PAQIF on the transposed band, to
+ * the relative residual tol.  H_c, H_min and integrals of P are functions of
+ * (P, H) whose partials the caller supplies (e.g. through autograd).
+ * Synchronises the stream.  Returns EHL_OK, EHL_ENOCONV if some instance
+ * stayed above tol, EHL_ENONFINITE. */
+ehl_status ehl_adjoint(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, const double* gP,
+                       const double* gH, const double* gH0, double* grad_rough, double* grad_ML, double* relres,
+                       double tol, int max_cycles);
 
 /* ------------------------------------------------------------------------
  * PAQIF without any allocation

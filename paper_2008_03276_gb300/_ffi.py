@@ -40,6 +40,7 @@ SYMBOLS = {
     "ehl_create": (ctypes.c_int, [ctypes.POINTER(EhlParams), ctypes.c_int, ctypes.POINTER(EhlParams),
                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "ehl_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "ehl_adjoint": (ctypes.c_int, [ctypes.c_void_p] * 10 + [ctypes.c_double, ctypes.c_int]),
     "ehl_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "ehl_jacobian_band": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

@@ -556,13 +556,17 @@ cudaError_t line_deform(LineCtx* c, const double* V, int vstride, const int* ski
 }
 
 // film + lubricant state + faces + residual + reductions at (P, H0)
+cudaError_t line_deform64(LineCtx* c, const double* V, int vstride, const int* skip) {
+  dim3 g((c->N + kDefTI - 1) / kDefTI, c->ksplit, c->n_inst);
+  k_line_deform64<<<g, kDefTI, 0, c->st>>>(c->inst, c->gtab64, V, vstride, skip,
+                                           reinterpret_cast<double*>(c->partial), c->n_inst, c->N);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t line_state(LineCtx* c, const double* P, const double* H0, const double* rough, const int* skip,
                        int* iters_done_flag_mode) {
-  dim3 g((c->N + kDefTI - 1) / kDefTI, c->ksplit, c->n_inst);
-  k_line_deform64<<<g, kDefTI, 0, c->st>>>(c->inst, c->gtab64, P, c->N, skip, reinterpret_cast<double*>(c->partial),
-                                           c->n_inst, c->N);
-  note_launch();
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = line_deform64(c, P, c->N, skip);
   if (e != cudaSuccess) return e;
   dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
   k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->partial, c->ksplit, H0, rough, c->N, skip, c->H,
@@ -687,10 +691,10 @@ cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double
 }  // namespace ehl
 
 namespace ehl {
-cudaError_t line_film_dir(LineCtx* c, const double* zh0, const int* skip) {
+cudaError_t line_film_dir(LineCtx* c, const double* zh0, const int* skip, bool p64) {
   dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
   k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->partial, c->ksplit, zh0, nullptr, c->N, skip, c->dH,
-                                             c->n_inst, c->N, 1, 0);
+                                             c->n_inst, c->N, 1, p64 ? 1 : 0);
   note_launch();
   return cudaGetLastError();
 }

@@ -34,6 +34,8 @@ struct LineCtx {
   std::vector<void*> allocs;
   // Newton-Krylov buffers (line_newton.cu)
   void* nk = nullptr;
+  // adjoint buffers (line_adjoint.cu), allocated on first use
+  void* adj = nullptr;
   // EHL_TRACE=k in the environment: one line per Newton step for the first k instances (stderr)
   int trace = 0;
 };
@@ -48,8 +50,11 @@ cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, u
 cudaError_t line_start(LineCtx* c, double* P, double* H0, const double* rough);
 cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double* rough);
 cudaError_t line_init_tables(LineCtx* c);
-// dH = -K v + zh0: the film's directional derivative (v in c->partial from line_deform)
-cudaError_t line_film_dir(LineCtx* c, const double* zh0, const int* skip);
+// The same sums in float64 (the residual's deformation; also the adjoint's products)
+cudaError_t line_deform64(LineCtx* c, const double* V, int vstride, const int* skip);
+// dH = -K v + zh0: the film's directional derivative (v in c->partial from line_deform, or
+// from line_deform64 with p64)
+cudaError_t line_film_dir(LineCtx* c, const double* zh0, const int* skip, bool p64 = false);
 // (dR/dP) v + (dR/dH0) v_h0 at (P, H0); v nodal (zero at the boundary nodes)
 cudaError_t line_jacobian_apply(LineCtx* c, const double* P, const double* H0, const double* rough, const double* v,
                                 const double* v_h0, double* out);
@@ -63,5 +68,13 @@ cudaError_t line_prolong(const double* Pc, const double* H0c, const int* cdone, 
 cudaError_t line_nk_alloc(LineCtx* c);
 void line_nk_free(LineCtx* c);
 cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough);
+// Adjoint of a converged state (line_adjoint.cu): gradients of an objective J(P, H, H0) given
+// its partials gP, gH ([n_inst][N], nullable) and gH0 ([n_inst], nullable) with respect to the
+// roughness (grad_rough [n_inst][N], nullable) and the Moes parameters (grad_ML [n_inst][2],
+// nullable); relres [n_inst] (nullable) the relative residual of the transposed solve.
+cudaError_t line_adjoint(LineCtx* c, const double* P, const double* H0, const double* rough, const double* gP,
+                         const double* gH, const double* gH0, double* grad_rough, double* grad_ML, double* relres,
+                         double tol, int max_cycles, int* cycles);
+void line_adj_free(LineCtx* c);
 
 }  // namespace ehl

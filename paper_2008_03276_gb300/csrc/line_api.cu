@@ -24,6 +24,8 @@ struct Bucket {
   std::vector<int> idx;      // caller instance of each bucket instance
   int* d_idx = nullptr;      // the same on the device
   double *Pb = nullptr, *H0b = nullptr, *rb = nullptr, *vb = nullptr, *vhb = nullptr, *ob = nullptr;
+  double *gPb = nullptr, *gHb = nullptr, *gH0b = nullptr, *grb = nullptr, *gmlb = nullptr;  // adjoint I/O
+  double* relw = nullptr;  // adjoint relative residuals [n_b]
   cudaEvent_t ev = nullptr;  // completion of the bucket's work on its stream
   bool own_stream = false;
 };
@@ -90,7 +92,7 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   p->h_init = 0.05;
   p->levels = -1;
   p->coarse_min_nodes = 65;
-  p->coarse_tol = 1e-6;
+  p->coarse_tol = 1e-4;
 }
 
 static bool params_ok(const ehl_params& p) {
@@ -123,6 +125,8 @@ static LineInst make_inst(const ehl_params& p) {
   q.omega = p.omega;
   q.tol = p.tol;
   q.h_init = p.h_init;
+  q.M = p.M;
+  q.L = p.L;
   return q;
 }
 
@@ -130,6 +134,7 @@ static void free_all(LineCtx* c) {
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   if (c->nk) line_nk_free(c);
+  if (c->adj) line_adj_free(c);
 }
 
 static void free_bucket(Bucket* b) {
@@ -269,7 +274,13 @@ static ehl_status init_bucket(Bucket* b, const ehl_params& p0, const std::vector
     A((void**)&b->vb, sizeof(double) * NN);
     A((void**)&b->vhb, sizeof(double) * n_inst);
     A((void**)&b->ob, sizeof(double) * NN);
+    A((void**)&b->gPb, sizeof(double) * NN);
+    A((void**)&b->gHb, sizeof(double) * NN);
+    A((void**)&b->gH0b, sizeof(double) * n_inst);
+    A((void**)&b->grb, sizeof(double) * NN);
+    A((void**)&b->gmlb, sizeof(double) * 2 * n_inst);
   }
+  A((void**)&b->relw, sizeof(double) * n_inst);
   if (ok && cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();
@@ -583,5 +594,45 @@ extern "C" ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const doubl
       nonfinite = nonfinite || v == 2;
       noconv = noconv || v == 0;
     }
+  return nonfinite ? EHL_ENONFINITE : (noconv ? EHL_ENOCONV : EHL_OK);
+}
+
+extern "C" ehl_status ehl_adjoint(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
+                                  const double* gP, const double* gH, const double* gH0, double* grad_rough,
+                                  double* grad_ML, double* relres, double tol, int max_cycles) {
+  if (!ctx || !P || !H0 || !(tol > 0.0) || max_cycles < 1 || max_cycles > 1000) return EHL_EINVAL;
+  cudaError_t e = fork(ctx);
+  for (Bucket* b : ctx->buckets) {
+    LineCtx* c = &b->c;
+    const double* Pb = gin(ctx, b, P, ctx->nx_max, c->N, b->Pb, e);
+    const double* H0b = gin(ctx, b, H0, 1, 1, b->H0b, e);
+    const double* rb = gin(ctx, b, rough, ctx->nx_max, c->N, b->rb, e);
+    const double* gPb = gin(ctx, b, gP, ctx->nx_max, c->N, b->gPb, e);
+    const double* gHb = gin(ctx, b, gH, ctx->nx_max, c->N, b->gHb, e);
+    const double* gH0b = gin(ctx, b, gH0, 1, 1, b->gH0b, e);
+    double* grb = grad_rough ? (ctx->direct ? grad_rough : b->grb) : nullptr;
+    double* gml = grad_ML ? (ctx->direct ? grad_ML : b->gmlb) : nullptr;
+    int cyc = 0;
+    if (e == cudaSuccess)
+      e = line_adjoint(c, Pb, H0b, rb, gPb, gHb, gH0b, grb, gml, b->relw, tol, max_cycles, &cyc);
+    if (!ctx->direct) {
+      if (e == cudaSuccess && grad_rough) e = put_rows(ctx, b, (const double*)b->grb, c->N, grad_rough, ctx->nx_max);
+      if (e == cudaSuccess && grad_ML) e = put_rows(ctx, b, (const double*)b->gmlb, 2, grad_ML, 2);
+    }
+    if (e == cudaSuccess && relres) e = put_rows(ctx, b, (const double*)b->relw, 1, relres, 1);
+  }
+  if (e == cudaSuccess) e = join(ctx);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  if (e != cudaSuccess) return cuda_status(e);
+  bool nonfinite = false, noconv = false;
+  for (Bucket* b : ctx->buckets) {
+    std::vector<double> h(b->c.n_inst);
+    if (cudaMemcpy(h.data(), b->relw, sizeof(double) * h.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cuda_status(cudaGetLastError());
+    for (double v : h) {
+      nonfinite = nonfinite || !(v == v);
+      noconv = noconv || v > tol;
+    }
+  }
   return nonfinite ? EHL_ENONFINITE : (noconv ? EHL_ENOCONV : EHL_OK);
 }

@@ -24,6 +24,7 @@ struct LineInst {
   double xa, h;
   double lam, abar, alpha, p0, z, pH;
   double switch_eps_h, dist_w, c_h0, omega, tol, h_init;
+  double M, L;       // Moes parameters (lam = 3 pi^2/(8 M^2), pH = L sqrt(M/(2 pi))/alpha)
 };
 
 // rho, d rho/dP, ln eta and (d eta/dP)/eta at pressure P (float64).

@@ -98,6 +98,7 @@ class Context:
         lib = _ffi.load()
         self._lib = lib
         self.params = params
+        self.per_inst = per_inst
         self.n_inst = n_inst
         self.nxs = [q.nx for q in per_inst] if per_inst is not None else [params.nx] * n_inst
         self.nx = max([params.nx] + self.nxs)
@@ -177,3 +178,57 @@ class Context:
         if check:
             _ffi.check(code, "ehl_solve")
         return P, H0, iters, res, code
+
+    def adjoint(self, P, H0, gP=None, gH=None, gH0=None, rough=None, tol=1e-10, max_cycles=10, check=True):
+        """Gradients of J(P, H, H0) at a converged state from its partials ``gP``, ``gH``
+        ([n_inst][nx]) and ``gH0`` ([n_inst]): ``(grad_rough [n_inst][nx], grad_ML [n_inst][2],
+        relres [n_inst], code)``."""
+        self._check(P, H0, rough, gP, gH0)
+        self._check(P, H0, gH)
+        grad_rough = torch.zeros_like(P)
+        grad_ML = torch.zeros((self.n_inst, 2), dtype=torch.float64, device=P.device)
+        relres = torch.zeros(self.n_inst, dtype=torch.float64, device=P.device)
+        code = self._lib.ehl_adjoint(self._h, _ptr(P), _ptr(H0), _ptr(rough), _ptr(gP), _ptr(gH), _ptr(gH0),
+                                     _ptr(grad_rough), _ptr(grad_ML), _ptr(relres), float(tol), int(max_cycles))
+        if check:
+            _ffi.check(code, "ehl_adjoint")
+        return grad_rough, grad_ML, relres, code
+
+
+class _SolveFunction(torch.autograd.Function):
+    """Converged ``(P, H, H0)`` as a differentiable function of ``(rough, ML)``."""
+
+    @staticmethod
+    def forward(fctx, ctx, rough, ML, P0, H00, tol, max_cycles):
+        ML_host = ML.detach().cpu().tolist()
+        for k, (M, L) in enumerate(ML_host):
+            q = ctx.per_inst[k] if ctx.per_inst is not None else ctx.params
+            if abs(M - q.M) > 1e-12 * abs(q.M) or abs(L - q.L) > 1e-12 * abs(q.L):
+                raise ValueError("ML must hold the context's (M, L) of every instance")
+        r = rough.detach().contiguous()
+        if P0 is None:
+            P, H0, iters, res, code = ctx.solve(rough=r)
+        else:
+            P, H0, iters, res, code = ctx.solve(P0, H00, rough=r)
+        _, H, _ = ctx.residual(P, H0, r)
+        fctx.ehl = ctx
+        fctx.tol = tol
+        fctx.max_cycles = max_cycles
+        fctx.save_for_backward(P, H0, r)
+        return P, H, H0
+
+    @staticmethod
+    def backward(fctx, gP, gH, gH0):
+        P, H0, r = fctx.saved_tensors
+        ctx = fctx.ehl
+        z = lambda g, t: (g if g is not None else torch.zeros_like(t)).contiguous()
+        grad_rough, grad_ML, relres, code = ctx.adjoint(P, H0, z(gP, P), z(gH, P), z(gH0, H0), rough=r,
+                                                        tol=fctx.tol, max_cycles=fctx.max_cycles)
+        return None, grad_rough, grad_ML, None, None, None, None
+
+
+def solve_differentiable(ctx, rough, ML, P0=None, H00=None, tol=1e-10, max_cycles=10):
+    """Solve through ``ctx`` and return ``(P, H, H0)`` differentiable with respect to the
+    roughness ``rough`` ([n_inst][nx]) and ``ML`` ([n_inst][2], the (M, L) the context was
+    created with); the backward pass is one ``ehl_adjoint`` call."""
+    return _SolveFunction.apply(ctx, rough, ML, P0, H00, tol, max_cycles)

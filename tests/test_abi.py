@@ -60,7 +60,7 @@ def test_params_struct_layout_matches_defaults():
     assert (p.compressible, p.elastic, p.limiter, p.halfband) == (1, 1, 0, 2)
     assert (p.switch_eps_h, p.dist_weight, p.c_h0, p.omega) == (0.6, 0.5, 0.05, 1.0)
     assert (p.method, p.tol, p.max_iter, p.krylov_dim, p.h_init) == (1, 1e-8, 200, 40, 0.05)
-    assert (p.levels, p.coarse_min_nodes, p.coarse_tol) == (-1, 65, 1e-6)
+    assert (p.levels, p.coarse_min_nodes, p.coarse_tol) == (-1, 65, 1e-4)
     assert ctypes.sizeof(p) == _ffi.EhlParams.coarse_tol.offset + 8
 
 
