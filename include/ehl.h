@@ -193,8 +193,10 @@ ehl_status ehl_residual(ehl_ctx* ctx, const double* P, const double* H0, const d
  *          the kernel, the weighted-change distribution on the subregion
  *          eps/h <= switch_eps_h, truncated to the band; cavitated rows
  *          (P = 0, R > 0) are identity rows (active = 1).
- *  kind 1: the band of the exact Jacobian dR/dP; rows with
- *          P_i <= R_i / |dR_i/dP_i| are identity rows (active = 1).
+ *  kind 1: the band of the exact Jacobian dR/dP; rows with P_i <= R_i / d_i
+ *          are identity rows (active = 1), d_i = max(|dR_i/dP_i|, m_i / 10)
+ *          with m_i the largest |entry| of the row's band (the Newton
+ *          row scale; the diagonal alone can pass through zero).
  * Asynchronous. */
 ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, int kind,
                              double* band, uint8_t* active);
@@ -239,7 +241,8 @@ ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const double* rough, i
  *   grad_ML    [n_inst][2]      (nullable)  (dJ/dM, dJ/dL),
  *   relres     [n_inst]         (nullable)  relative residual reached by
  *              the transposed solve.
- * The rows with P_i > R_i / |dR_i/dP_i| carry the equation R_i = 0, the
+ * The rows with P_i > R_i / d_i (d_i as for ehl_jacobian_band kind 1) carry
+ * the equation R_i = 0, the
  * others keep P_i = 0; the transposed bordered system of these equations is
  * solved by GMRES (a basis of max(krylov_dim, 120) vectors, restarted up to
  * max_cycles times) on the exact

@@ -431,15 +431,22 @@ __global__ void k_line_jac_band(const LineInst* __restrict__ inst, LineRowCtx c,
     }
     if (jh) jh[(size_t)z * n + r] = a ? 0.0 : q.JH_frozen(i);
   } else {
-    const double jii = q.J_exact(i, i, ef0, ef1);
-    const double d = fabs(jii) > 0.0 ? fabs(jii) : 1.0;
-    a = Pi <= Ri / d;
+    // row scale d = max(|J_ii|, |J_i|_max / 10) over the band: |J_ii| alone can pass
+    // through zero in the Hertzian zone, where the row is carried by its neighbours
+    double rmax = 0.0, jii = 0.0;
     for (int j = 0; j < bw; ++j) {
       const int col = r - beta + j;
       double v = 0.0;
       if (col >= 0 && col < n) v = q.J_exact(i, col + 1, ef0, ef1);
-      row[j] = a ? (j == beta ? 1.0 : 0.0) : v;
+      row[j] = v;
+      rmax = fmax(rmax, fabs(v));
+      if (j == beta) jii = v;
     }
+    double d = fmax(fabs(jii), 0.1 * rmax);
+    d = d > 0.0 ? d : 1.0;
+    a = Pi <= Ri / d;
+    if (a)
+      for (int j = 0; j < bw; ++j) row[j] = (j == beta ? 1.0 : 0.0);
     if (jh) jh[(size_t)z * n + r] = a ? 0.0 : q.JH_exact(i, ef0, ef1);
     if (dg) dg[(size_t)z * n + r] = d;
   }

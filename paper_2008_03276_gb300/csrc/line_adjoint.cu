@@ -3,7 +3,7 @@
 // At a solution of the discrete problem (Sec. 3.3, Example 6: P >= 0,
 // R >= 0, P R = 0 and h sum P = pi/2) the Newton-Krylov equations
 //   Phi_i = P_i (rows with P_i <= R_i/d_i)  or  R_i/d_i (the others),
-//   Phi_n = h sum P - pi/2,     d_i = |dR_i/dP_i|,
+//   Phi_n = h sum P - pi/2,     d_i = max(|dR_i/dP_i|, max_{|j-i|<=beta} |dR_i/dP_j| / 10),
 // define (P, H0) implicitly as functions of the roughness profile and the
 // Moes parameters M, L.  For an objective J(P, H, H0):
 //   Phi_x^T mu = dJ/dx,   dJ/dtheta = dJ/dtheta|_explicit - mu^T dPhi/dtheta.

@@ -9,6 +9,7 @@
 
 #include "ehl_internal.h"
 #include "line.h"
+#include "point.h"
 
 using namespace ehl;
 
@@ -36,6 +37,9 @@ struct ehl_ctx {
   bool direct = true;  // single bucket in caller order: no gather/scatter
   cudaStream_t st = nullptr;
   std::vector<Bucket*> buckets;
+  PtCtx* pt = nullptr;  // point contact (dim 2): one grid for every instance
+  std::vector<PtCtx*> ptlv;       // its coarse grids (nested iteration), coarsest first
+  std::vector<double*> ptrough;   // roughness injected on each coarse grid
 };
 
 // dst[r][0:len] = src[idx[r]][0:len]  (gather, forward) or the reverse (scatter)
@@ -67,7 +71,7 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   memset(p, 0, sizeof(*p));
   p->dim = dim;
   p->nx = 129;
-  p->ny = 1;
+  p->ny = dim == 2 ? 129 : 1;
   p->xa = -4.5;
   p->xb = 1.5;
   p->ya = -3.0;
@@ -95,8 +99,14 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   p->coarse_tol = 1e-4;
 }
 
+static bool point_grid_ok(const ehl_params& p) {
+  if (p.dim != 2) return true;
+  const double hx = (p.xb - p.xa) / (p.nx - 1), hy = (p.yb - p.ya) / (p.ny - 1);
+  return p.ny >= 5 && p.ny <= 4097 && p.nx <= 4097 && p.yb > p.ya && fabs(hx - hy) <= 1e-12 * hx && p.method == 1;
+}
+
 static bool params_ok(const ehl_params& p) {
-  return p.dim == 1 && p.nx >= 5 && p.nx <= 65536 && p.halfband >= 1 && p.halfband <= 8 && p.M > 0.0 &&
+  return (p.dim == 1 || p.dim == 2) && point_grid_ok(p) && p.nx >= 5 && p.nx <= 65536 && p.halfband >= 1 && p.halfband <= 8 && p.M > 0.0 &&
          p.L >= 0.0 && p.xb > p.xa && p.alpha > 0.0 && p.p0 > 0.0 && p.z > 0.0 && (p.limiter == 0 || p.limiter == 1) &&
          (p.method == 0 || p.method == 1) && p.max_iter >= 1 && p.krylov_dim >= 1 && p.krylov_dim <= 200 &&
          p.tol > 0.0 && isfinite(p.h_init) && isfinite(p.c_h0) && isfinite(p.omega) && isfinite(p.dist_weight) &&
@@ -296,9 +306,97 @@ static ehl_status init_bucket(Bucket* b, const ehl_params& p0, const std::vector
   return EHL_OK;
 }
 
+static PointInst make_point(const ehl_params& p) {
+  PointInst q;
+  memset(&q, 0, sizeof(q));
+  q.m = make_inst(p);
+  // point-contact Moes conversion: lambda = (128 pi^3 / (3 M^4))^(1/3), alpha_bar = (L/pi)(3M/2)^(1/3)
+  q.m.lam = cbrt(128.0 * M_PI * M_PI * M_PI / (3.0 * p.M * p.M * p.M * p.M));
+  q.m.abar = (p.L / M_PI) * cbrt(1.5 * p.M);
+  q.m.pH = q.m.abar / p.alpha;
+  q.nx = p.nx;
+  q.ny = p.ny;
+  q.xa = p.xa;
+  q.ya = p.ya;
+  q.h = (p.xb - p.xa) / (p.nx - 1);
+  return q;
+}
+
+static ehl_status create_point(const ehl_params* p, int n_inst, const ehl_params* per_inst, cudaStream_t stream,
+                               ehl_ctx** out) {
+  std::vector<PointInst> insts(n_inst);
+  for (int k = 0; k < n_inst; ++k) {
+    const ehl_params& q = per_inst ? per_inst[k] : *p;
+    if (q.nx != p->nx || q.ny != p->ny || q.xa != p->xa || q.xb != p->xb || q.ya != p->ya || q.yb != p->yb)
+      return EHL_EINVAL;
+    insts[k] = make_point(q);
+  }
+  ehl_ctx* ctx = new ehl_ctx();
+  ctx->dim = 2;
+  ctx->n_inst = n_inst;
+  ctx->nx_max = p->nx;
+  ctx->beta = p->halfband;
+  ctx->st = stream;
+  ctx->pt = new PtCtx();
+  ctx->pt->st = stream;
+  if (const char* tr = getenv("EHL_TRACE")) ctx->pt->trace = atoi(tr) > 0 ? atoi(tr) : 0;
+  ehl_status st = pt_init(ctx->pt, insts, p->halfband, p->max_iter, p->krylov_dim);
+  // coarse grids: halve the intervals in both directions while both stay even and
+  // the coarse grid keeps coarse_min_nodes nodes per direction
+  int gx = p->nx, gy = p->ny;
+  std::vector<std::pair<int, int>> grids;
+  while (st == EHL_OK && (gx - 1) % 2 == 0 && (gy - 1) % 2 == 0 && (gx - 1) / 2 + 1 >= p->coarse_min_nodes &&
+         (gy - 1) / 2 + 1 >= p->coarse_min_nodes && (p->levels < 0 || (int)grids.size() < p->levels)) {
+    gx = (gx - 1) / 2 + 1;
+    gy = (gy - 1) / 2 + 1;
+    grids.insert(grids.begin(), {gx, gy});
+  }
+  for (auto& gxy : grids) {
+    if (st != EHL_OK) break;
+    std::vector<PointInst> ci(n_inst);
+    for (int k = 0; k < n_inst; ++k) {
+      ehl_params q = per_inst ? per_inst[k] : *p;
+      q.nx = gxy.first;
+      q.ny = gxy.second;
+      q.tol = q.tol > q.coarse_tol ? q.tol : q.coarse_tol;
+      ci[k] = make_point(q);
+    }
+    PtCtx* l = new PtCtx();
+    l->st = stream;
+    l->trace = ctx->pt->trace;
+    ctx->ptlv.push_back(l);
+    st = pt_init(l, ci, p->halfband, p->max_iter, p->krylov_dim);
+    double* r = nullptr;
+    if (st == EHL_OK && pt_alloc(l, (void**)&r, sizeof(double) * n_inst * (size_t)l->NN) != cudaSuccess) {
+      cudaGetLastError();
+      st = EHL_ENOMEM;
+    }
+    ctx->ptrough.push_back(r);
+  }
+  if (st != EHL_OK) {
+    for (PtCtx* l : ctx->ptlv) {
+      pt_free(l);
+      delete l;
+    }
+    pt_free(ctx->pt);
+    delete ctx->pt;
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return EHL_OK;
+}
+
 extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_params* per_inst, void* stream,
                                  ehl_ctx** out) {
   if (!p || !out || n_inst < 1 || n_inst > 65535 || !params_ok(*p)) return EHL_EINVAL;
+  if (p->dim == 2) {
+    if (per_inst)
+      for (int k = 0; k < n_inst; ++k)
+        if (!params_ok(per_inst[k]) || per_inst[k].dim != 2 || per_inst[k].halfband != p->halfband)
+          return EHL_EINVAL;
+    return create_point(p, n_inst, per_inst, (cudaStream_t)stream, out);
+  }
   int nx_max = p->nx;
   if (per_inst) {
     for (int k = 0; k < n_inst; ++k) {
@@ -361,6 +459,16 @@ extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_para
 extern "C" ehl_status ehl_destroy(ehl_ctx* ctx) {
   if (!ctx) return EHL_EINVAL;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
+  if (ctx->pt) {
+    for (PtCtx* l : ctx->ptlv) {
+      pt_free(l);
+      delete l;
+    }
+    ctx->ptlv.clear();
+    pt_free(ctx->pt);
+    delete ctx->pt;
+    ctx->pt = nullptr;
+  }
   free_ctx(ctx);
   return EHL_OK;
 }
@@ -428,9 +536,94 @@ static cudaError_t put_rows(ehl_ctx* ctx, Bucket* b, const T* src, int len, T* d
   return rows(c->st, src, len, dst, dstride, b->d_idx, c->n_inst, len, true);
 }
 
+// ------------------------------------------------------------ point contact
+static cudaError_t pt_put_comp(PtCtx* c, double* comp_res) {
+  return cudaMemcpy2DAsync(comp_res, 2 * sizeof(double), c->red, 4 * sizeof(double), 2 * sizeof(double), c->n_inst,
+                           cudaMemcpyDeviceToDevice, c->st);
+}
+
+static ehl_status pt_residual_api(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, double* R,
+                                  double* H, double* comp_res) {
+  PtCtx* c = ctx->pt;
+  const size_t NNt = (size_t)c->n_inst * c->NN;
+  cudaError_t e = pt_state(c, P, H0, rough, nullptr);
+  if (e == cudaSuccess) e = pt_finalize(c, nullptr, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(R, c->R, sizeof(double) * NNt, cudaMemcpyDeviceToDevice, c->st);
+  if (e == cudaSuccess && H) e = cudaMemcpyAsync(H, c->H, sizeof(double) * NNt, cudaMemcpyDeviceToDevice, c->st);
+  if (e == cudaSuccess && comp_res) e = pt_put_comp(c, comp_res);
+  return cuda_status(e);
+}
+
+// outer iterations of one point-contact grid from (Pw, H0w); done flags in hdone
+static cudaError_t pt_iterate(PtCtx* c, const double* rough, std::vector<int>& hdone) {
+  const int ni = c->n_inst;
+  cudaError_t e = cudaMemsetAsync(c->done, 0, sizeof(int) * ni, c->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->iters, 0, sizeof(int) * ni, c->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->best, 0x7f, sizeof(double) * ni, c->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->stall, 0, sizeof(int) * ni, c->st);
+  hdone.assign(ni, 0);
+  for (int it = 0; it < c->max_iter && e == cudaSuccess; ++it) {
+    e = pt_nk_step(c, c->Pw, c->H0w, rough);
+    if (e != cudaSuccess) break;
+    e = cudaMemcpyAsync(hdone.data(), c->done, sizeof(int) * ni, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    bool all = true;
+    for (int v : hdone) all = all && (v != 0);
+    if (all) break;
+  }
+  return e;
+}
+
+static ehl_status pt_solve_api(ehl_ctx* ctx, double* P, double* H0, const double* rough, int init, int* iters,
+                               double* final_res) {
+  PtCtx* c = ctx->pt;
+  const int ni = c->n_inst;
+  const size_t NNt = (size_t)ni * c->NN;
+  cudaError_t e = cudaSuccess;
+  std::vector<int> hdone(ni, 0);
+  if (init == 1) {
+    e = cudaMemcpyAsync(c->Pw, P, sizeof(double) * NNt, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->H0w, H0, sizeof(double) * ni, cudaMemcpyDeviceToDevice, c->st);
+  } else {
+    PtCtx* prev = nullptr;
+    for (size_t l = 0; l < ctx->ptlv.size() && e == cudaSuccess; ++l) {
+      PtCtx* cl = ctx->ptlv[l];
+      const double* rl = nullptr;
+      if (rough) {
+        e = pt_inject(c, rough, cl, ctx->ptrough[l]);
+        rl = ctx->ptrough[l];
+      }
+      if (e == cudaSuccess) e = pt_start(cl, cl->Pw, cl->H0w, rl);
+      if (e == cudaSuccess && prev) e = pt_prolong(prev, cl);
+      if (e == cudaSuccess) e = pt_iterate(cl, rl, hdone);
+      prev = cl;
+    }
+    if (e == cudaSuccess) e = pt_start(c, c->Pw, c->H0w, rough);
+    if (e == cudaSuccess && prev) e = pt_prolong(prev, c);
+  }
+  if (e == cudaSuccess) e = pt_iterate(c, rough, hdone);
+  if (e == cudaSuccess) e = pt_state(c, c->Pw, c->H0w, rough, nullptr);
+  if (e == cudaSuccess) e = pt_finalize(c, nullptr, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(P, c->Pw, sizeof(double) * NNt, cudaMemcpyDeviceToDevice, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(H0, c->H0w, sizeof(double) * ni, cudaMemcpyDeviceToDevice, c->st);
+  if (e == cudaSuccess && iters)
+    e = cudaMemcpyAsync(iters, c->iters, sizeof(int) * ni, cudaMemcpyDeviceToDevice, c->st);
+  if (e == cudaSuccess && final_res) e = pt_put_comp(c, final_res);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hdone.data(), c->done, sizeof(int) * ni, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_status(e);
+  bool nonfinite = false, noconv = false;
+  for (int v : hdone) {
+    nonfinite = nonfinite || v == 2;
+    noconv = noconv || v == 0;
+  }
+  return nonfinite ? EHL_ENONFINITE : (noconv ? EHL_ENOCONV : EHL_OK);
+}
+
 extern "C" ehl_status ehl_residual(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, double* R,
                                    double* H, double* comp_res) {
   if (!ctx || !P || !H0 || !R) return EHL_EINVAL;
+  if (ctx->pt) return pt_residual_api(ctx, P, H0, rough, R, H, comp_res);
   cudaError_t e = fork(ctx);
   for (Bucket* b : ctx->buckets) {
     LineCtx* c = &b->c;
@@ -446,6 +639,12 @@ extern "C" ehl_status ehl_residual(ehl_ctx* ctx, const double* P, const double* 
 extern "C" ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
                                         int kind, double* band, uint8_t* active) {
   if (!ctx || !P || !H0 || !band || !active || (kind != 0 && kind != 1)) return EHL_EINVAL;
+  if (ctx->pt) {
+    if (kind != 1) return EHL_EINVAL;
+    cudaError_t e = pt_state(ctx->pt, P, H0, rough, nullptr);
+    if (e == cudaSuccess) e = pt_jac_band(ctx->pt, P, band, active, nullptr, nullptr, nullptr);
+    return cuda_status(e);
+  }
   const int bw = 2 * ctx->beta + 1, nmax = ctx->nx_max - 2;
   cudaError_t e = fork(ctx);
   for (Bucket* b : ctx->buckets) {
@@ -469,6 +668,7 @@ extern "C" ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const dou
 extern "C" ehl_status ehl_jacobian_apply(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
                                          const double* v, const double* v_h0, double* out) {
   if (!ctx || !P || !H0 || !v || !v_h0 || !out) return EHL_EINVAL;
+  if (ctx->pt) return cuda_status(pt_jacobian_apply(ctx->pt, P, H0, rough, v, v_h0, out));
   cudaError_t e = fork(ctx);
   for (Bucket* b : ctx->buckets) {
     LineCtx* c = &b->c;
@@ -557,6 +757,7 @@ static cudaError_t solve_bucket(ehl_ctx* ctx, Bucket* b, const double* P, const 
 extern "C" ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const double* rough, int init, int* iters,
                                 double* final_res) {
   if (!ctx || !P || !H0 || (init != 0 && init != 1)) return EHL_EINVAL;
+  if (ctx->pt) return pt_solve_api(ctx, P, H0, rough, init, iters, final_res);
   cudaError_t e = fork(ctx);
   if (e != cudaSuccess) return cuda_status(e);
   const size_t nb = ctx->buckets.size();
@@ -601,6 +802,7 @@ extern "C" ehl_status ehl_adjoint(ehl_ctx* ctx, const double* P, const double* H
                                   const double* gP, const double* gH, const double* gH0, double* grad_rough,
                                   double* grad_ML, double* relres, double tol, int max_cycles) {
   if (!ctx || !P || !H0 || !(tol > 0.0) || max_cycles < 1 || max_cycles > 1000) return EHL_EINVAL;
+  if (ctx->pt) return EHL_EINVAL;  // the point-contact adjoint is not built
   cudaError_t e = fork(ctx);
   for (Bucket* b : ctx->buckets) {
     LineCtx* c = &b->c;

@@ -6,7 +6,8 @@
 // method keeps its three hot-path parts -- the TVD residual, the deformation
 // integral and PAQIF on a band Jacobian -- and uses them in an inexact
 // semismooth Newton iteration:
-//   Phi_i = min(P_i, R_i / d_i)   (d_i = |dR_i/dP_i|, a row scaling),
+//   Phi_i = min(P_i, R_i / d_i)   (a row scaling: d_i = |dR_i/dP_i|, floored at a
+//                                   tenth of the largest band entry of the row),
 //   Phi_n = h sum P - pi/2,
 // each step solving J_Phi dz = -Phi by GMRES on the exact Jacobian (J v from
 // one deformation of v and a local directional derivative), right-

@@ -1,0 +1,69 @@
+// point.h -- host-side state and stage launchers of the point-contact path.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ehl_internal.h"
+#include "line_kernels.cuh"
+
+namespace ehl {
+
+// One point-contact instance: the lubricant constants (in the line record, whose
+// fields line_material reads) and the grid.
+struct PointInst {
+  LineInst m;  // lam, abar, alpha, p0, z, pH, compressible, elastic, limiter, tol, h_init, M, L
+  int nx, ny;
+  double xa, ya, h;
+};
+
+struct PtCtx {
+  int n_inst = 0, nx = 0, ny = 0, NN = 0, n = 0, lines = 0, beta = 2, max_iter = 0, m = 30;
+  cudaStream_t st = nullptr;
+  std::vector<PointInst> h_inst;
+  PointInst* inst = nullptr;
+  float2* gtab = nullptr;    // (2/pi^2) G(a, b) as double-float, [n_inst][ny][nx] (b = y offset)
+  double* gtab64 = nullptr;  // the same in float64
+  int ksplit = 1, nblk = 1, nvb = 1;
+  void* partial = nullptr;   // [ksplit][n_inst][NN] double or float2
+  double *H = nullptr, *rho = nullptr, *drho = nullptr, *deta_rel = nullptr, *eps = nullptr, *u = nullptr;
+  double *F = nullptr, *psia = nullptr, *psib = nullptr, *R = nullptr, *Pw = nullptr, *dH = nullptr;
+  double *blk = nullptr, *red = nullptr, *H0w = nullptr, *best = nullptr;
+  int *done = nullptr, *iters = nullptr, *stall = nullptr;
+  double *band = nullptr, *jh = nullptr, *dg = nullptr, *rhs = nullptr, *sigma = nullptr;
+  uint8_t* act = nullptr;
+  void* pq_ws = nullptr;
+  int* pq_info = nullptr;
+  void* fstore = nullptr;
+  // Newton-Krylov
+  double *V = nullptr, *Z = nullptr, *Hh = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *w = nullptr;
+  double *phinorm = nullptr, *zH = nullptr, *den = nullptr, *delta = nullptr, *Pt = nullptr, *H0t = nullptr;
+  double *tstep = nullptr, *rtol = nullptr, *beta0 = nullptr, *znode = nullptr, *dots = nullptr, *hcol = nullptr;
+  double* zh0 = nullptr;  // border component of the current preconditioned vector, per instance
+  int *gm_k = nullptr, *gm_conv = nullptr, *lsdone = nullptr, *lsphase = nullptr, *skip = nullptr;
+  int* acc = nullptr;     // line search: trial accepted in this pass
+  int trace = 0;
+  std::vector<void*> allocs;
+};
+
+cudaError_t pt_alloc(PtCtx* c, void** p, size_t bytes);
+ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int max_iter, int krylov_dim);
+void pt_free(PtCtx* c);
+// state (film, lubricant, faces, residual, block partials) at (P, H0); all [n_inst][ny][nx]
+cudaError_t pt_state(PtCtx* c, const double* P, const double* H0, const double* rough, const int* skip);
+cudaError_t pt_finalize(PtCtx* c, int* done, int* iters);
+// exact x-line band Jacobian: band [n_inst][ny-2][nx-2][2 beta + 1], act [n_inst][n]
+cudaError_t pt_jac_band(PtCtx* c, const double* P, double* band, uint8_t* act, double* jh, double* dg,
+                        const int* skip);
+cudaError_t pt_jacobian_apply(PtCtx* c, const double* P, const double* H0, const double* rough, const double* v,
+                              const double* v_h0, double* out);
+cudaError_t pt_start(PtCtx* c, double* P, double* H0, const double* rough);
+// grid sequence: coarse values of a fine nodal array; bilinear prolongation of (Pw, H0w)
+cudaError_t pt_inject(const PtCtx* fine, const double* src, PtCtx* coarse, double* dst);
+cudaError_t pt_prolong(const PtCtx* coarse, PtCtx* fine);
+// dH = K zn + zh0 (double-float deformation; the Krylov products)
+cudaError_t pt_deform_dir(PtCtx* c, const double* zn, const double* zh0, const int* skip);
+cudaError_t pt_nk_step(PtCtx* c, double* P, double* H0, const double* rough);
+
+}  // namespace ehl

@@ -1,0 +1,627 @@
+// point_newton.cu -- Newton-Krylov step of the point-contact solve.
+//
+// Phi_r = P_r (rows with P <= R/d) or R_r/d_r (the others), d = |dR_r/dP_r| floored
+// at a tenth of the largest x-band entry of the row,
+// Phi_n = h^2 sum P - 2 pi/3.  Each step: the exact x-line bands, scaled by
+// 1/d; PAQIF factorization of every grid row's band (ny-2 systems per
+// instance) solving for the border column dR/dH0; GMRES with classical
+// Gram-Schmidt applied twice, right-preconditioned by the bordered x-line
+// solve; the exact Jacobian product from one 2-D deformation of the Krylov
+// vector; backtracking on ||Phi||_2 (projected trials first, unprojected
+// after 2^-10, as in line contact).  Vector kernels use many blocks per
+// instance, each thread kPtVPT elements; per-instance scalars are finished by
+// one-block kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <vector>
+
+#include "ehl_internal.h"
+#include "point.h"
+
+namespace ehl {
+
+constexpr int kNB = 256;   // threads of the vector kernels
+constexpr int kNV = 8;     // elements per thread
+
+struct PtView {  // device pointers the vector kernels need
+  const PointInst* inst;
+  int nx, ny, NN, n, n1, m, nvb, beta;
+  const int* done;
+  const int* skip;
+  double *V, *Z, *Hh, *cs, *sn, *g, *w, *dots, *hcol, *delta, *zH, *rhs, *sigma, *band, *jh, *dg, *R, *red;
+  double *phinorm, *den, *rtol, *beta0, *tstep, *zh0, *H0t, *Pt, *znode;
+  const uint8_t* act;
+  int *gm_k, *gm_conv, *lsdone, *lsphase, *acc;
+};
+
+__device__ __forceinline__ double nk_block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kNB / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ int nk_node(int r, int nx) { return (r / (nx - 2) + 1) * nx + (r % (nx - 2)) + 1; }
+
+// element k of this thread's share of [0, len)
+#define NK_FOR(r, len)                                                         \
+  for (int _k = 0, r = blockIdx.x * (kNB * kNV) + threadIdx.x; _k < kNV; ++_k, \
+           r = blockIdx.x * (kNB * kNV) + threadIdx.x + _k * kNB)              \
+    if (r < (len))
+
+__global__ void k_pn_skip(const int* __restrict__ done, const int* __restrict__ other, int* __restrict__ skip, int ni) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z < ni) skip[z] = (done[z] != 0) || (other && other[z] != 0);
+}
+
+// scale equation rows by 1/d; rhs = (dR/dH0)/d; Phi into V_0 (unnormalised); partial |Phi|^2
+__global__ void __launch_bounds__(kNB) k_pn_setup(PtView v, const double* __restrict__ P) {
+  const int z = blockIdx.y;
+  if (v.done[z]) return;
+  __shared__ double sh[kNB];
+  const int w = 2 * v.beta + 1;
+  double ss = 0.0;
+  double* V0 = v.V + (size_t)z * (v.m + 1) * v.n1;
+  NK_FOR(r, v.n) {
+    const size_t o = (size_t)z * v.n + r;
+    const size_t node = (size_t)z * v.NN + nk_node(r, v.nx);
+    double ph;
+    if (v.act[o]) {
+      ph = P[node];
+      v.rhs[o] = 0.0;
+    } else {
+      const double d = v.dg[o];
+      double* row = v.band + o * w;
+      for (int t = 0; t < w; ++t) row[t] /= d;
+      v.rhs[o] = v.jh[o] / d;
+      ph = v.R[node] / d;
+    }
+    V0[r] = ph;
+    ss += ph * ph;
+  }
+  ss = nk_block_sum(ss, sh);
+  if (threadIdx.x == 0) v.dots[((size_t)z * v.nvb + blockIdx.x) * (v.m + 2)] = ss;
+}
+
+// |Phi|, the GMRES start and the Newton-step tolerance
+__global__ void __launch_bounds__(kNB) k_pn_setup2(PtView v) {
+  const int z = blockIdx.x;
+  if (v.done[z]) return;
+  __shared__ double sh[kNB];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < v.nvb; b += kNB) s += v.dots[((size_t)z * v.nvb + b) * (v.m + 2)];
+  s = nk_block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    const double f = v.red[z * 4 + 1];
+    const double nrm = sqrt(s + f * f);
+    double* V0 = v.V + (size_t)z * (v.m + 1) * v.n1;
+    V0[v.n] = f;
+    v.phinorm[z] = nrm;
+    v.beta0[z] = nrm;
+    v.g[(size_t)z * (v.m + 1)] = nrm;
+    v.gm_k[z] = 0;
+    v.gm_conv[z] = nrm > 0.0 ? 0 : 1;
+    v.rtol[z] = fmin(1e-3, fmax(1e-6, 1e-2 * v.red[z * 4 + 0]));
+    v.hcol[(size_t)z * (v.m + 2) + v.m + 1] = nrm > 0.0 ? -1.0 / nrm : 0.0;
+  }
+}
+
+// x[0:len] *= hcol[m+1]; optionally rhs = x[0:n]
+__global__ void __launch_bounds__(kNB) k_pn_scale(PtView v, double* __restrict__ x, size_t xstride, int copy_rhs,
+                                                  const int* __restrict__ skip) {
+  const int z = blockIdx.y;
+  if (skip[z]) return;
+  const double a = v.hcol[(size_t)z * (v.m + 2) + v.m + 1];
+  double* xz = x + (size_t)z * xstride;
+  NK_FOR(r, v.n1) {
+    const double y = xz[r] * a;
+    xz[r] = y;
+    if (copy_rhs && r < v.n) v.rhs[(size_t)z * v.n + r] = y;
+  }
+}
+
+// partial sums of a[0:n] (per instance stride astride) into dots slot q
+__global__ void __launch_bounds__(kNB) k_pn_psum(PtView v, const double* __restrict__ a, size_t astride, int q,
+                                                 const int* __restrict__ skip) {
+  const int z = blockIdx.y;
+  if (skip[z]) return;
+  __shared__ double sh[kNB];
+  double s = 0.0;
+  NK_FOR(r, v.n) s += a[(size_t)z * astride + r];
+  s = nk_block_sum(s, sh);
+  if (threadIdx.x == 0) v.dots[((size_t)z * v.nvb + blockIdx.x) * (v.m + 2) + q] = s;
+}
+
+__device__ __forceinline__ double pn_total(const PtView& v, int z, int q, double* sh) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < v.nvb; b += kNB) s += v.dots[((size_t)z * v.nvb + b) * (v.m + 2) + q];
+  return nk_block_sum(s, sh);
+}
+
+// zH = sigma; den = h^2 sum zH (after k_pn_psum of sigma into slot 0); first PAQIF input = V_0[0:n]
+__global__ void __launch_bounds__(kNB) k_pn_border(PtView v) {
+  const int z = blockIdx.x;
+  if (v.done[z]) return;
+  __shared__ double sh[kNB];
+  const double s = pn_total(v, z, 0, sh);
+  const double h = v.inst[z].h;
+  if (threadIdx.x == 0) v.den[z] = fabs(h * h * s) > 1e-300 ? h * h * s : 1e-300;
+  const double* V0 = v.V + (size_t)z * (v.m + 1) * v.n1;
+  for (int r = threadIdx.x; r < v.n; r += kNB) {
+    v.zH[(size_t)z * v.n + r] = v.sigma[(size_t)z * v.n + r];
+    v.rhs[(size_t)z * v.n + r] = V0[r];
+  }
+}
+
+// xi = (h^2 sum sigma - V_j[n]) / den  (after k_pn_psum of sigma into slot 0)
+__global__ void __launch_bounds__(kNB) k_pn_prec2(PtView v, int j) {
+  const int z = blockIdx.x;
+  if (v.skip[z]) return;
+  __shared__ double sh[kNB];
+  const double s = pn_total(v, z, 0, sh);
+  if (threadIdx.x == 0) {
+    const double h = v.inst[z].h;
+    const double* Vj = v.V + ((size_t)z * (v.m + 1) + j) * v.n1;
+    const double xi = (h * h * s - Vj[v.n]) / v.den[z];
+    v.zh0[z] = xi;
+    v.Z[((size_t)z * v.m + j) * v.n1 + v.n] = xi;
+  }
+}
+
+// Z_j = sigma - xi zH on the interior; the nodal copy for the deformation (0 on the boundary)
+__global__ void __launch_bounds__(kNB) k_pn_prec3(PtView v, int j) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= v.NN) return;
+  const int jj = t / v.nx, ii = t % v.nx;
+  double val = 0.0;
+  if (ii >= 1 && ii <= v.nx - 2 && jj >= 1 && jj <= v.ny - 2) {
+    const int r = (jj - 1) * (v.nx - 2) + (ii - 1);
+    const size_t o = (size_t)z * v.n + r;
+    val = v.sigma[o] - v.zh0[z] * v.zH[o];
+    v.Z[((size_t)z * v.m + j) * v.n1 + r] = val;
+  }
+  v.znode[(size_t)z * v.NN + t] = val;
+}
+
+// w = J_Phi Z_j on the interior rows (the force row by k_pn_psum + k_pn_force)
+struct PnRowArgs {
+  const double *P, *H, *rho, *drho, *deta_rel, *eps, *psia, *psib, *dH;
+};
+__global__ void __launch_bounds__(kNB) k_pn_jv(PtView v, PnRowArgs q, int j) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  const PointInst in = v.inst[z];
+  const int nx = v.nx;
+  const size_t base = (size_t)z * v.NN;
+  const double* Zj = v.Z + ((size_t)z * v.m + j) * v.n1;
+  const double h = in.h;
+  NK_FOR(r, v.n) {
+    const size_t o = (size_t)z * v.n + r;
+    const int i = r % (nx - 2) + 1, jj = r / (nx - 2) + 1;
+    double out;
+    if (v.act[o]) {
+      out = Zj[r];
+    } else {
+      auto idx = [&](int p, int qq) { return base + (size_t)qq * nx + p; };
+      auto dH = [&](int p, int qq) { return q.dH[idx(p, qq)]; };
+      auto zn = [&](int p, int qq) { return v.znode[idx(p, qq)]; };
+      auto dU = [&](int p, int qq) {
+        const size_t k = idx(p, qq);
+        return q.rho[k] * dH(p, qq) + q.drho[k] * q.H[k] * zn(p, qq);
+      };
+      auto dE = [&](int p, int qq) {
+        const size_t k = idx(p, qq);
+        return (3.0 * q.eps[k] / q.H[k]) * dH(p, qq) + q.eps[k] * (q.drho[k] / q.rho[k] - q.deta_rel[k]) * zn(p, qq);
+      };
+      auto dF = [&](int f, int qq) {
+        const double d0 = dU(f, qq);
+        if (f == 0) return d0;
+        const size_t k = idx(f, qq);
+        return d0 + 0.5 * (q.psia[k] * (d0 - dU(f - 1, qq)) + q.psib[k] * (dU(f + 1, qq) - d0));
+      };
+      const size_t c = idx(i, jj);
+      const double e = q.eps[c], p = q.P[c];
+      const double ex1 = 0.5 * (e + q.eps[c + 1]), ex0 = 0.5 * (q.eps[c - 1] + e);
+      const double ey1 = 0.5 * (e + q.eps[c + nx]), ey0 = 0.5 * (q.eps[c - nx] + e);
+      const double dEc = dE(i, jj), z0 = zn(i, jj);
+      const double dC = (dF(i, jj) - dF(i - 1, jj)) / h;
+      const double dq = 0.5 * (dEc + dE(i + 1, jj)) * (q.P[c + 1] - p) + ex1 * (zn(i + 1, jj) - z0) -
+                        0.5 * (dE(i - 1, jj) + dEc) * (p - q.P[c - 1]) - ex0 * (z0 - zn(i - 1, jj)) +
+                        0.5 * (dEc + dE(i, jj + 1)) * (q.P[c + nx] - p) + ey1 * (zn(i, jj + 1) - z0) -
+                        0.5 * (dE(i, jj - 1) + dEc) * (p - q.P[c - nx]) - ey0 * (z0 - zn(i, jj - 1));
+      out = (dC - dq / (h * h)) / v.dg[o];
+    }
+    v.w[(size_t)z * v.n1 + r] = out;
+  }
+}
+
+// w[n] = h^2 sum Z_j[0:n] (after k_pn_psum of Z_j into slot 0)
+__global__ void __launch_bounds__(kNB) k_pn_force(PtView v) {
+  const int z = blockIdx.x;
+  if (v.skip[z]) return;
+  __shared__ double sh[kNB];
+  const double s = pn_total(v, z, 0, sh);
+  if (threadIdx.x == 0) {
+    const double h = v.inst[z].h;
+    v.w[(size_t)z * v.n1 + v.n] = h * h * s;
+  }
+}
+
+// partial dot products w . V_i, i = 0..j, into dots slots 0..j
+__global__ void __launch_bounds__(kNB) k_pn_dots(PtView v, int j) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  __shared__ double sh[kNB];
+  const double* wz = v.w + (size_t)z * v.n1;
+  for (int i = 0; i <= j; ++i) {
+    const double* Vi = v.V + ((size_t)z * (v.m + 1) + i) * v.n1;
+    double s = 0.0;
+    NK_FOR(r, v.n1) s += wz[r] * Vi[r];
+    s = nk_block_sum(s, sh);
+    if (threadIdx.x == 0) v.dots[((size_t)z * v.nvb + blockIdx.x) * (v.m + 2) + i] = s;
+  }
+}
+
+// h_i = sum of the partials; H(:, j) = h (first pass) or += h (second pass)
+__global__ void __launch_bounds__(kNB) k_pn_hsum(PtView v, int j, int pass) {
+  const int z = blockIdx.x;
+  if (v.skip[z]) return;
+  __shared__ double sh[kNB];
+  double* H = v.Hh + (size_t)z * (v.m + 1) * v.m;
+  for (int i = 0; i <= j; ++i) {
+    const double s = pn_total(v, z, i, sh);
+    if (threadIdx.x == 0) {
+      v.hcol[(size_t)z * (v.m + 2) + i] = s;
+      H[i + (size_t)j * (v.m + 1)] = pass == 0 ? s : H[i + (size_t)j * (v.m + 1)] + s;
+    }
+  }
+}
+
+// w -= sum_i h_i V_i
+__global__ void __launch_bounds__(kNB) k_pn_orth(PtView v, int j) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  const double* hz = v.hcol + (size_t)z * (v.m + 2);
+  double* wz = v.w + (size_t)z * v.n1;
+  NK_FOR(r, v.n1) {
+    double s = wz[r];
+    for (int i = 0; i <= j; ++i) s -= hz[i] * v.V[((size_t)z * (v.m + 1) + i) * v.n1 + r];
+    wz[r] = s;
+  }
+}
+
+// partial |w|^2 into slot 0
+__global__ void __launch_bounds__(kNB) k_pn_norm(PtView v) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  __shared__ double sh[kNB];
+  const double* wz = v.w + (size_t)z * v.n1;
+  double s = 0.0;
+  NK_FOR(r, v.n1) s += wz[r] * wz[r];
+  s = nk_block_sum(s, sh);
+  if (threadIdx.x == 0) v.dots[((size_t)z * v.nvb + blockIdx.x) * (v.m + 2)] = s;
+}
+
+// H(j+1, j) = |w|; Givens rotations; convergence; 1/|w| for the normalisation
+__global__ void __launch_bounds__(kNB) k_pn_givens(PtView v, int j) {
+  const int z = blockIdx.x;
+  if (v.skip[z]) return;
+  __shared__ double sh[kNB];
+  const double nn = sqrt(pn_total(v, z, 0, sh));
+  if (threadIdx.x != 0) return;
+  const int m = v.m;
+  double* H = v.Hh + (size_t)z * (m + 1) * m;
+  double* cs = v.cs + (size_t)z * m;
+  double* sn = v.sn + (size_t)z * m;
+  double* g = v.g + (size_t)z * (m + 1);
+  H[j + 1 + (size_t)j * (m + 1)] = nn;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i + (size_t)j * (m + 1)], b = H[i + 1 + (size_t)j * (m + 1)];
+    H[i + (size_t)j * (m + 1)] = cs[i] * a + sn[i] * b;
+    H[i + 1 + (size_t)j * (m + 1)] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = H[j + (size_t)j * (m + 1)], b = H[j + 1 + (size_t)j * (m + 1)];
+  const double rr = hypot(a, b);
+  const double c = rr > 0.0 ? a / rr : 1.0, s = rr > 0.0 ? b / rr : 0.0;
+  cs[j] = c;
+  sn[j] = s;
+  H[j + (size_t)j * (m + 1)] = rr;
+  H[j + 1 + (size_t)j * (m + 1)] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  v.gm_k[z] = j + 1;
+  if (fabs(g[j + 1]) <= v.rtol[z] * v.beta0[z] || j + 1 == m || nn == 0.0) v.gm_conv[z] = 1;
+  v.hcol[(size_t)z * (m + 2) + m + 1] = nn > 0.0 ? 1.0 / nn : 0.0;
+}
+
+// V_{j+1} = w / |w|, next PAQIF input
+__global__ void __launch_bounds__(kNB) k_pn_next(PtView v, int j) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  const double a = v.hcol[(size_t)z * (v.m + 2) + v.m + 1];
+  double* Vn = v.V + ((size_t)z * (v.m + 1) + j + 1) * v.n1;
+  const double* wz = v.w + (size_t)z * v.n1;
+  NK_FOR(r, v.n1) {
+    const double y = wz[r] * a;
+    Vn[r] = y;
+    if (r < v.n) v.rhs[(size_t)z * v.n + r] = y;
+  }
+}
+
+// y = R^-1 g (into hcol), then the step delta = sum y_q Z_q
+__global__ void __launch_bounds__(kNB) k_pn_ysolve(PtView v) {
+  const int z = blockIdx.x;
+  if (v.done[z]) return;
+  if (threadIdx.x != 0) return;
+  const int m = v.m, k = v.gm_k[z];
+  const double* H = v.Hh + (size_t)z * (m + 1) * m;
+  const double* g = v.g + (size_t)z * (m + 1);
+  double* y = v.hcol + (size_t)z * (m + 2);
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int q = i + 1; q < k; ++q) s -= H[i + (size_t)q * (m + 1)] * y[q];
+    const double dgl = H[i + (size_t)i * (m + 1)];
+    y[i] = dgl != 0.0 ? s / dgl : 0.0;
+  }
+  v.tstep[z] = 1.0;
+  v.lsdone[z] = 0;
+  v.lsphase[z] = 0;
+}
+__global__ void __launch_bounds__(kNB) k_pn_delta(PtView v) {
+  const int z = blockIdx.y;
+  if (v.done[z]) return;
+  const int k = v.gm_k[z];
+  const double* y = v.hcol + (size_t)z * (v.m + 2);
+  NK_FOR(r, v.n1) {
+    double s = 0.0;
+    for (int q = 0; q < k; ++q) s += y[q] * v.Z[((size_t)z * v.m + q) * v.n1 + r];
+    v.delta[(size_t)z * v.n1 + r] = s;
+  }
+}
+
+// trial point (projected in phase 0)
+__global__ void __launch_bounds__(kNB) k_pn_trial(PtView v, const double* __restrict__ P,
+                                                  const double* __restrict__ H0) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= v.NN) return;
+  const int jj = t / v.nx, ii = t % v.nx;
+  const double st = v.tstep[z];
+  double val = 0.0;
+  if (ii >= 1 && ii <= v.nx - 2 && jj >= 1 && jj <= v.ny - 2) {
+    const int r = (jj - 1) * (v.nx - 2) + (ii - 1);
+    val = P[(size_t)z * v.NN + t] + st * v.delta[(size_t)z * v.n1 + r];
+    if (v.lsphase[z] == 0) val = val > 0.0 ? val : 0.0;
+  }
+  v.Pt[(size_t)z * v.NN + t] = val;
+  if (t == 0) v.H0t[z] = H0[z] + st * v.delta[(size_t)z * v.n1 + v.n];
+}
+
+// partial |min(P_t, R_t/d)|^2 (slot 0) and a non-finite count (slot 1)
+__global__ void __launch_bounds__(kNB) k_pn_merit1(PtView v) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  __shared__ double sh[kNB];
+  double s = 0.0, nf = 0.0;
+  NK_FOR(r, v.n) {
+    const size_t node = (size_t)z * v.NN + nk_node(r, v.nx);
+    const double pt = v.Pt[node], rt = v.R[node] / v.dg[(size_t)z * v.n + r];
+    const double ph = pt < rt ? pt : rt;
+    if (!(ph == ph) || isinf(ph)) nf += 1.0;
+    s += ph * ph;
+  }
+  s = nk_block_sum(s, sh);
+  nf = nk_block_sum(nf, sh);
+  if (threadIdx.x == 0) {
+    double* d = v.dots + ((size_t)z * v.nvb + blockIdx.x) * (v.m + 2);
+    d[0] = s;
+    d[1] = nf;
+  }
+}
+
+// accept (H0 here, P by k_pn_accept) or shorten the step
+__global__ void __launch_bounds__(kNB) k_pn_merit2(PtView v, double* __restrict__ H0) {
+  const int z = blockIdx.x;
+  if (v.skip[z]) return;
+  __shared__ double sh[kNB];
+  const double s = pn_total(v, z, 0, sh);
+  const double nf = pn_total(v, z, 1, sh);
+  if (threadIdx.x != 0) return;
+  const double f = v.red[z * 4 + 1];
+  const double nrm = sqrt(s + f * f);
+  const double t = v.tstep[z];
+  const int phase = v.lsphase[z];
+  const bool ok = nf == 0.0 && nrm == nrm && nrm <= (1.0 - 1e-4 * t) * v.phinorm[z];
+  const bool accept = ok || (phase == 1 && t < 1e-10);
+  v.acc[z] = accept ? 1 : 0;
+  if (accept) {
+    H0[z] = v.H0t[z];
+    v.lsdone[z] = 1;
+  } else if (phase == 0 && 0.5 * t < 0x1p-10) {
+    v.lsphase[z] = 1;
+    v.tstep[z] = 1.0;
+  } else {
+    v.tstep[z] = 0.5 * t;
+  }
+}
+
+__global__ void k_pn_accept(PtView v, double* __restrict__ P) {
+  const int z = blockIdx.y;
+  if (v.skip[z] || !v.acc[z]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < v.NN) P[(size_t)z * v.NN + t] = v.Pt[(size_t)z * v.NN + t];
+}
+
+// ----------------------------------------------------------------- host side
+static PtView pt_view(PtCtx* c, const int* skip) {
+  PtView v;
+  v.inst = c->inst;
+  v.nx = c->nx;
+  v.ny = c->ny;
+  v.NN = c->NN;
+  v.n = c->n;
+  v.n1 = c->n + 1;
+  v.m = c->m;
+  v.nvb = c->nvb;
+  v.beta = c->beta;
+  v.done = c->done;
+  v.skip = skip;
+  v.V = c->V;
+  v.Z = c->Z;
+  v.Hh = c->Hh;
+  v.cs = c->cs;
+  v.sn = c->sn;
+  v.g = c->g;
+  v.w = c->w;
+  v.dots = c->dots;
+  v.hcol = c->hcol;
+  v.delta = c->delta;
+  v.zH = c->zH;
+  v.rhs = c->rhs;
+  v.sigma = c->sigma;
+  v.band = c->band;
+  v.jh = c->jh;
+  v.dg = c->dg;
+  v.R = c->R;
+  v.red = c->red;
+  v.phinorm = c->phinorm;
+  v.den = c->den;
+  v.rtol = c->rtol;
+  v.beta0 = c->beta0;
+  v.tstep = c->tstep;
+  v.zh0 = c->zh0;
+  v.H0t = c->H0t;
+  v.Pt = c->Pt;
+  v.znode = c->znode;
+  v.act = c->act;
+  v.gm_k = c->gm_k;
+  v.gm_conv = c->gm_conv;
+  v.lsdone = c->lsdone;
+  v.lsphase = c->lsphase;
+  v.acc = c->acc;
+  return v;
+}
+
+static cudaError_t pn_paqif(PtCtx* c, const double* rhs, double* x, bool factor) {
+  PaqifLaunch L;
+  L.n_sys = c->lines;
+  L.n = c->nx - 2;
+  L.beta = c->beta;
+  L.mode = 0;
+  L.band = c->band;
+  L.rhs = rhs;
+  L.act = nullptr;
+  L.stack = c->pq_ws;
+  L.x = x;
+  L.iters = nullptr;
+  L.info = c->pq_info;
+  return factor ? launch_paqif_factor(L, c->fstore, c->st) : launch_paqif_resolve(L, c->fstore, c->st);
+}
+
+static bool pn_all(PtCtx* c, const int* a, const int* b, cudaError_t& e) {
+  std::vector<int> ha(c->n_inst), hb(c->n_inst);
+  e = cudaMemcpyAsync(ha.data(), a, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess && b) e = cudaMemcpyAsync(hb.data(), b, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  for (int k = 0; k < c->n_inst; ++k)
+    if (!ha[k] && !(b && hb[k])) return false;
+  return true;
+}
+
+cudaError_t pt_nk_step(PtCtx* c, double* P, double* H0, const double* rough) {
+  const int ni = c->n_inst;
+  cudaError_t e = pt_state(c, P, H0, rough, c->done);
+  if (e == cudaSuccess) e = pt_finalize(c, c->done, c->iters);
+  if (e == cudaSuccess) e = pt_jac_band(c, P, c->band, c->act, c->jh, c->dg, c->done);
+  if (e != cudaSuccess) return e;
+  const dim3 gv(c->nvb, ni), gn((c->NN + 255) / 256, ni);
+  PtView vd = pt_view(c, c->done);
+  k_pn_setup<<<gv, kNB, 0, c->st>>>(vd, P);
+  note_launch();
+  k_pn_setup2<<<ni, kNB, 0, c->st>>>(vd);
+  note_launch();
+  k_pn_scale<<<gv, kNB, 0, c->st>>>(vd, c->V, (size_t)(c->m + 1) * (c->n + 1), 0, c->done);
+  note_launch();
+  e = pn_paqif(c, c->rhs, c->sigma, true);  // factor; sigma = B^-1 (dR/dH0)/d
+  if (e != cudaSuccess) return e;
+  k_pn_psum<<<gv, kNB, 0, c->st>>>(vd, c->sigma, (size_t)c->n, 0, c->done);
+  note_launch();
+  k_pn_border<<<ni, kNB, 0, c->st>>>(vd);
+  note_launch();
+  PtView vs = pt_view(c, c->skip);
+  const PnRowArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH};
+  for (int j = 0; j < c->m; ++j) {
+    k_pn_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, c->gm_conv, c->skip, ni);
+    note_launch();
+    e = pn_paqif(c, c->rhs, c->sigma, false);
+    if (e != cudaSuccess) return e;
+    k_pn_psum<<<gv, kNB, 0, c->st>>>(vs, c->sigma, (size_t)c->n, 0, c->skip);
+    note_launch();
+    k_pn_prec2<<<ni, kNB, 0, c->st>>>(vs, j);
+    note_launch();
+    k_pn_prec3<<<gn, 256, 0, c->st>>>(vs, j);
+    note_launch();
+    // dH = K z + xi: the double-float deformation of the Krylov vector
+    e = pt_deform_dir(c, c->znode, c->zh0, c->skip);
+    if (e != cudaSuccess) return e;
+    k_pn_jv<<<gv, kNB, 0, c->st>>>(vs, q, j);
+    note_launch();
+    k_pn_psum<<<gv, kNB, 0, c->st>>>(vs, c->Z + (size_t)j * (c->n + 1), (size_t)c->m * (c->n + 1), 0, c->skip);
+    note_launch();
+    k_pn_force<<<ni, kNB, 0, c->st>>>(vs);
+    note_launch();
+    for (int pass = 0; pass < 2; ++pass) {
+      k_pn_dots<<<gv, kNB, 0, c->st>>>(vs, j);
+      note_launch();
+      k_pn_hsum<<<ni, kNB, 0, c->st>>>(vs, j, pass);
+      note_launch();
+      k_pn_orth<<<gv, kNB, 0, c->st>>>(vs, j);
+      note_launch();
+    }
+    k_pn_norm<<<gv, kNB, 0, c->st>>>(vs);
+    note_launch();
+    k_pn_givens<<<ni, kNB, 0, c->st>>>(vs, j);
+    note_launch();
+    k_pn_next<<<gv, kNB, 0, c->st>>>(vs, j);
+    note_launch();
+    if ((j + 1) % 8 == 0 && j + 1 < c->m) {
+      if (pn_all(c, c->done, c->gm_conv, e)) break;
+      if (e != cudaSuccess) return e;
+    }
+  }
+  k_pn_ysolve<<<ni, kNB, 0, c->st>>>(vd);
+  note_launch();
+  k_pn_delta<<<gv, kNB, 0, c->st>>>(vd);
+  note_launch();
+  for (int trial = 0; trial < 64; ++trial) {
+    k_pn_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, c->lsdone, c->skip, ni);
+    note_launch();
+    k_pn_trial<<<gn, 256, 0, c->st>>>(vs, P, H0);
+    note_launch();
+    e = pt_state(c, c->Pt, c->H0t, rough, c->skip);
+    if (e == cudaSuccess) e = pt_finalize(c, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    k_pn_merit1<<<gv, kNB, 0, c->st>>>(vs);
+    note_launch();
+    k_pn_merit2<<<ni, kNB, 0, c->st>>>(vs, H0);
+    note_launch();
+    k_pn_accept<<<gn, 256, 0, c->st>>>(vs, P);
+    note_launch();
+    if (pn_all(c, c->done, c->lsdone, e)) break;
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ehl

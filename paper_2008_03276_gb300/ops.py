@@ -100,9 +100,13 @@ class Context:
         self.params = params
         self.per_inst = per_inst
         self.n_inst = n_inst
+        self.dim = params.dim
         self.nxs = [q.nx for q in per_inst] if per_inst is not None else [params.nx] * n_inst
         self.nx = max([params.nx] + self.nxs)
+        self.ny = params.ny if self.dim == 2 else 1
         self.ragged = any(v != self.nx for v in self.nxs)
+        # nodal arrays: [n_inst][nx] (line) or [n_inst][ny][nx] (point, x fastest)
+        self.node_shape = (n_inst, self.nx) if self.dim == 1 else (n_inst, self.ny, self.nx)
         self.beta = params.halfband
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         arr = None
@@ -130,8 +134,8 @@ class Context:
 
     def _check(self, P, H0, rough=None, v=None, v_h0=None):
         _check_dev(P, H0, rough, v, v_h0)
-        for t, shape in ((P, (self.n_inst, self.nx)), (H0, (self.n_inst,)), (rough, (self.n_inst, self.nx)),
-                         (v, (self.n_inst, self.nx)), (v_h0, (self.n_inst,))):
+        ns = self.node_shape
+        for t, shape in ((P, ns), (H0, (self.n_inst,)), (rough, ns), (v, ns), (v_h0, (self.n_inst,))):
             if t is not None and (tuple(t.shape) != shape or t.dtype != torch.float64):
                 raise ValueError(f"expected a float64 tensor of shape {shape}, got {tuple(t.shape)} {t.dtype}")
 
@@ -145,11 +149,13 @@ class Context:
         return R, H, comp
 
     def jacobian_band(self, P, H0, kind=0, rough=None):
+        """Band Jacobian: [n_inst][nx-2][2 beta + 1] (line) or the x-line bands
+        [n_inst][ny-2][nx-2][2 beta + 1] of the exact Jacobian (point, kind 1)."""
         self._check(P, H0, rough)
-        n = self.nx - 2
+        rows = (self.nx - 2,) if self.dim == 1 else (self.ny - 2, self.nx - 2)
         alloc = torch.zeros if self.ragged else torch.empty
-        band = alloc((self.n_inst, n, 2 * self.beta + 1), dtype=torch.float64, device=P.device)
-        act = alloc((self.n_inst, n), dtype=torch.uint8, device=P.device)
+        band = alloc((self.n_inst,) + rows + (2 * self.beta + 1,), dtype=torch.float64, device=P.device)
+        act = alloc((self.n_inst,) + rows, dtype=torch.uint8, device=P.device)
         code = self._lib.ehl_jacobian_band(self._h, _ptr(P), _ptr(H0), _ptr(rough), kind, _ptr(band), _ptr(act))
         _ffi.check(code, "ehl_jacobian_band")
         return band, act
@@ -166,7 +172,7 @@ class Context:
         init = 1
         if P is None:
             init = 0
-            P = torch.zeros((self.n_inst, self.nx), dtype=torch.float64, device=dev)
+            P = torch.zeros(self.node_shape, dtype=torch.float64, device=dev)
             H0 = torch.zeros(self.n_inst, dtype=torch.float64, device=dev)
         else:
             P = P.clone()
