@@ -157,6 +157,10 @@ typedef struct {
                         /*   -1 as many as allowed (default), 0 none                     */
   int coarse_min_nodes; /* coarsest grid keeps at least this many nodes (65)             */
   double coarse_tol;    /* tolerance of the coarse-grid solves, max(tol, coarse_tol) (1e-4) */
+  int precond_blocks;   /* line contact, method 1: the band preconditioner is PAQIF on r  */
+                        /*   diagonal blocks of each band (block Jacobi: couplings between */
+                        /*   blocks dropped), r the largest divisor of nx - 2 not above    */
+                        /*   precond_blocks with blocks of at least 32 rows; 1: one system */
 } ehl_params;
 
 /* Fill *p with the defaults above for dimension `dim` (1). */

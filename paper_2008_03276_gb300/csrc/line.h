@@ -27,6 +27,7 @@ struct LineCtx {
   void* pq_ws = nullptr;
   size_t pq_ws_bytes = 0;
   int* pq_info = nullptr;
+  int pq_parts = 1;  // Krylov preconditioner: PAQIF blocks per band (block Jacobi)
   double *Pw = nullptr, *H0w = nullptr, *dH = nullptr;
   int *done = nullptr, *iters = nullptr;
   double* best = nullptr;  // smallest ||min(P,R)||_inf seen (stall test of the rounding-floor stop)

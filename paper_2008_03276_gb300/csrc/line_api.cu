@@ -97,6 +97,7 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   p->levels = -1;
   p->coarse_min_nodes = 65;
   p->coarse_tol = 1e-4;
+  p->precond_blocks = 1;
 }
 
 static bool point_grid_ok(const ehl_params& p) {
@@ -110,7 +111,8 @@ static bool params_ok(const ehl_params& p) {
          p.L >= 0.0 && p.xb > p.xa && p.alpha > 0.0 && p.p0 > 0.0 && p.z > 0.0 && (p.limiter == 0 || p.limiter == 1) &&
          (p.method == 0 || p.method == 1) && p.max_iter >= 1 && p.krylov_dim >= 1 && p.krylov_dim <= 200 &&
          p.tol > 0.0 && isfinite(p.h_init) && isfinite(p.c_h0) && isfinite(p.omega) && isfinite(p.dist_weight) &&
-         isfinite(p.switch_eps_h) && p.levels >= -1 && p.coarse_min_nodes >= 5 && p.coarse_tol > 0.0;
+         isfinite(p.switch_eps_h) && p.levels >= -1 && p.coarse_min_nodes >= 5 && p.coarse_tol > 0.0 &&
+         p.precond_blocks >= 1 && p.precond_blocks <= 4096;
 }
 
 static LineInst make_inst(const ehl_params& p) {
@@ -207,12 +209,21 @@ static ehl_status init_line(LineCtx* c, const std::vector<LineInst>& insts, int 
   A((void**)&c->iters, sizeof(int) * n_inst);
   A((void**)&c->best, sizeof(double) * n_inst);
   A((void**)&c->stall, sizeof(int) * n_inst);
-  A((void**)&c->pq_info, sizeof(int) * n_inst);
+  // preconditioner blocks: the largest divisor r of n with r <= precond_blocks and n / r >= 32
+  c->pq_parts = 1;
+  if (p.method == 1)
+    for (int r = p.precond_blocks; r > 1; --r)
+      if (c->n % r == 0 && c->n / r >= 32) {
+        c->pq_parts = r;
+        break;
+      }
+  A((void**)&c->pq_info, sizeof(int) * n_inst * c->pq_parts);
   if (ok) {
-    size_t wb = 0;
+    size_t wb = 0, wb2 = 0;
     ehl_paqif_workspace_size(n_inst, c->n, c->beta, 0, &wb);
-    c->pq_ws_bytes = wb;
-    A(&c->pq_ws, wb);
+    ehl_paqif_workspace_size(n_inst * c->pq_parts, c->n / c->pq_parts, c->beta, 0, &wb2);
+    c->pq_ws_bytes = wb > wb2 ? wb : wb2;
+    A(&c->pq_ws, c->pq_ws_bytes);
   }
   if (ok && c->method == 1 && line_nk_alloc(c) != cudaSuccess) ok = false;
   if (!ok) {

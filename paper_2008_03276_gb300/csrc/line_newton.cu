@@ -417,7 +417,7 @@ cudaError_t line_nk_alloc(LineCtx* c) {
             {(void**)&b->lsdone, sizeof(int) * ni},
             {(void**)&b->lsphase, sizeof(int) * ni},
             {(void**)&b->skip, sizeof(int) * ni},
-            {(void**)&b->fstore, paqif_factor_store_bytes(ni, c->n, c->beta)}};
+            {(void**)&b->fstore, paqif_factor_store_bytes(ni * c->pq_parts, c->n / c->pq_parts, c->beta)}};
   for (auto& x : al) {
     cudaError_t e = ctx_alloc(c, x.p, x.bytes);
     if (e != cudaSuccess) return e;
@@ -433,8 +433,11 @@ cudaError_t line_nk_alloc(LineCtx* c) {
 static cudaError_t paqif_on(LineCtx* c, const double* rhs, double* x, bool factor) {
   NkBuf& b = *(NkBuf*)c->nk;
   PaqifLaunch L;
-  L.n_sys = c->n_inst;
-  L.n = c->n;
+  // pq_parts diagonal blocks per band, consecutive rows: the band rows of block p
+  // start at row p n/r, and entries that couple to other blocks fall outside the
+  // block's matrix, so PAQIF ignores them (block Jacobi)
+  L.n_sys = c->n_inst * c->pq_parts;
+  L.n = c->n / c->pq_parts;
   L.beta = c->beta;
   L.mode = 0;
   L.band = c->band;

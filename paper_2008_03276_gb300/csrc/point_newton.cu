@@ -600,6 +600,19 @@ cudaError_t pt_nk_step(PtCtx* c, double* P, double* H0, const double* rough) {
       if (e != cudaSuccess) return e;
     }
   }
+  std::vector<int> tk, tc;
+  std::vector<double> tphin;
+  if (c->trace) {
+    const int nt = c->trace < ni ? c->trace : ni;
+    tk.resize(nt);
+    tc.resize(nt);
+    tphin.resize(nt);
+    e = cudaMemcpyAsync(tk.data(), c->gm_k, sizeof(int) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tc.data(), c->gm_conv, sizeof(int) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tphin.data(), c->phinorm, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e != cudaSuccess) return e;
+  }
   k_pn_ysolve<<<ni, kNB, 0, c->st>>>(vd);
   note_launch();
   k_pn_delta<<<gv, kNB, 0, c->st>>>(vd);
@@ -620,6 +633,21 @@ cudaError_t pt_nk_step(PtCtx* c, double* P, double* H0, const double* rough) {
     note_launch();
     if (pn_all(c, c->done, c->lsdone, e)) break;
     if (e != cudaSuccess) return e;
+  }
+  if (c->trace) {
+    const int nt = (int)tk.size();
+    std::vector<double> tt(nt), tred(4 * nt);
+    std::vector<int> tph(nt), tdone(nt), tit(nt);
+    e = cudaMemcpyAsync(tt.data(), c->tstep, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tph.data(), c->lsphase, sizeof(int) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tdone.data(), c->done, sizeof(int) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tit.data(), c->iters, sizeof(int) * nt, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return e;
+    for (int z = 0; z < nt; ++z)
+      if (!tdone[z])
+        fprintf(stderr, "ehl pt %dx%d inst %d it %d |Phi| %.3e gmres %d conv %d t %.3e phase %d\n", c->nx, c->ny, z,
+                tit[z], tphin[z], tk[z], tc[z], tt[z], tph[z]);
   }
   return cudaGetLastError();
 }
