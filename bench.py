@@ -13,8 +13,11 @@ Workload: the high-load line-contact configuration.  One step is
       half-width 8, Newton-Krylov with the PAQIF band preconditioner, from
       the Hertzian start to ||min(P,R)||_inf <= 1e-8 and |h sum P - pi/2| <= 1e-8.
 `value` is converged solves per second of leg B; leg A's GB/s and its HBM
-roofline are reported under "paqif" and "roofline".  All inputs are
-synthetic; nothing is read from disk.
+roofline are reported under "paqif" and "roofline".  After the timed steps,
+"configs" holds one measurement of each remaining configuration (the paper's
+load with both methods, the ragged batch of 512, point contact at 257^2 and
+the adjoint batch; --no-configs skips them).  All inputs are synthetic;
+nothing is read from disk.
 
 Timing: a barrier and torch.cuda.synchronize() bracket the K timed steps;
 each leg is timed with CUDA events on the launching stream.  Leg A moves
@@ -292,9 +295,99 @@ def run_ours(args):
         "clocks": clk.summary(),
         "wall_s": round(wall, 3),
     }
+    if world == 1 and not args.no_configs:
+        line["configs"] = config_legs(ops, inputs, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(band_h, rhs_h, budget_s=args.cpu_seconds)
     return line
+
+
+# ------------------------------------------------------------- the other configs
+def _timed(torch, fn, reps=1, warm=1):
+    """CUDA-event time (ms, best of reps) of fn() after warm calls, and fn's last result."""
+    out = None
+    for _ in range(warm):
+        out = fn()
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return best, out
+
+
+def config_legs(ops, inputs, torch, dev):
+    """One measurement per remaining configuration, outside the K timed steps:
+    C1 (the paper's load, both methods), C3 (ragged batch of 512), C4 (point
+    contact 257^2) and C5 (adjoint gradients of H_min, batch of 64)."""
+    res = {}
+
+    def summary(it, rs, code, tol):
+        it = it.cpu().numpy()
+        r = np.abs(rs.cpu().numpy())
+        return dict(newton_iters_min_max=[int(it.min()), int(it.max())], max_final_residual=float(r.max()),
+                    converged=int(np.sum((r[:, 0] <= 10 * tol) & (r[:, 1] <= 10 * tol))), status=int(code))
+
+    # C1: N = 129, M = 20, L = 10, minmod, beta 2, one instance
+    for method in (0, 1):
+        p = ops.default_params(1, nx=129, M=20.0, L=10.0, limiter=0, halfband=2, method=method, tol=1e-8,
+                               max_iter=4000 if method == 0 else 60)
+        ctx = ops.Context(p)
+        ms, out = _timed(torch, lambda: ctx.solve(check=False), reps=5)
+        d = dict(workload="line N=129, M=20, L=10, minmod, beta=2, 1 instance, tol 1e-8",
+                 method=("paper relaxation" if method == 0 else "Newton-Krylov"), ms=round(ms, 3),
+                 solves_per_s=round(1e3 / ms, 2))
+        d.update(summary(out[2], out[3], out[4], 1e-8))
+        res[f"C1_method{method}"] = d
+    # C3: 512 instances, M log-uniform [10, 1000], L uniform [5, 20], N from {257, ..., 2049}
+    per = inputs.batched_line_params(512, seed=1)
+    kw = dict(limiter=0, halfband=2, method=1, tol=1e-8, max_iter=60)
+    pp = [ops.default_params(1, nx=q["N"], M=q["M"], L=q["L"], **kw) for q in per]
+    ctx = ops.Context(pp[0], n_inst=len(pp), per_inst=pp)
+    ms, out = _timed(torch, lambda: ctx.solve(check=False))
+    d = dict(workload="ragged batch: 512 line instances, N from {257, 513, 1025, 2049}, M 10^U(1,3), L U(5,20), "
+                      "minmod, beta=2, tol 1e-8 (seed 1)", ms=round(ms, 2), solves_per_s=round(512e3 / ms, 2))
+    d.update(summary(out[2], out[3], out[4], 1e-8))
+    res["C3"] = d
+    del ctx
+    # C4: point contact 257 x 257, M = 100, L = 10, minmod, beta 2
+    p = ops.default_params(2, nx=257, ny=257, M=100.0, L=10.0, limiter=0, halfband=2, method=1, tol=1e-8,
+                           max_iter=60, coarse_min_nodes=33)
+    ctx = ops.Context(p)
+    ms, out = _timed(torch, lambda: ctx.solve(check=False), warm=0)
+    d = dict(workload="point contact 257x257, M=100, L=10, minmod, beta=2 (x-line PAQIF preconditioner), "
+                      "tol 1e-8, nested 33-65-129-257", ms=round(ms, 1), solves_per_s=round(1e3 / ms, 4))
+    d.update(summary(out[2], out[3], out[4], 1e-8))
+    res["C4"] = d
+    del ctx
+    # C5: adjoint, N = 1025, M = 50, L = 10, batch 64, roughness 0.1 sin(2 pi X/0.25) + field (0.05, 0.1)
+    N, n = 1025, 64
+    X = np.linspace(-4.5, 1.5, N)
+    rgh = np.stack([inputs.sin_grf_roughness(X, seed=2 + k, amp=0.1, wavelength=0.25, sigma=0.05, corr=0.1)
+                    for k in range(n)])
+    rough = torch.tensor(rgh, device=dev)
+    p = ops.default_params(1, nx=N, M=50.0, L=10.0, limiter=1, halfband=8, method=1, tol=1e-10, max_iter=80)
+    ctx = ops.Context(p, n_inst=n)
+    P, H0, it, rs, code = ctx.solve(rough=rough, check=False)
+    _, H, _ = ctx.residual(P, H0, rough)
+    gH = torch.zeros_like(P)
+    gH[torch.arange(n, device=dev), H.argmin(dim=1)] = 1.0
+    ms, out = _timed(torch, lambda: ctx.adjoint(P, H0, None, gH, None, rough=rough, tol=1e-10, max_cycles=20,
+                                                check=False))
+    rr = np.abs(rs.cpu().numpy())
+    conv = (rr[:, 0] <= 1e-8) & (rr[:, 1] <= 1e-8)
+    rel = out[2].cpu().numpy()
+    res["C5"] = dict(workload="adjoint of H_min w.r.t. roughness and (M, L): line N=1025, M=50, L=10, van Leer, "
+                              "beta=8, batch 64, roughness 0.1 sin(2 pi X/0.25) + GRF(0.05, 0.1), seeds 2..65",
+                     ms=round(ms, 2), gradients_per_s=round(n * 1e3 / ms, 2), forward_converged=int(conv.sum()),
+                     contact_instances=int(np.sum(H.min(dim=1).values.cpu().numpy() <= 0.0)),
+                     adjoint_relres_le_1e_8=int(np.sum(rel[conv] <= 1e-8)))
+    return res
 
 
 # --------------------------------------------------------------------------- oracle
@@ -373,6 +466,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the one-shot C1/C3/C4/C5 measurements")
     ap.add_argument("--ref-systems", type=int, default=4)
     ap.add_argument("--ehl-batch", type=int, default=512, help="line-contact instances solved per step")
     ap.add_argument("--paqif-nsys", type=int, default=PAQIF_NSYS,

@@ -151,7 +151,7 @@ typedef struct {
                         /* 1: Newton-Krylov, PAQIF band preconditioner (default)         */
   double tol;           /* converged when ||min(P,R)||_inf <= tol and |h sum P - pi/2| <= tol */
   int max_iter;         /* cap on outer iterations                                      */
-  int krylov_dim;       /* GMRES basis size per Newton step (method 1)                  */
+  int krylov_dim;       /* GMRES basis size per Newton step (method 1; 40 line, 100 point) */
   double h_init;        /* Hertzian start: H0 chosen so that min H = h_init             */
   int levels;           /* nested iteration: coarse grids solved first (init = 0 only);  */
                         /*   -1 as many as allowed (default), 0 none                     */
