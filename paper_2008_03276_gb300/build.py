@@ -64,7 +64,8 @@ def build(verbose=False, force=False):
     with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 4))) as ex:
         list(ex.map(run, cmds))
     tmp = LIB + ".tmp"
-    run([nv, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nv))), "lib64")
+    run([nv, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas", "-Xlinker", "-rpath", "-Xlinker", cuda_lib])
     os.replace(tmp, LIB)
     return LIB
 

@@ -1,6 +1,7 @@
 // line.cu -- line-contact hot path (Sec. 3.3): closed-form kernel table,
 // double-float Toeplitz deformation, float64 lubricant model and TVD residual,
 // the band Jacobians, and the paper's limiter-based Newton-Raphson relaxation.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kDefTI) k_line_deform64(const LineInst* __rest
 }
 
 // mode 0: H = H0 + X^2/2 - D + rough;  mode 1: out = -D + dh0 (directional derivative of H)
-// partial holds float64 chunk sums when p64 is set, double-float ones otherwise
+// partial holds float64 chunk sums (p64 = 1), double-float ones (0) or one float32 product (2)
 __global__ void k_line_film(const LineInst* __restrict__ inst, const float2* __restrict__ partial, int ksplit,
                             const double* __restrict__ H0, const double* __restrict__ rough, int rstride,
                             const int* __restrict__ skip, double* __restrict__ out, int n_inst, int N, int mode,
@@ -143,7 +144,9 @@ __global__ void k_line_film(const LineInst* __restrict__ inst, const float2* __r
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double Dd;
-  if (p64) {
+  if (p64 == 2) {  // one float32 product [n_inst][N] (the GEMM of the mixed-precision Krylov products)
+    Dd = (double)reinterpret_cast<const float*>(partial)[(size_t)z * N + i];
+  } else if (p64) {
     const double* pd = reinterpret_cast<const double*>(partial);
     Dd = 0.0;
     for (int y = 0; y < ksplit; ++y) Dd += pd[((size_t)y * n_inst + z) * N + i];
@@ -698,6 +701,78 @@ cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double
 }  // namespace ehl
 
 namespace ehl {
+// ------------------------------------------------ mixed-precision Krylov products
+// K as a dense float32 matrix (column-major, symmetric) from the float64 table of instance 0
+__global__ void k_line_kfull(const double* __restrict__ gtab64, float* __restrict__ Kf, int N) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)N * N) return;
+  const int i = (int)(t % N), k = (int)(t / N);
+  Kf[t] = (float)gtab64[i > k ? i - k : k - i];
+}
+
+__global__ void k_line_to_f32(const double* __restrict__ V, int vstride, float* __restrict__ Vf, int N) {
+  const int z = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) Vf[(size_t)z * N + i] = (float)V[(size_t)z * vstride + i];
+}
+
+cudaError_t line_mixed_init(LineCtx* c, int precision) {
+  c->precision = 0;
+  if (precision <= 0) return cudaSuccess;
+  // one K for the bucket: every instance must share the grid spacing
+  for (const LineInst& q : c->h_inst)
+    if (q.h != c->h_inst[0].h || q.elastic != c->h_inst[0].elastic) return cudaSuccess;
+  if (!c->h_inst[0].elastic) return cudaSuccess;
+  const size_t NN = (size_t)c->N * c->N, NI = (size_t)c->N * c->n_inst;
+  cudaError_t e = ctx_alloc(c, (void**)&c->Kf, sizeof(float) * NN);
+  if (e == cudaSuccess) e = ctx_alloc(c, (void**)&c->Vf, sizeof(float) * NI);
+  if (e == cudaSuccess) e = ctx_alloc(c, (void**)&c->Df, sizeof(float) * NI);
+  if (e != cudaSuccess) return e;
+  if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+  cublasSetStream(c->blas, c->st);
+  cublasSetMathMode(c->blas, CUBLAS_DEFAULT_MATH);
+  k_line_kfull<<<(unsigned)((NN + 255) / 256), 256, 0, c->st>>>(c->gtab64, c->Kf, c->N);
+  note_launch();
+  c->precision = precision;
+  return cudaGetLastError();
+}
+
+void line_mixed_free(LineCtx* c) {
+  if (c->blas) cublasDestroy(c->blas);
+  c->blas = nullptr;
+}
+
+// dH = -K v + zh0 for the Krylov vectors: the double-float Toeplitz kernel, or
+// with precision > 0 one float32-output GEMM K [N x N] . V [N x n_inst] of the
+// whole bucket (precision 1 float32, 2 float32 emulated on BF16 tensor cores,
+// 3 TF32, 4 BF16 tensor cores).
+cudaError_t line_krylov_deform(LineCtx* c, const double* V, const double* zh0, const int* skip) {
+  if (c->precision <= 0) {
+    cudaError_t e = line_deform(c, V, c->N, skip);
+    if (e == cudaSuccess) e = line_film_dir(c, zh0, skip);
+    return e;
+  }
+  const int N = c->N, ni = c->n_inst;
+  dim3 g((N + 255) / 256, ni);
+  k_line_to_f32<<<g, 256, 0, c->st>>>(V, N, c->Vf, N);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cublasComputeType_t ct = CUBLAS_COMPUTE_32F;
+  if (c->precision == 2) ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+  if (c->precision == 3) ct = CUBLAS_COMPUTE_32F_FAST_TF32;
+  if (c->precision == 4) ct = CUBLAS_COMPUTE_32F_FAST_16BF;
+  const float one = 1.0f, zero = 0.0f;
+  if (cublasGemmEx(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, N, ni, N, &one, c->Kf, CUDA_R_32F, N, c->Vf, CUDA_R_32F, N,
+                   &zero, c->Df, CUDA_R_32F, N, ct, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+    return cudaErrorUnknown;
+  dim3 gn((N + kNodeBlock - 1) / kNodeBlock, ni);
+  k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, reinterpret_cast<const float2*>(c->Df), 1, zh0, nullptr, N,
+                                             skip, c->dH, ni, N, 1, 2);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t line_film_dir(LineCtx* c, const double* zh0, const int* skip, bool p64) {
   dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
   k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->partial, c->ksplit, zh0, nullptr, c->N, skip, c->dH,

@@ -1,5 +1,6 @@
 // line.h -- host-side state and stage launchers of the line-contact path.
 #pragma once
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,6 +29,10 @@ struct LineCtx {
   size_t pq_ws_bytes = 0;
   int* pq_info = nullptr;
   int pq_parts = 1;  // Krylov preconditioner: PAQIF blocks per band (block Jacobi)
+  // mixed-precision Krylov products (precision > 0): dense float32 K, vectors, products
+  int precision = 0;
+  cublasHandle_t blas = nullptr;
+  float *Kf = nullptr, *Vf = nullptr, *Df = nullptr;
   double *Pw = nullptr, *H0w = nullptr, *dH = nullptr;
   int *done = nullptr, *iters = nullptr;
   double* best = nullptr;  // smallest ||min(P,R)||_inf seen (stall test of the rounding-floor stop)
@@ -77,5 +82,9 @@ cudaError_t line_adjoint(LineCtx* c, const double* P, const double* H0, const do
                          const double* gH, const double* gH0, double* grad_rough, double* grad_ML, double* relres,
                          double tol, int max_cycles, int* cycles);
 void line_adj_free(LineCtx* c);
+// Krylov products dH = -K v + zh0 (double-float, or a float32-output GEMM with precision > 0)
+cudaError_t line_mixed_init(LineCtx* c, int precision);
+void line_mixed_free(LineCtx* c);
+cudaError_t line_krylov_deform(LineCtx* c, const double* V, const double* zh0, const int* skip);
 
 }  // namespace ehl

@@ -98,6 +98,7 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   p->coarse_min_nodes = 65;
   p->coarse_tol = 1e-4;
   p->precond_blocks = 1;
+  p->precision = 0;
 }
 
 static bool point_grid_ok(const ehl_params& p) {
@@ -112,7 +113,7 @@ static bool params_ok(const ehl_params& p) {
          (p.method == 0 || p.method == 1) && p.max_iter >= 1 && p.krylov_dim >= 1 && p.krylov_dim <= 200 &&
          p.tol > 0.0 && isfinite(p.h_init) && isfinite(p.c_h0) && isfinite(p.omega) && isfinite(p.dist_weight) &&
          isfinite(p.switch_eps_h) && p.levels >= -1 && p.coarse_min_nodes >= 5 && p.coarse_tol > 0.0 &&
-         p.precond_blocks >= 1 && p.precond_blocks <= 4096;
+         p.precond_blocks >= 1 && p.precond_blocks <= 4096 && p.precision >= 0 && p.precision <= 4;
 }
 
 static LineInst make_inst(const ehl_params& p) {
@@ -147,6 +148,7 @@ static void free_all(LineCtx* c) {
   c->allocs.clear();
   if (c->nk) line_nk_free(c);
   if (c->adj) line_adj_free(c);
+  line_mixed_free(c);
 }
 
 static void free_bucket(Bucket* b) {
@@ -233,6 +235,7 @@ static ehl_status init_line(LineCtx* c, const std::vector<LineInst>& insts, int 
   cudaError_t e = cudaMemcpyAsync(c->inst, c->h_inst.data(), sizeof(LineInst) * n_inst, cudaMemcpyHostToDevice,
                                   c->st);
   if (e == cudaSuccess) e = line_init_tables(c);
+  if (e == cudaSuccess && c->method == 1) e = line_mixed_init(c, p.precision);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return EHL_ECUDA;
@@ -457,6 +460,7 @@ extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_para
     p0.method = p->method;
     p0.levels = p->levels;
     p0.coarse_min_nodes = p->coarse_min_nodes;
+    p0.precision = p->precision;
     const ehl_status st = init_bucket(b, p0, ps, !ctx->direct);
     if (st != EHL_OK) {
       free_ctx(ctx);

@@ -483,9 +483,7 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
     if (e != cudaSuccess) return e;
     k_nk_prec<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, b.skip, N);
     note_launch();
-    e = line_deform(c, b.znode, N, b.skip);
-    if (e != cudaSuccess) return e;
-    e = line_film_dir(c, b.zh0, b.skip);
+    e = line_krylov_deform(c, b.znode, b.zh0, b.skip);
     if (e != cudaSuccess) return e;
     JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, b.znode};
     k_nk_jv<<<gn, 256, 0, c->st>>>(c->inst, b, q, c->act, c->dg, b.skip, N);

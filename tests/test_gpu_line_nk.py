@@ -94,3 +94,22 @@ def test_nested_iteration_low_load_van_leer(rough):
           f"oracle levels {info['levels']}")
     assert code == 0 and iters[0] < 20
     check(P[0], H0[0], pb, Pr, H0r)
+
+
+@pytest.mark.parametrize("precision", [1, 2, 3])
+def test_mixed_precision_krylov_products(precision):
+    """Krylov products as a float32-output GEMM (1 float32, 2 float32 on BF16 tensor cores, 3 TF32):
+    the residual stays float64, so the converged solution matches the oracle as tightly."""
+    N, M, L = 513, 200.0, 10.0
+    pb = lr.LineProblem(N, M, L, limiter="vanleer")
+    Pr, H0r, info = lr.solve(pb)
+    assert info["converged"]
+    per = [dict(M=M, L=L)] * 4
+    kw = dict(limiter=1, halfband=8, method=1, tol=1e-10, max_iter=60, krylov_dim=40, precision=precision)
+    p = ops.default_params(1, nx=N, M=M, L=L, **kw)
+    ctx = ops.Context(p, n_inst=4, per_inst=[ops.default_params(1, nx=N, **kw, **d) for d in per])
+    P, H0, iters, res, code = ctx.solve(check=False)
+    assert code == 0, (code, iters.tolist())
+    P, H0 = P.cpu().numpy(), H0.cpu().numpy()
+    for k in range(4):
+        check(P[k], H0[k], pb, Pr, H0r)
