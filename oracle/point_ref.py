@@ -115,13 +115,20 @@ def comp_residual(pb, P_int, H0):
     return np.max(np.abs(np.minimum(P_int, R))), pb.h**2 * np.sum(P_int) - pb.load
 
 
-def _tangent(pb, s, dH, dP):
-    """``dR`` (interior, flattened) for the perturbations ``dH``, ``dP`` ([nx, ny, c]) of H and P."""
+def _tangent(pb, s, dH, dP, dlnpH=None, dlnlam=None):
+    """``dR`` (interior, flattened) for the perturbations ``dH``, ``dP`` ([nx, ny, c]) of H and P,
+    and optionally of ``ln p_H`` and ``ln lambda`` (``[c]``; rho and eta depend on ``P p_H``, so
+    ``d/d ln p_H = P d/dP``)."""
     h = pb.h
     H, rho, eps, P = s["H"], s["rho"], s["eps"], s["P"]
     drho = s["drho"][..., None] * dP
     dlneta = (s["deta"] / s["eta"])[..., None] * dP
+    if dlnpH is not None:
+        drho = drho + (s["drho"] * P)[..., None] * dlnpH
+        dlneta = dlneta + (s["deta"] / s["eta"] * P)[..., None] * dlnpH
     deps = eps[..., None] * (drho / rho[..., None] + 3.0 * dH / H[..., None] - dlneta)
+    if dlnlam is not None:
+        deps = deps - eps[..., None] * dlnlam
     du = drho * H[..., None] + rho[..., None] * dH
     dF = du[:-1].copy()
     pa, pbb = s["psi_a"], s["psi_b"]
@@ -255,3 +262,43 @@ def solve_nested(pb_factory, nx, ny, n_min=17, tol=1e-12, coarse_tol=1e-6, **kw)
         prev = pb
     info["levels"] = out
     return pb, P, H0, info
+
+
+# ------------------------------------------------------------------- adjoint
+def moes_point_log_derivatives(M, L):
+    """``d ln(lambda)/d(M, L)`` and ``d ln(p_H)/d(M, L)`` for the point-contact conversion."""
+    return np.array([-4.0 / (3.0 * M), 0.0]), np.array([1.0 / (3.0 * M), 1.0 / L])
+
+
+def adjoint(pb, P_int, H0, gP, gH, gH0):
+    """Gradient of ``J(P, H, H0)`` w.r.t. the roughness (nodal ``[nx, ny]``), ``M`` and ``L``.
+
+    As the line-contact adjoint (``adjoint_ref.adjoint``) on the point problem:
+    equation rows ``P_i > R_i / |dR_ii/dP_ii|``, bordered with the force row
+    ``h^2``, dense LU of the transpose.  ``gP``, ``gH`` are nodal ``[nx, ny]``.
+    Meant for small grids (the roughness tangent is dense).
+    """
+    nx, ny, n, NN = pb.nx, pb.ny, pb.n, pb.nx * pb.ny
+    Kd = pb.deform_matrix()
+    J, JH = jacobian_exact(pb, P_int, H0, Kd)
+    R = residual(pb, P_int, H0)
+    d = np.abs(np.diag(J))
+    d = np.where(d > 0.0, d, 1.0)
+    A = np.nonzero(P_int > R / d)[0]
+    na = len(A)
+    s = state(pb, P_int, H0)
+    Trough = _tangent(pb, s, np.eye(NN).reshape(nx, ny, NN), np.zeros((nx, ny, NN)))   # [n, NN]
+    dlam, dpH = moes_point_log_derivatives(pb.M, pb.L)
+    TML = _tangent(pb, s, np.zeros((nx, ny, 2)), np.zeros((nx, ny, 2)), dlnpH=dpH, dlnlam=dlam)  # [n, 2]
+    Fx = np.zeros((na + 1, na + 1))
+    Fx[:na, :na] = J[np.ix_(A, A)]
+    Fx[:na, na] = JH[A]
+    Fx[na, :na] = pb.h**2
+    gP = np.asarray(gP, dtype=np.float64)
+    gH = np.asarray(gH, dtype=np.float64)
+    gPt = gP[1:-1, 1:-1].ravel() + Kd.T @ gH.ravel()
+    gH0t = float(gH0) + float(np.sum(gH))
+    lam = np.linalg.solve(Fx.T, np.concatenate([gPt[A], [gH0t]]))
+    grad_rough = gH.ravel() - lam[:na] @ Trough[A]
+    gML = -(lam[:na] @ TML[A])
+    return dict(rough=grad_rough.reshape(nx, ny), M=float(gML[0]), L=float(gML[1]), rows=A)

@@ -109,3 +109,42 @@ def test_point_nested_matches_direct(solved_33):
     assert inf["converged"] and [l[0] for l in inf["levels"]] == [(17, 17), (33, 33)]
     assert np.max(np.abs(Pn - P)) <= 1e-8 * np.max(P)
     assert abs(H0n - H0) <= 1e-8 * abs(H0)
+
+
+def test_point_parameter_tangents_vs_residual_differences(solved_33):
+    pb, P, H0, info = solved_33
+    s = pr.state(pb, P, H0)
+    dlam, dpH = pr.moes_point_log_derivatives(pb.M, pb.L)
+    T = pr._tangent(pb, s, np.zeros((pb.nx, pb.ny, 2)), np.zeros((pb.nx, pb.ny, 2)), dlnpH=dpH, dlnlam=dlam)
+    for k, (dM, dL) in enumerate([(1e-6 * pb.M, 0.0), (0.0, 1e-6 * pb.L)]):
+        Rp = pr.residual(pr.PointProblem(pb.nx, pb.ny, pb.M + dM, pb.L + dL), P, H0)
+        Rm = pr.residual(pr.PointProblem(pb.nx, pb.ny, pb.M - dM, pb.L - dL), P, H0)
+        fd = (Rp - Rm) / (2 * (dM + dL))
+        assert np.max(np.abs(fd - T[:, k])) <= 1e-6 * max(1.0, np.max(np.abs(fd)))
+
+
+@pytest.mark.slow
+def test_point_adjoint_vs_resolved_differences(solved_33):
+    pb, P, H0, info = solved_33
+    c = (int(np.argmin(np.abs(pb.X))), int(np.argmin(np.abs(pb.Y))))
+    gH = np.zeros((pb.nx, pb.ny))
+    gH[c] = 1.0                                   # H_c = H at (0, 0)
+    g = pr.adjoint(pb, P, H0, np.zeros_like(gH), gH, 0.0)
+
+    def hc(M=pb.M, L=pb.L, rough=None):
+        q = pr.PointProblem(pb.nx, pb.ny, M, L, rough=rough)
+        Pq, H0q, inf = pr.solve(q, P_init=P, H0_init=H0, tol=1e-12)
+        assert inf["converged"]
+        return q.film(Pq, H0q)[c]
+
+    d = 1e-6
+    for node in ((c[0], c[1]), (c[0] - 3, c[1] + 2)):
+        rp, rm = np.zeros((pb.nx, pb.ny)), np.zeros((pb.nx, pb.ny))
+        rp[node] += d
+        rm[node] -= d
+        fd = (hc(rough=rp) - hc(rough=rm)) / (2 * d)
+        assert abs(fd - g["rough"][node]) <= 1e-5 * abs(fd) + 1e-7 * np.max(np.abs(g["rough"]))
+    fd = (hc(M=pb.M * (1 + d)) - hc(M=pb.M * (1 - d))) / (2 * d * pb.M)
+    assert abs(fd - g["M"]) <= 1e-5 * abs(fd)
+    fd = (hc(L=pb.L * (1 + d)) - hc(L=pb.L * (1 - d))) / (2 * d * pb.L)
+    assert abs(fd - g["L"]) <= 1e-5 * abs(fd)
