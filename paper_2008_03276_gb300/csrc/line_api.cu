@@ -817,7 +817,26 @@ extern "C" ehl_status ehl_adjoint(ehl_ctx* ctx, const double* P, const double* H
                                   const double* gP, const double* gH, const double* gH0, double* grad_rough,
                                   double* grad_ML, double* relres, double tol, int max_cycles) {
   if (!ctx || !P || !H0 || !(tol > 0.0) || max_cycles < 1 || max_cycles > 1000) return EHL_EINVAL;
-  if (ctx->pt) return EHL_EINVAL;  // the point-contact adjoint is not built
+  if (ctx->pt) {
+    PtCtx* c = ctx->pt;
+    std::vector<double> h(c->n_inst);
+    double* rel = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&rel, sizeof(double) * c->n_inst, c->st);
+    if (e == cudaSuccess)
+      e = pt_adjoint(c, P, H0, rough, gP, gH, gH0, grad_rough, grad_ML, rel, tol, max_cycles);
+    if (e == cudaSuccess && relres)
+      e = cudaMemcpyAsync(relres, rel, sizeof(double) * c->n_inst, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), rel, sizeof(double) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
+    if (rel) cudaFreeAsync(rel, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    bool nonfinite = false, noconv = false;
+    for (double v : h) {
+      nonfinite = nonfinite || !(v == v);
+      noconv = noconv || v > tol;
+    }
+    return nonfinite ? EHL_ENONFINITE : (noconv ? EHL_ENOCONV : EHL_OK);
+  }
   cudaError_t e = fork(ctx);
   for (Bucket* b : ctx->buckets) {
     LineCtx* c = &b->c;

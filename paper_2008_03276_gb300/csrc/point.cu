@@ -547,6 +547,7 @@ cudaError_t pt_alloc(PtCtx* c, void** p, size_t bytes) {
 void pt_free(PtCtx* c) {
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
+  pt_adj_free(c);
 }
 
 static PtRow pt_row(PtCtx* c, const double* P) {
@@ -701,6 +702,16 @@ cudaError_t pt_deform_dir(PtCtx* c, const double* zn, const double* zh0, const i
   if (e != cudaSuccess) return e;
   const dim3 gn((c->NN + kPtNode - 1) / kPtNode, c->n_inst);
   k_pt_film<<<gn, kPtNode, 0, c->st>>>(c->inst, c->partial, c->ksplit, 0, zh0, nullptr, skip, c->dH, c->n_inst, 1);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t pt_deform_dir64(PtCtx* c, const double* v, const int* skip) {
+  cudaError_t e = pt_deform(c, v, skip, true);
+  if (e != cudaSuccess) return e;
+  const dim3 gn((c->NN + kPtNode - 1) / kPtNode, c->n_inst);
+  k_pt_film<<<gn, kPtNode, 0, c->st>>>(c->inst, c->partial, c->ksplit, 1, nullptr, nullptr, skip, c->dH, c->n_inst,
+                                       1);
   note_launch();
   return cudaGetLastError();
 }

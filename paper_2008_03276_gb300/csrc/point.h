@@ -43,6 +43,7 @@ struct PtCtx {
   double* zh0 = nullptr;  // border component of the current preconditioned vector, per instance
   int *gm_k = nullptr, *gm_conv = nullptr, *lsdone = nullptr, *lsphase = nullptr, *skip = nullptr;
   int* acc = nullptr;     // line search: trial accepted in this pass
+  void* adj = nullptr;    // adjoint buffers (point_newton.cu), allocated on first use
   int trace = 0;
   std::vector<void*> allocs;
 };
@@ -64,6 +65,15 @@ cudaError_t pt_inject(const PtCtx* fine, const double* src, PtCtx* coarse, doubl
 cudaError_t pt_prolong(const PtCtx* coarse, PtCtx* fine);
 // dH = K zn + zh0 (double-float deformation; the Krylov products)
 cudaError_t pt_deform_dir(PtCtx* c, const double* zn, const double* zh0, const int* skip);
+// dH = K v in float64 (the adjoint's products)
+cudaError_t pt_deform_dir64(PtCtx* c, const double* v, const int* skip);
+// Adjoint of a converged point-contact state (point_newton.cu): gradients of J(P, H, H0) from its
+// partials gP, gH ([n_inst][ny][nx], nullable) and gH0 ([n_inst], nullable) with respect to the
+// roughness (grad_rough, nullable) and (M, L) (grad_ML [n_inst][2], nullable); relres [n_inst]
+cudaError_t pt_adjoint(PtCtx* c, const double* P, const double* H0, const double* rough, const double* gP,
+                       const double* gH, const double* gH0, double* grad_rough, double* grad_ML, double* relres,
+                       double tol, int max_cycles);
+void pt_adj_free(PtCtx* c);
 cudaError_t pt_nk_step(PtCtx* c, double* P, double* H0, const double* rough);
 
 }  // namespace ehl

@@ -652,4 +652,521 @@ cudaError_t pt_nk_step(PtCtx* c, double* P, double* H0, const double* rough) {
   return cudaGetLastError();
 }
 
+
+// ===================================================================== adjoint
+// Sensitivities of a converged point-contact state, as for line contact: the
+// transposed bordered system of the equation rows solved by restarted GMRES on
+// the exact transposed operator (the transposed 2-D stencil of the residual
+// plus one float64 deformation per product; K is symmetric and H = ... + K P),
+// preconditioned by PAQIF on the transposed x-line bands, with the force
+// column h^2 and the dR/dH0 row as border.
+namespace {
+
+struct PtAdj {
+  double *bandT = nullptr, *cb = nullptr, *hvec = nullptr, *zr = nullptr, *gx = nullptr, *mu = nullptr;
+  double *res = nullptr, *wn = nullptr, *gHn = nullptr, *gPn = nullptr, *relres = nullptr, *gxn = nullptr;
+  int* adone = nullptr;
+  void* fstore = nullptr;
+};
+
+struct PaNodes {
+  const double *P, *H, *rho, *drho, *deta_rel, *eps, *psia, *psib;
+};
+
+// adjoint of the node perturbations (dU, dE, zn) at node (p, q) for row weights wn
+__device__ __forceinline__ void pa_local(const PaNodes& q, const double* __restrict__ wn, size_t base, int p, int qq,
+                                         int nx, int ny, double h, double& aU, double& aE, double& aZ) {
+  auto W = [&](int i, int j) { return (i >= 0 && i < nx && j >= 0 && j < ny) ? wn[base + (size_t)j * nx + i] : 0.0; };
+  auto idx = [&](int i, int j) { return base + (size_t)j * nx + i; };
+  auto phx = [&](int f) { return (f >= 0 && f <= nx - 2) ? (W(f, qq) - W(f + 1, qq)) / h : 0.0; };
+  auto phy = [&](int g) { return (g >= 0 && g <= ny - 2) ? (W(p, g) - W(p, g + 1)) / h : 0.0; };
+  auto pa = [&](int f) { return (f >= 0 && f <= nx - 2) ? q.psia[idx(f, qq)] : 0.0; };
+  auto pb = [&](int f) { return (f >= 0 && f <= nx - 2) ? q.psib[idx(f, qq)] : 0.0; };
+  const double fm = phx(p), fm1 = phx(p - 1), fp1 = phx(p + 1);
+  aU = fm * (1.0 + 0.5 * pa(p) - 0.5 * pb(p)) - 0.5 * pa(p + 1) * fp1 + 0.5 * pb(p - 1) * fm1;
+  const double cx = -fm / h, cx1 = -fm1 / h;
+  const double dPx = (p <= nx - 2) ? q.P[idx(p + 1, qq)] - q.P[idx(p, qq)] : 0.0;
+  const double dPx1 = (p >= 1) ? q.P[idx(p, qq)] - q.P[idx(p - 1, qq)] : 0.0;
+  const double ex = (p <= nx - 2) ? 0.5 * (q.eps[idx(p, qq)] + q.eps[idx(p + 1, qq)]) : 0.0;
+  const double ex1 = (p >= 1) ? 0.5 * (q.eps[idx(p - 1, qq)] + q.eps[idx(p, qq)]) : 0.0;
+  const double cy = -phy(qq) / h, cy1 = -phy(qq - 1) / h;
+  const double dPy = (qq <= ny - 2) ? q.P[idx(p, qq + 1)] - q.P[idx(p, qq)] : 0.0;
+  const double dPy1 = (qq >= 1) ? q.P[idx(p, qq)] - q.P[idx(p, qq - 1)] : 0.0;
+  const double ey = (qq <= ny - 2) ? 0.5 * (q.eps[idx(p, qq)] + q.eps[idx(p, qq + 1)]) : 0.0;
+  const double ey1 = (qq >= 1) ? 0.5 * (q.eps[idx(p, qq - 1)] + q.eps[idx(p, qq)]) : 0.0;
+  aE = 0.5 * (cx * dPx + cx1 * dPx1) + 0.5 * (cy * dPy + cy1 * dPy1);
+  aZ = (cx1 * ex1 - cx * ex) + (cy1 * ey1 - cy * ey);
+}
+
+__global__ void k_pa_local(const PointInst* __restrict__ inst, PaNodes q, const double* __restrict__ wn,
+                           const int* __restrict__ skip, double* __restrict__ gHn, double* __restrict__ gPn) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  const PointInst in = inst[z];
+  const int nx = in.nx, ny = in.ny, NN = nx * ny;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NN) return;
+  const size_t base = (size_t)z * NN, o = base + t;
+  double aU, aE, aZ;
+  pa_local(q, wn, base, t % nx, t / nx, nx, ny, in.h, aU, aE, aZ);
+  const double e = q.eps[o], H = q.H[o], r = q.rho[o];
+  gHn[o] = aU * r + aE * 3.0 * e / H;
+  gPn[o] = aU * q.drho[o] * H + aE * e * (q.drho[o] / r - q.deta_rel[o]) + aZ;
+}
+
+__global__ void k_pa_prepare(PtView v, PtAdj a) {
+  const int z = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= v.n) return;
+  const int w = 2 * v.beta + 1;
+  const size_t o = (size_t)z * v.n + r;
+  if (!v.act[o]) {
+    const double d = v.dg[o];
+    double* row = v.band + o * w;
+    for (int t = 0; t < w; ++t) row[t] /= d;
+    a.cb[o] = v.jh[o] / d;
+  } else {
+    a.cb[o] = 0.0;
+  }
+  const double h = v.inst[z].h;
+  a.hvec[o] = h * h;
+}
+
+// transposed x-line bands: bandT[line][r][j] = band[line][r - beta + j][2 beta - j]
+__global__ void k_pa_transpose(PtView v, PtAdj a) {
+  const int z = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= v.n) return;
+  const int ni = v.nx - 2, beta = v.beta, w = 2 * beta + 1;
+  const int line = r / ni, rl = r % ni;
+  const double* B = v.band + ((size_t)z * v.n + (size_t)line * ni) * w;
+  double* T = a.bandT + ((size_t)z * v.n + r) * w;
+  for (int j = 0; j < w; ++j) {
+    const int sr = rl - beta + j;
+    T[j] = (sr >= 0 && sr < ni) ? B[(size_t)sr * w + (2 * beta - j)] : 0.0;
+  }
+}
+
+// gx[0:n] = gP + K gH (dH holds K gH), partial |gx|^2 in slot 0; partial sum gH over nodes in slot 1
+__global__ void __launch_bounds__(kNB) k_pa_rhs(PtView v, PtAdj a, const double* __restrict__ gP,
+                                                const double* __restrict__ gH, const double* __restrict__ dH) {
+  const int z = blockIdx.y;
+  __shared__ double sh[kNB];
+  double ss = 0.0, sH = 0.0;
+  NK_FOR(r, v.n) {
+    const size_t node = (size_t)z * v.NN + nk_node(r, v.nx);
+    const double g = (gP ? gP[node] : 0.0) + (gH ? dH[node] : 0.0);
+    a.gx[(size_t)z * v.n1 + r] = g;
+    ss += g * g;
+  }
+  // nodes by a grid-stride loop (NN exceeds the interior count the vector blocks cover)
+  if (gH)
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < v.NN; t += gridDim.x * blockDim.x)
+      sH += gH[(size_t)z * v.NN + t];
+  ss = nk_block_sum(ss, sh);
+  sH = nk_block_sum(sH, sh);
+  if (threadIdx.x == 0) {
+    double* d = v.dots + ((size_t)z * v.nvb + blockIdx.x) * (v.m + 2);
+    d[0] = ss;
+    d[1] = sH;
+  }
+}
+
+__global__ void __launch_bounds__(kNB) k_pa_rhs2(PtView v, PtAdj a, const double* __restrict__ gH0) {
+  const int z = blockIdx.x;
+  __shared__ double sh[kNB];
+  const double ss = pn_total(v, z, 0, sh), sH = pn_total(v, z, 1, sh);
+  if (threadIdx.x == 0) {
+    const double gn = (gH0 ? gH0[z] : 0.0) + sH;
+    a.gx[(size_t)z * v.n1 + v.n] = gn;
+    a.gxn[z] = sqrt(ss + gn * gn);
+    a.adone[z] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kNB) k_pa_init(PtView v, PtAdj a) {
+  const int z = blockIdx.y;
+  NK_FOR(r, v.n1) {
+    a.mu[(size_t)z * v.n1 + r] = 0.0;
+    a.res[(size_t)z * v.n1 + r] = a.gx[(size_t)z * v.n1 + r];
+  }
+}
+
+// partial sum of cb . x[0:n] into slot 0 (x of instance z at x + z xstride)
+__global__ void __launch_bounds__(kNB) k_pa_cdot(PtView v, PtAdj a, const double* __restrict__ x, size_t xstride,
+                                                 const int* __restrict__ skip) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  __shared__ double sh[kNB];
+  double s = 0.0;
+  NK_FOR(r, v.n) s += a.cb[(size_t)z * v.n + r] * x[(size_t)z * xstride + r];
+  s = nk_block_sum(s, sh);
+  if (threadIdx.x == 0) v.dots[((size_t)z * v.nvb + blockIdx.x) * (v.m + 2)] = s;
+}
+
+__global__ void __launch_bounds__(kNB) k_pa_den(PtView v, PtAdj a) {
+  const int z = blockIdx.x;
+  __shared__ double sh[kNB];
+  const double s = pn_total(v, z, 0, sh);
+  if (threadIdx.x == 0) v.den[z] = fabs(s) > 1e-300 ? s : 1e-300;
+}
+
+// restart: |res| (after partial sums of res^2 in slot 0), V_0 = res/|res|, GMRES state
+__global__ void __launch_bounds__(kNB) k_pa_norm_res(PtView v, PtAdj a) {
+  const int z = blockIdx.y;
+  if (a.adone[z]) return;
+  __shared__ double sh[kNB];
+  double s = 0.0;
+  NK_FOR(r, v.n1) {
+    const double x = a.res[(size_t)z * v.n1 + r];
+    s += x * x;
+  }
+  s = nk_block_sum(s, sh);
+  if (threadIdx.x == 0) v.dots[((size_t)z * v.nvb + blockIdx.x) * (v.m + 2)] = s;
+}
+
+__global__ void __launch_bounds__(kNB) k_pa_start2(PtView v, PtAdj a, double tol, int* __restrict__ skip) {
+  const int z = blockIdx.x;
+  __shared__ double sh[kNB];
+  const double nrm = a.adone[z] ? 0.0 : sqrt(pn_total(v, z, 0, sh));
+  if (threadIdx.x == 0) {
+    v.g[(size_t)z * (v.m + 1)] = nrm;
+    v.gm_k[z] = 0;
+    v.beta0[z] = a.gxn[z];
+    v.rtol[z] = 0.1 * tol;
+    v.gm_conv[z] = (a.adone[z] || nrm <= 0.1 * tol * a.gxn[z]) ? 1 : 0;
+    skip[z] = v.gm_conv[z];
+    v.hcol[(size_t)z * (v.m + 2) + v.m + 1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kNB) k_pa_v0(PtView v, PtAdj a) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  const double s = v.hcol[(size_t)z * (v.m + 2) + v.m + 1];
+  double* V0 = v.V + (size_t)z * (v.m + 1) * v.n1;
+  NK_FOR(r, v.n1) {
+    const double y = a.res[(size_t)z * v.n1 + r] * s;
+    V0[r] = y;
+    if (r < v.n) v.rhs[(size_t)z * v.n + r] = y;
+  }
+}
+
+// xi = (cb . sigma - V_j[n]) / den (after k_pa_cdot of sigma)
+__global__ void __launch_bounds__(kNB) k_pa_prec2(PtView v, int j) {
+  const int z = blockIdx.x;
+  if (v.skip[z]) return;
+  __shared__ double sh[kNB];
+  const double s = pn_total(v, z, 0, sh);
+  if (threadIdx.x == 0) {
+    const double* Vj = v.V + ((size_t)z * (v.m + 1) + j) * v.n1;
+    const double xi = (s - Vj[v.n]) / v.den[z];
+    v.zh0[z] = xi;
+    v.Z[((size_t)z * v.m + j) * v.n1 + v.n] = xi;
+  }
+}
+
+// Z_j = sigma - xi zr; row weights wn = Z_j / d on the equation rows
+__global__ void __launch_bounds__(kNB) k_pa_prec3(PtView v, PtAdj a, int j) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= v.NN) return;
+  const int jj = t / v.nx, ii = t % v.nx;
+  double wv = 0.0;
+  if (ii >= 1 && ii <= v.nx - 2 && jj >= 1 && jj <= v.ny - 2) {
+    const int r = (jj - 1) * (v.nx - 2) + (ii - 1);
+    const size_t o = (size_t)z * v.n + r;
+    const double val = v.sigma[o] - v.zh0[z] * a.zr[o];
+    v.Z[((size_t)z * v.m + j) * v.n1 + r] = val;
+    wv = v.act[o] ? 0.0 : val / v.dg[o];
+  }
+  a.wn[(size_t)z * v.NN + t] = wv;
+}
+
+// wn = x / d on the equation rows (x of instance z at x + z n1)
+__global__ void k_pa_weights(PtView v, PtAdj a, const double* __restrict__ x, const int* __restrict__ skip) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= v.NN) return;
+  const int jj = t / v.nx, ii = t % v.nx;
+  double wv = 0.0;
+  if (ii >= 1 && ii <= v.nx - 2 && jj >= 1 && jj <= v.ny - 2) {
+    const int r = (jj - 1) * (v.nx - 2) + (ii - 1);
+    const size_t o = (size_t)z * v.n + r;
+    wv = v.act[o] ? 0.0 : x[(size_t)z * v.n1 + r] / v.dg[o];
+  }
+  a.wn[(size_t)z * v.NN + t] = wv;
+}
+
+// out[0:n] = gP(w) + K gH(w) + x on identity rows + h^2 xi; partial cb . x into slot 0
+__global__ void __launch_bounds__(kNB) k_pa_combine(PtView v, PtAdj a, const double* __restrict__ x, size_t xstride,
+                                                    const double* __restrict__ dH, double* __restrict__ out,
+                                                    const int* __restrict__ skip) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  __shared__ double sh[kNB];
+  const double* xz = x + (size_t)z * xstride;
+  const double h = v.inst[z].h, xi = xz[v.n];
+  double s = 0.0;
+  NK_FOR(r, v.n) {
+    const size_t o = (size_t)z * v.n + r;
+    const size_t node = (size_t)z * v.NN + nk_node(r, v.nx);
+    out[(size_t)z * v.n1 + r] = a.gPn[node] + dH[node] + (v.act[o] ? xz[r] : 0.0) + h * h * xi;
+    s += a.cb[o] * xz[r];
+  }
+  s = nk_block_sum(s, sh);
+  if (threadIdx.x == 0) v.dots[((size_t)z * v.nvb + blockIdx.x) * (v.m + 2)] = s;
+}
+
+__global__ void __launch_bounds__(kNB) k_pa_combine2(PtView v, double* __restrict__ out, const int* __restrict__ skip) {
+  const int z = blockIdx.x;
+  if (skip && skip[z]) return;
+  __shared__ double sh[kNB];
+  const double s = pn_total(v, z, 0, sh);
+  if (threadIdx.x == 0) out[(size_t)z * v.n1 + v.n] = s;
+}
+
+__global__ void __launch_bounds__(kNB) k_pa_mu(PtView v, PtAdj a) {
+  const int z = blockIdx.y;
+  if (a.adone[z]) return;
+  NK_FOR(r, v.n1) a.mu[(size_t)z * v.n1 + r] += v.delta[(size_t)z * v.n1 + r];
+}
+
+// res = gx - w, partial |res|^2 in slot 0
+__global__ void __launch_bounds__(kNB) k_pa_resid(PtView v, PtAdj a) {
+  const int z = blockIdx.y;
+  if (a.adone[z]) return;
+  __shared__ double sh[kNB];
+  double s = 0.0;
+  NK_FOR(r, v.n1) {
+    const size_t o = (size_t)z * v.n1 + r;
+    const double x = a.gx[o] - v.w[o];
+    a.res[o] = x;
+    s += x * x;
+  }
+  s = nk_block_sum(s, sh);
+  if (threadIdx.x == 0) v.dots[((size_t)z * v.nvb + blockIdx.x) * (v.m + 2)] = s;
+}
+
+__global__ void __launch_bounds__(kNB) k_pa_resid2(PtView v, PtAdj a, double tol) {
+  const int z = blockIdx.x;
+  if (a.adone[z]) return;
+  __shared__ double sh[kNB];
+  const double s = pn_total(v, z, 0, sh);
+  if (threadIdx.x == 0) {
+    const double gn = a.gxn[z];
+    const double rel = gn > 0.0 ? sqrt(s) / gn : 0.0;
+    a.relres[z] = rel;
+    if (!(rel > tol)) a.adone[z] = 1;
+  }
+}
+
+// grad_rough = gH - g_H(lambda) per node; partial parameter sums (M slot 0, L slot 1)
+__global__ void __launch_bounds__(kNB) k_pa_grad(PtView v, PtAdj a, PaNodes q, const double* __restrict__ gH,
+                                                 double* __restrict__ grad_rough) {
+  const int z = blockIdx.y;
+  __shared__ double sh[kNB];
+  const PointInst in = v.inst[z];
+  const size_t base = (size_t)z * v.NN;
+  // point Moes: d ln(lambda)/dM = -4/(3M), d ln(pH)/dM = 1/(3M), d ln(pH)/dL = 1/L
+  const double lpM = 1.0 / (3.0 * in.m.M), lpL = 1.0 / in.m.L, llM = -4.0 / (3.0 * in.m.M);
+  double sM = 0.0, sL = 0.0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < v.NN; t += gridDim.x * blockDim.x) {
+    const size_t o = base + t;
+    double aU, aE, aZ;
+    pa_local(q, a.wn, base, t % v.nx, t / v.nx, v.nx, v.ny, in.h, aU, aE, aZ);
+    const double P = q.P[o], H = q.H[o], r = q.rho[o], e = q.eps[o];
+    const double drl = q.drho[o] * P, del = q.deta_rel[o] * P;
+    sM += aU * H * drl * lpM + aE * e * ((drl / r - del) * lpM - llM);
+    sL += aU * H * drl * lpL + aE * e * ((drl / r - del) * lpL);
+    if (grad_rough) grad_rough[o] = (gH ? gH[o] : 0.0) - a.gHn[o];
+  }
+  sM = nk_block_sum(sM, sh);
+  sL = nk_block_sum(sL, sh);
+  if (threadIdx.x == 0) {
+    double* d = v.dots + ((size_t)z * v.nvb + blockIdx.x) * (v.m + 2);
+    d[0] = sM;
+    d[1] = sL;
+  }
+}
+
+__global__ void __launch_bounds__(kNB) k_pa_grad2(PtView v, double* __restrict__ grad_ML) {
+  const int z = blockIdx.x;
+  __shared__ double sh[kNB];
+  const double sM = pn_total(v, z, 0, sh), sL = pn_total(v, z, 1, sh);
+  if (threadIdx.x == 0 && grad_ML) {
+    grad_ML[2 * z] = -sM;
+    grad_ML[2 * z + 1] = -sL;
+  }
+}
+
+}  // namespace
+
+static cudaError_t pa_paqif(PtCtx* c, PtAdj& a, const double* rhs, double* x, bool factor) {
+  PaqifLaunch L;
+  L.n_sys = c->lines;
+  L.n = c->nx - 2;
+  L.beta = c->beta;
+  L.mode = 0;
+  L.band = a.bandT;
+  L.rhs = rhs;
+  L.act = nullptr;
+  L.stack = c->pq_ws;
+  L.x = x;
+  L.iters = nullptr;
+  L.info = c->pq_info;
+  return factor ? launch_paqif_factor(L, a.fstore, c->st) : launch_paqif_resolve(L, a.fstore, c->st);
+}
+
+// out = Phi_x^T x with the row weights of x in a.wn
+static cudaError_t pa_apply(PtCtx* c, PtAdj& a, const PtView& v, const PaNodes& q, const double* x, size_t xstride,
+                            double* out, const int* skip) {
+  const int ni = c->n_inst;
+  const dim3 gn((c->NN + 255) / 256, ni), gv(c->nvb, ni);
+  k_pa_local<<<gn, 256, 0, c->st>>>(c->inst, q, a.wn, skip, a.gHn, a.gPn);
+  note_launch();
+  cudaError_t e = pt_deform_dir64(c, a.gHn, skip);  // dH = K gH
+  if (e != cudaSuccess) return e;
+  k_pa_combine<<<gv, kNB, 0, c->st>>>(v, a, x, xstride, c->dH, out, skip);
+  note_launch();
+  k_pa_combine2<<<ni, kNB, 0, c->st>>>(v, out, skip);
+  note_launch();
+  return cudaGetLastError();
+}
+
+void pt_adj_free(PtCtx* c) {
+  delete (PtAdj*)c->adj;
+  c->adj = nullptr;
+}
+
+cudaError_t pt_adjoint(PtCtx* c, const double* P, const double* H0, const double* rough, const double* gP,
+                       const double* gH, const double* gH0, double* grad_rough, double* grad_ML, double* relres,
+                       double tol, int max_cycles) {
+  const int ni = c->n_inst;
+  if (!c->adj) {
+    PtAdj* a = new PtAdj();
+    c->adj = a;
+    const size_t nt = (size_t)ni * c->n, n1t = (size_t)ni * (c->n + 1), NNt = (size_t)ni * c->NN;
+    struct A {
+      void** p;
+      size_t bytes;
+    } al[] = {{(void**)&a->bandT, sizeof(double) * nt * (2 * c->beta + 1)},
+              {(void**)&a->cb, sizeof(double) * nt},
+              {(void**)&a->hvec, sizeof(double) * nt},
+              {(void**)&a->zr, sizeof(double) * nt},
+              {(void**)&a->gx, sizeof(double) * n1t},
+              {(void**)&a->mu, sizeof(double) * n1t},
+              {(void**)&a->res, sizeof(double) * n1t},
+              {(void**)&a->wn, sizeof(double) * NNt},
+              {(void**)&a->gHn, sizeof(double) * NNt},
+              {(void**)&a->gPn, sizeof(double) * NNt},
+              {(void**)&a->relres, sizeof(double) * ni},
+              {(void**)&a->gxn, sizeof(double) * ni},
+              {(void**)&a->adone, sizeof(int) * ni},
+              {(void**)&a->fstore, paqif_factor_store_bytes(c->lines, c->nx - 2, c->beta)}};
+    for (auto& x : al) {
+      cudaError_t e = pt_alloc(c, x.p, x.bytes);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  PtAdj& a = *(PtAdj*)c->adj;
+  cudaError_t e = pt_state(c, P, H0, rough, nullptr);
+  if (e == cudaSuccess) e = pt_jac_band(c, P, c->band, c->act, c->jh, c->dg, nullptr);
+  if (e != cudaSuccess) return e;
+  PtView v = pt_view(c, c->skip);
+  v.done = a.adone;
+  const PaNodes q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib};
+  const dim3 gr((c->n + 127) / 128, ni), gv(c->nvb, ni), gn((c->NN + 255) / 256, ni);
+  k_pa_prepare<<<gr, 128, 0, c->st>>>(v, a);
+  note_launch();
+  k_pa_transpose<<<gr, 128, 0, c->st>>>(v, a);
+  note_launch();
+  if (gH) {
+    e = pt_deform_dir64(c, gH, nullptr);  // dH = K gH
+    if (e != cudaSuccess) return e;
+  }
+  k_pa_rhs<<<gv, kNB, 0, c->st>>>(v, a, gP, gH, c->dH);
+  note_launch();
+  k_pa_rhs2<<<ni, kNB, 0, c->st>>>(v, a, gH0);
+  note_launch();
+  k_pa_init<<<gv, kNB, 0, c->st>>>(v, a);
+  note_launch();
+  e = pa_paqif(c, a, a.hvec, a.zr, true);  // factor B^T; zr = B^-T h^2
+  if (e != cudaSuccess) return e;
+  k_pa_cdot<<<gv, kNB, 0, c->st>>>(v, a, a.zr, (size_t)c->n, nullptr);
+  note_launch();
+  k_pa_den<<<ni, kNB, 0, c->st>>>(v, a);
+  note_launch();
+  for (int cyc = 0; cyc < max_cycles; ++cyc) {
+    k_pa_norm_res<<<gv, kNB, 0, c->st>>>(v, a);
+    note_launch();
+    k_pa_start2<<<ni, kNB, 0, c->st>>>(v, a, tol, c->skip);
+    note_launch();
+    k_pa_v0<<<gv, kNB, 0, c->st>>>(v, a);
+    note_launch();
+    for (int j = 0; j < c->m; ++j) {
+      e = pa_paqif(c, a, c->rhs, c->sigma, false);
+      if (e != cudaSuccess) return e;
+      k_pa_cdot<<<gv, kNB, 0, c->st>>>(v, a, c->sigma, (size_t)c->n, c->skip);
+      note_launch();
+      k_pa_prec2<<<ni, kNB, 0, c->st>>>(v, j);
+      note_launch();
+      k_pa_prec3<<<gn, 256, 0, c->st>>>(v, a, j);
+      note_launch();
+      e = pa_apply(c, a, v, q, c->Z + (size_t)j * (c->n + 1), (size_t)c->m * (c->n + 1), c->w, c->skip);
+      if (e != cudaSuccess) return e;
+      for (int pass = 0; pass < 2; ++pass) {
+        k_pn_dots<<<gv, kNB, 0, c->st>>>(v, j);
+        note_launch();
+        k_pn_hsum<<<ni, kNB, 0, c->st>>>(v, j, pass);
+        note_launch();
+        k_pn_orth<<<gv, kNB, 0, c->st>>>(v, j);
+        note_launch();
+      }
+      k_pn_norm<<<gv, kNB, 0, c->st>>>(v);
+      note_launch();
+      k_pn_givens<<<ni, kNB, 0, c->st>>>(v, j);
+      note_launch();
+      k_pn_next<<<gv, kNB, 0, c->st>>>(v, j);
+      note_launch();
+      k_pn_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(a.adone, c->gm_conv, c->skip, ni);
+      note_launch();
+      if ((j + 1) % 8 == 0 && j + 1 < c->m) {
+        if (pn_all(c, a.adone, c->gm_conv, e)) break;
+        if (e != cudaSuccess) return e;
+      }
+    }
+    k_pn_ysolve<<<ni, kNB, 0, c->st>>>(v);
+    note_launch();
+    k_pn_delta<<<gv, kNB, 0, c->st>>>(v);
+    note_launch();
+    k_pa_mu<<<gv, kNB, 0, c->st>>>(v, a);
+    note_launch();
+    k_pa_weights<<<gn, 256, 0, c->st>>>(v, a, a.mu, a.adone);
+    note_launch();
+    e = pa_apply(c, a, v, q, a.mu, (size_t)(c->n + 1), c->w, a.adone);
+    if (e != cudaSuccess) return e;
+    k_pa_resid<<<gv, kNB, 0, c->st>>>(v, a);
+    note_launch();
+    k_pa_resid2<<<ni, kNB, 0, c->st>>>(v, a, tol);
+    note_launch();
+    if (pn_all(c, a.adone, nullptr, e)) break;
+    if (e != cudaSuccess) return e;
+  }
+  // lambda = mu / d on the equation rows; g_H(lambda); gradients
+  k_pa_weights<<<gn, 256, 0, c->st>>>(v, a, a.mu, nullptr);
+  note_launch();
+  k_pa_local<<<gn, 256, 0, c->st>>>(c->inst, q, a.wn, nullptr, a.gHn, a.gPn);
+  note_launch();
+  k_pa_grad<<<gv, kNB, 0, c->st>>>(v, a, q, gH, grad_rough);
+  note_launch();
+  k_pa_grad2<<<ni, kNB, 0, c->st>>>(v, grad_ML);
+  note_launch();
+  if (relres) e = cudaMemcpyAsync(relres, a.relres, sizeof(double) * ni, cudaMemcpyDeviceToDevice, c->st);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 }  // namespace ehl

@@ -15,7 +15,7 @@ LIM = {0: "minmod", 1: "vanleer"}
 
 
 def dev(a):
-    return torch.tensor(np.asarray(a, dtype=np.float64), device="cuda")
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
 
 
 def make(n, M=20.0, L=10.0, limiter=0, beta=2, tol=1e-11, n_inst=1, per=None, levels=-1, **kw):
@@ -135,3 +135,65 @@ def test_point_solve_129_properties():
     assert np.max(np.abs(np.minimum(Pint, R))) <= 2e-8
     assert abs(pb.h**2 * Pint.sum() - 2 * np.pi / 3) <= 1e-8
     assert np.max(np.abs(Pn - Pn[::-1, :])) <= 1e-6 * np.max(Pn)       # Y -> -Y
+
+
+# ---------------------------------------------------------------- point-contact adjoint
+@pytest.mark.parametrize("which", ["H_c", "P2"])
+def test_point_adjoint_matches_dense_oracle(which):
+    n, M, L = 33, 20.0, 10.0
+    rg = rough2(n, seed=5, amp=0.005)                     # [ny, nx]
+    ctx = make(n, M=M, L=L, tol=1e-12)
+    P, H0, iters, res, code = ctx.solve(rough=dev(rg[None]), check=False)
+    assert code == 0
+    Pn, H0n = P.cpu().numpy()[0], float(H0.cpu()[0])
+    pb = pr.PointProblem(n, n, M, L, rough=rg.T)
+    Pint = Pn.T[1:-1, 1:-1].ravel()
+    gP, gH = np.zeros((n, n)), np.zeros((n, n))          # oracle layout [nx, ny]
+    if which == "H_c":
+        gH[int(np.argmin(np.abs(pb.X))), int(np.argmin(np.abs(pb.Y)))] = 1.0
+    else:
+        gP[:] = 2.0 * pb.h**2 * pb.full(Pint)
+    ref = pr.adjoint(pb, Pint, H0n, gP, gH, 0.0)
+    gr, gml, rel, code = ctx.adjoint(P, H0, dev(gP.T[None]), dev(gH.T[None]), None, rough=dev(rg[None]), tol=1e-11,
+                                     max_cycles=20)
+    assert code == 0, rel.tolist()
+    gr, gml = gr.cpu().numpy()[0].T, gml.cpu().numpy()[0]  # back to [nx, ny]
+    scale = np.max(np.abs(ref["rough"]))
+    assert np.max(np.abs(gr - ref["rough"])) <= 1e-8 * scale, np.max(np.abs(gr - ref["rough"])) / scale
+    assert abs(gml[0] - ref["M"]) <= 1e-8 * abs(ref["M"])
+    assert abs(gml[1] - ref["L"]) <= 1e-8 * abs(ref["L"])
+
+
+@pytest.mark.slow
+def test_point_adjoint_129_vs_resolved_differences():
+    """The adjoint workload's point-contact backward: 129 x 129, M = 100, L = 10."""
+    n, M, L = 129, 100.0, 10.0
+    rg = rough2(n, seed=9, amp=0.005)
+    ctx = make(n, M=M, L=L, beta=4, tol=1e-11)
+    P, H0, iters, res, code = ctx.solve(rough=dev(rg[None]), check=False)
+    assert code == 0, (iters.tolist(), res.tolist())
+    X, Y = np.linspace(-4.5, 1.5, n), np.linspace(-3, 3, n)
+    ci, cj = int(np.argmin(np.abs(X))), int(np.argmin(np.abs(Y)))
+    gH = np.zeros((n, n))
+    gH[cj, ci] = 1.0                                       # H_c, GPU layout [ny, nx]
+    gr, gml, rel, code = ctx.adjoint(P, H0, None, dev(gH[None]), None, rough=dev(rg[None]), tol=1e-11, max_cycles=20)
+    assert code == 0, rel.tolist()
+    gr, gml = gr.cpu().numpy()[0], gml.cpu().numpy()[0]
+
+    def hc(rgx, M_=M, L_=L):
+        cx = make(n, M=M_, L=L_, beta=4, tol=1e-12)
+        Pp, H0p, it, rs, cd = cx.solve(P, H0, rough=dev(rgx[None]), check=False)
+        _, H, _ = cx.residual(Pp, H0p, dev(rgx[None]))
+        return float(H[0, cj, ci].cpu())
+
+    d = 1e-6
+    for node in ((cj, ci), (cj + 3, ci - 4)):
+        rp, rm = rg.copy(), rg.copy()
+        rp[node] += d
+        rm[node] -= d
+        fd = (hc(rp) - hc(rm)) / (2 * d)
+        assert abs(fd - gr[node]) <= 1e-5 * abs(fd) + 1e-7 * np.max(np.abs(gr)), (node, fd, gr[node])
+    # M enters smoothly; a wider step keeps the re-solves' rounding floor (~1e-11 in H_c) out of the difference
+    dm = 1e-4
+    fd = (hc(rg, M_=M * (1 + dm)) - hc(rg, M_=M * (1 - dm))) / (2 * dm * M)
+    assert abs(fd - gml[0]) <= 1e-5 * abs(fd), (fd, gml[0])
