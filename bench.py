@@ -321,6 +321,9 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------- the other configs
+PRECISION = {0: "Krylov products in double-float (plain path)",
+             2: "Krylov products as float32 GEMMs emulated on BF16 tensor cores (cuBLAS); residual float64"}
+
 def _timed(torch, fn, reps=1, warm=1):
     """CUDA-event time (ms, best of reps) of fn() after warm calls, and fn's last result."""
     out = None
@@ -364,25 +367,41 @@ def config_legs(ops, inputs, torch, dev):
         res[f"C1_method{method}"] = d
     # C3: 512 instances, M log-uniform [10, 1000], L uniform [5, 20], N from {257, ..., 2049}
     per = inputs.batched_line_params(512, seed=1)
-    kw = dict(limiter=0, halfband=2, method=1, tol=1e-8, max_iter=60)
-    pp = [ops.default_params(1, nx=q["N"], M=q["M"], L=q["L"], **kw) for q in per]
-    ctx = ops.Context(pp[0], n_inst=len(pp), per_inst=pp)
-    ms, out = _timed(torch, lambda: ctx.solve(check=False))
-    d = dict(workload="ragged batch: 512 line instances, N from {257, 513, 1025, 2049}, M 10^U(1,3), L U(5,20), "
-                      "minmod, beta=2, tol 1e-8 (seed 1)", ms=round(ms, 2), solves_per_s=round(512e3 / ms, 2))
-    d.update(summary(out[2], out[3], out[4], 1e-8))
-    res["C3"] = d
-    del ctx
+    Href = None
+    for prec in (0, 2):
+        kw = dict(limiter=0, halfband=2, method=1, tol=1e-8, max_iter=60, precision=prec)
+        pp = [ops.default_params(1, nx=q["N"], M=q["M"], L=q["L"], **kw) for q in per]
+        ctx = ops.Context(pp[0], n_inst=len(pp), per_inst=pp)
+        ms, out = _timed(torch, lambda: ctx.solve(check=False))
+        d = dict(workload="ragged batch: 512 line instances, N from {257, 513, 1025, 2049}, M 10^U(1,3), L U(5,20), "
+                          "minmod, beta=2, tol 1e-8 (seed 1)", precision=PRECISION[prec], ms=round(ms, 2),
+                 solves_per_s=round(512e3 / ms, 2))
+        d.update(summary(out[2], out[3], out[4], 1e-8))
+        _, H, _ = ctx.residual(out[0], out[1])
+        if Href is None:
+            Href = H
+        else:
+            d["H_rel_err_vs_plain"] = float((H - Href).abs().max() / Href.abs().max())
+        res["C3" if prec == 0 else "C3_mixed"] = d
+        del ctx
     # C4: point contact 257 x 257, M = 100, L = 10, minmod, beta 2
-    p = ops.default_params(2, nx=257, ny=257, M=100.0, L=10.0, limiter=0, halfband=2, method=1, tol=1e-8,
-                           max_iter=60, coarse_min_nodes=33)
-    ctx = ops.Context(p)
-    ms, out = _timed(torch, lambda: ctx.solve(check=False), warm=0)
-    d = dict(workload="point contact 257x257, M=100, L=10, minmod, beta=2 (x-line PAQIF preconditioner), "
-                      "tol 1e-8, nested 33-65-129-257", ms=round(ms, 1), solves_per_s=round(1e3 / ms, 4))
-    d.update(summary(out[2], out[3], out[4], 1e-8))
-    res["C4"] = d
-    del ctx
+    Href = None
+    for prec in (0, 2):
+        p = ops.default_params(2, nx=257, ny=257, M=100.0, L=10.0, limiter=0, halfband=2, method=1, tol=1e-8,
+                               max_iter=60, coarse_min_nodes=33, precision=prec)
+        ctx = ops.Context(p)
+        ms, out = _timed(torch, lambda: ctx.solve(check=False), warm=0)
+        d = dict(workload="point contact 257x257, M=100, L=10, minmod, beta=2 (x-line PAQIF preconditioner), "
+                          "tol 1e-8, nested 33-65-129-257", precision=PRECISION[prec], ms=round(ms, 1),
+                 solves_per_s=round(1e3 / ms, 4))
+        d.update(summary(out[2], out[3], out[4], 1e-8))
+        _, H, _ = ctx.residual(out[0], out[1])
+        if Href is None:
+            Href = H
+        else:
+            d["H_rel_err_vs_plain"] = float((H - Href).abs().max() / Href.abs().max())
+        res["C4" if prec == 0 else "C4_mixed"] = d
+        del ctx
     # C5: adjoint, N = 1025, M = 50, L = 10, batch 64, roughness 0.1 sin(2 pi X/0.25) + field (0.05, 0.1)
     N, n = 1025, 64
     X = np.linspace(-4.5, 1.5, N)

@@ -161,12 +161,14 @@ typedef struct {
                         /*   diagonal blocks of each band (block Jacobi: couplings between */
                         /*   blocks dropped), r the largest divisor of nx - 2 not above    */
                         /*   precond_blocks with blocks of at least 32 rows; 1: one system */
-  int precision;        /* line contact, method 1: arithmetic of the Krylov products K v   */
+  int precision;        /* method 1: arithmetic of the Krylov products K v (line and point) */
                         /*   (the residual stays float64, so the converged answer does     */
                         /*   not depend on it): 0 double-float Toeplitz kernel; with one   */
                         /*   grid spacing per grid size, a float32-output GEMM of all     */
                         /*   instances: 1 float32, 2 float32 emulated on BF16 tensor cores,*/
-                        /*   3 TF32 tensor cores, 4 BF16 tensor cores                     */
+                        /*   3 TF32 tensor cores, 4 BF16 tensor cores; point contact: one */
+                        /*   GEMM [nx x nx ny] . [nx ny x ny] per instance from the        */
+                        /*   block-Toeplitz structure of the 2-D kernel                    */
 } ehl_params;
 
 /* Fill *p with the defaults above for dimension `dim` (1). */

@@ -16,6 +16,7 @@
 // the dR/dH0 column and the force row.  Vector reductions run over many
 // blocks per instance (an instance has up to ~65k unknowns); the Arnoldi
 // step is classical Gram-Schmidt applied twice.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
@@ -174,7 +175,9 @@ __global__ void k_pt_film(const PointInst* __restrict__ inst, const void* __rest
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= NN) return;
   double D;
-  if (p64) {
+  if (p64 == 2) {  // one float32 product [n_inst][NN] (the GEMM path)
+    D = (double)reinterpret_cast<const float*>(partial)[(size_t)z * NN + t];
+  } else if (p64) {
     const double* pd = reinterpret_cast<const double*>(partial);
     D = 0.0;
     for (int y = 0; y < ksplit; ++y) D += pd[((size_t)y * n_inst + z) * NN + t];
@@ -548,6 +551,38 @@ void pt_free(PtCtx* c) {
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   pt_adj_free(c);
+  if (c->blas) cublasDestroy(c->blas);
+  c->blas = nullptr;
+}
+
+// T_all[i + (d nx + k) nx] = T[d][|i - k|]  (column-major nx x (nx ny), float32)
+__global__ void k_pt_tall(const double* __restrict__ gtab64, float* __restrict__ Tall, int nx, int ny) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t total = (size_t)nx * nx * ny;
+  if (t >= total) return;
+  const int i = (int)(t % nx);
+  const size_t col = t / nx;
+  const int d = (int)(col / nx), k = (int)(col % nx);
+  Tall[t] = (float)gtab64[(size_t)d * nx + (i > k ? i - k : k - i)];
+}
+
+// Q[(d nx + k) + j (nx ny)] = V[j][k] (d = 0) or V[j-d][k] + V[j+d][k] (rows outside the grid are 0)
+__global__ void k_pt_qmat(const double* __restrict__ V, float* __restrict__ Q, int nx, int ny) {
+  const int z = blockIdx.y;
+  const size_t NN = (size_t)nx * ny;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NN * ny) return;
+  const int j = (int)(t / NN);
+  const size_t rem = t % NN;
+  const int d = (int)(rem / nx), k = (int)(rem % nx);
+  const double* Vz = V + (size_t)z * NN;
+  double s;
+  if (d == 0) {
+    s = Vz[(size_t)j * nx + k];
+  } else {
+    s = (j - d >= 0 ? Vz[(size_t)(j - d) * nx + k] : 0.0) + (j + d < ny ? Vz[(size_t)(j + d) * nx + k] : 0.0);
+  }
+  Q[(size_t)z * NN * ny + t] = (float)s;
 }
 
 static PtRow pt_row(PtCtx* c, const double* P) {
@@ -566,7 +601,8 @@ static PtRow pt_row(PtCtx* c, const double* P) {
   return r;
 }
 
-ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int max_iter, int krylov_dim) {
+ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int max_iter, int krylov_dim,
+                   int precision) {
   const int ni = (int)insts.size();
   c->n_inst = ni;
   c->nx = insts[0].nx;
@@ -634,6 +670,21 @@ ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int 
     note_launch();
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess && precision > 0 && insts[0].m.elastic) {
+    const size_t tall = (size_t)c->nx * c->nx * c->ny, q = (size_t)c->NN * c->ny * ni;
+    if (pt_alloc(c, (void**)&c->Tall, sizeof(float) * tall) != cudaSuccess ||
+        pt_alloc(c, (void**)&c->Qf, sizeof(float) * q) != cudaSuccess ||
+        pt_alloc(c, (void**)&c->Df, sizeof(float) * NNt) != cudaSuccess) {
+      cudaGetLastError();
+      return EHL_ENOMEM;
+    }
+    if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) return EHL_ECUDA;
+    cublasSetStream(c->blas, c->st);
+    k_pt_tall<<<(unsigned)((tall + 255) / 256), 256, 0, c->st>>>(c->gtab64, c->Tall, c->nx, c->ny);
+    note_launch();
+    c->precision = precision;
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -697,7 +748,33 @@ cudaError_t pt_start(PtCtx* c, double* P, double* H0, const double* rough) {
   return cudaGetLastError();
 }
 
+// The Krylov products with precision > 0: per instance one GEMM T_all [nx x nx ny] . Q [nx ny x ny]
+// (precision 1 float32, 2 float32 emulated on BF16 tensor cores, 3 TF32, 4 BF16), float32 output.
+static cudaError_t pt_deform_gemm(PtCtx* c, const double* zn, const int* skip, const double* zh0) {
+  const size_t NN = c->NN, qn = NN * c->ny;
+  dim3 g((unsigned)((qn + 255) / 256), c->n_inst);
+  k_pt_qmat<<<g, 256, 0, c->st>>>(zn, c->Qf, c->nx, c->ny);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cublasComputeType_t ct = CUBLAS_COMPUTE_32F;
+  if (c->precision == 2) ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+  if (c->precision == 3) ct = CUBLAS_COMPUTE_32F_FAST_TF32;
+  if (c->precision == 4) ct = CUBLAS_COMPUTE_32F_FAST_16BF;
+  const float one = 1.0f, zero = 0.0f;
+  const int m = c->nx, n = c->ny, k = c->nx * c->ny;
+  if (cublasGemmStridedBatchedEx(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, c->Tall, CUDA_R_32F, m, 0,
+                                 c->Qf, CUDA_R_32F, k, (long long)qn, &zero, c->Df, CUDA_R_32F, m, (long long)NN,
+                                 c->n_inst, ct, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+    return cudaErrorUnknown;
+  const dim3 gn((c->NN + kPtNode - 1) / kPtNode, c->n_inst);
+  k_pt_film<<<gn, kPtNode, 0, c->st>>>(c->inst, c->Df, 1, 2, zh0, nullptr, skip, c->dH, c->n_inst, 1);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t pt_deform_dir(PtCtx* c, const double* zn, const double* zh0, const int* skip) {
+  if (c->precision > 0) return pt_deform_gemm(c, zn, skip, zh0);
   cudaError_t e = pt_deform(c, zn, skip, false);
   if (e != cudaSuccess) return e;
   const dim3 gn((c->NN + kPtNode - 1) / kPtNode, c->n_inst);

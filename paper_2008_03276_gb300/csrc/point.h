@@ -1,5 +1,6 @@
 // point.h -- host-side state and stage launchers of the point-contact path.
 #pragma once
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,12 +45,18 @@ struct PtCtx {
   int *gm_k = nullptr, *gm_conv = nullptr, *lsdone = nullptr, *lsphase = nullptr, *skip = nullptr;
   int* acc = nullptr;     // line search: trial accepted in this pass
   void* adj = nullptr;    // adjoint buffers (point_newton.cu), allocated on first use
+  // mixed-precision Krylov products (precision > 0): the deformation as one GEMM per instance,
+  // T_all [nx][nx*ny] (the x-Toeplitz blocks of every y offset) times the shifted sums of the rows
+  int precision = 0;
+  cublasHandle_t blas = nullptr;
+  float *Tall = nullptr, *Qf = nullptr, *Df = nullptr;
   int trace = 0;
   std::vector<void*> allocs;
 };
 
 cudaError_t pt_alloc(PtCtx* c, void** p, size_t bytes);
-ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int max_iter, int krylov_dim);
+ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int max_iter, int krylov_dim,
+                   int precision = 0);
 void pt_free(PtCtx* c);
 // state (film, lubricant, faces, residual, block partials) at (P, H0); all [n_inst][ny][nx]
 cudaError_t pt_state(PtCtx* c, const double* P, const double* H0, const double* rough, const int* skip);

@@ -109,12 +109,13 @@ def oracle_33():
     return pb, P, H0
 
 
-@pytest.mark.parametrize("levels,beta", [(0, 2), (-1, 2), (-1, 4)])
-def test_point_solve_matches_oracle(oracle_33, levels, beta):
+@pytest.mark.parametrize("levels,beta,precision", [(0, 2, 0), (-1, 2, 0), (-1, 4, 0), (-1, 2, 2), (-1, 2, 3)])
+def test_point_solve_matches_oracle(oracle_33, levels, beta, precision):
+    """precision > 0: the Krylov products as one tensor-core GEMM per instance (the residual stays float64)."""
     pb, Pr, H0r = oracle_33
-    ctx = make(33, levels=levels, beta=beta)
+    ctx = make(33, levels=levels, beta=beta, precision=precision)
     P, H0, iters, res, code = ctx.solve(check=False)
-    print(f"levels {levels} beta {beta}: code {code} iters {iters.tolist()} res {res.tolist()}")
+    print(f"levels {levels} beta {beta} precision {precision}: code {code} iters {iters.tolist()} res {res.tolist()}")
     assert code == 0
     P, H0 = P.cpu().numpy()[0], float(H0.cpu()[0])
     assert np.max(np.abs(P[1:-1, 1:-1] - pb.full(Pr)[1:-1, 1:-1].T)) <= 1e-8 * np.max(Pr)
