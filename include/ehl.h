@@ -169,6 +169,9 @@ typedef struct {
                         /*   3 TF32 tensor cores, 4 BF16 tensor cores; point contact: one */
                         /*   GEMM [nx x nx ny] . [nx ny x ny] per instance from the        */
                         /*   block-Toeplitz structure of the 2-D kernel                    */
+  int graph;            /* line contact, method 1: 1 = each Newton step is one CUDA graph  */
+                        /*   launch (captured once, replayed; one host check per step);    */
+                        /*   0 = launched kernel by kernel with early exits (default)      */
 } ehl_params;
 
 /* Fill *p with the defaults above for dimension `dim` (1). */

@@ -8,7 +8,14 @@
 
 namespace ehl {
 static std::atomic<unsigned long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local unsigned long long t_launches = 0;
+void note_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+unsigned long long thread_launches() { return t_launches; }
+// graph capture: the captured launches did not run (d < 0); each replay runs them (d > 0)
+void add_launches(long long d) { g_launches.fetch_add((unsigned long long)d, std::memory_order_relaxed); }
 }  // namespace ehl
 
 using namespace ehl;

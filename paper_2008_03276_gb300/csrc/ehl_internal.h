@@ -16,6 +16,11 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Count of kernels this library has launched (observability; see ehl_kernel_launches).
 void note_launch();
+unsigned long long thread_launches();  // note_launch() calls of this host thread
+void add_launches(long long d);
+// set the kernels' shared-memory attributes for half-band beta on the current device (before
+// any stream capture: the launches themselves then make no attribute call)
+cudaError_t paqif_prepare(int beta);
 
 struct PaqifLaunch {
   int n_sys, n, beta, mode;

@@ -730,6 +730,12 @@ cudaError_t line_mixed_init(LineCtx* c, int precision) {
   if (e != cudaSuccess) return e;
   if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
   cublasSetStream(c->blas, c->st);
+  // a workspace of its own, so that no GEMM allocates (also inside a graph capture)
+  void* ws = nullptr;
+  const size_t wsb = (size_t)32 << 20;
+  e = ctx_alloc(c, &ws, wsb);
+  if (e != cudaSuccess) return e;
+  cublasSetWorkspace(c->blas, ws, wsb);
   cublasSetMathMode(c->blas, CUBLAS_DEFAULT_MATH);
   k_line_kfull<<<(unsigned)((NN + 255) / 256), 256, 0, c->st>>>(c->gtab64, c->Kf, c->N);
   note_launch();

@@ -44,6 +44,12 @@ struct LineCtx {
   void* adj = nullptr;
   // EHL_TRACE=k in the environment: one line per Newton step for the first k instances (stderr)
   int trace = 0;
+  // graph mode: one Newton step captured as a CUDA graph (no host checks inside; the first
+  // kGraphTrials line-search trials), replayed each outer iteration
+  bool use_graph = false, capturing = false;
+  cudaGraphExec_t graph = nullptr;
+  const double *g_P = nullptr, *g_H0 = nullptr, *g_rough = nullptr;  // pointers the graph was captured with
+  long long graph_launches = 0;
 };
 
 cudaError_t ctx_alloc(LineCtx* c, void** p, size_t bytes);
@@ -74,6 +80,9 @@ cudaError_t line_prolong(const double* Pc, const double* H0c, const int* cdone, 
 cudaError_t line_nk_alloc(LineCtx* c);
 void line_nk_free(LineCtx* c);
 cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough);
+// line-search trials first_trial.. after a graph replay, for instances still searching
+cudaError_t line_nk_finish(LineCtx* c, double* P, double* H0, const double* rough, int first_trial);
+constexpr int kGraphTrials = 6;
 // Adjoint of a converged state (line_adjoint.cu): gradients of an objective J(P, H, H0) given
 // its partials gP, gH ([n_inst][N], nullable) and gH0 ([n_inst], nullable) with respect to the
 // roughness (grad_rough [n_inst][N], nullable) and the Moes parameters (grad_ML [n_inst][2],

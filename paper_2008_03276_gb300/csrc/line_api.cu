@@ -35,6 +35,7 @@ struct ehl_ctx {
   int dim = 1;
   int n_inst = 0, nx_max = 0, beta = 0;
   bool direct = true;  // single bucket in caller order: no gather/scatter
+  bool own_streams = false;  // buckets run on streams of their own (several buckets, or graphs)
   cudaStream_t st = nullptr;
   std::vector<Bucket*> buckets;
   PtCtx* pt = nullptr;  // point contact (dim 2): one grid for every instance
@@ -99,6 +100,7 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   p->coarse_tol = 1e-4;
   p->precond_blocks = 1;
   p->precision = 0;
+  p->graph = 0;
 }
 
 static bool point_grid_ok(const ehl_params& p) {
@@ -113,7 +115,8 @@ static bool params_ok(const ehl_params& p) {
          (p.method == 0 || p.method == 1) && p.max_iter >= 1 && p.krylov_dim >= 1 && p.krylov_dim <= 200 &&
          p.tol > 0.0 && isfinite(p.h_init) && isfinite(p.c_h0) && isfinite(p.omega) && isfinite(p.dist_weight) &&
          isfinite(p.switch_eps_h) && p.levels >= -1 && p.coarse_min_nodes >= 5 && p.coarse_tol > 0.0 &&
-         p.precond_blocks >= 1 && p.precond_blocks <= 4096 && p.precision >= 0 && p.precision <= 4;
+         p.precond_blocks >= 1 && p.precond_blocks <= 4096 && p.precision >= 0 && p.precision <= 4 &&
+         (p.graph == 0 || p.graph == 1);
 }
 
 static LineInst make_inst(const ehl_params& p) {
@@ -149,6 +152,8 @@ static void free_all(LineCtx* c) {
   if (c->nk) line_nk_free(c);
   if (c->adj) line_adj_free(c);
   line_mixed_free(c);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
 }
 
 static void free_bucket(Bucket* b) {
@@ -236,6 +241,8 @@ static ehl_status init_line(LineCtx* c, const std::vector<LineInst>& insts, int 
                                   c->st);
   if (e == cudaSuccess) e = line_init_tables(c);
   if (e == cudaSuccess && c->method == 1) e = line_mixed_init(c, p.precision);
+  if (e == cudaSuccess) e = paqif_prepare(c->beta);  // no attribute calls inside a graph capture
+  c->use_graph = c->method == 1 && p.graph == 1;
   if (e != cudaSuccess) {
     cudaGetLastError();
     return EHL_ECUDA;
@@ -439,11 +446,13 @@ extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_para
   ctx->beta = p->halfband;
   ctx->st = (cudaStream_t)stream;
   ctx->direct = sizes.size() == 1;
+  // a graph cannot be captured on the legacy default stream the caller may pass
+  ctx->own_streams = !ctx->direct || (p->graph == 1 && p->method == 1);
   for (size_t q = 0; q < sizes.size(); ++q) {
     Bucket* b = new Bucket();
     ctx->buckets.push_back(b);
     b->idx = members[q];
-    if (ctx->direct) {
+    if (!ctx->own_streams) {
       b->c.st = ctx->st;
     } else {
       if (cudaStreamCreateWithFlags(&b->c.st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -461,6 +470,7 @@ extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_para
     p0.levels = p->levels;
     p0.coarse_min_nodes = p->coarse_min_nodes;
     p0.precision = p->precision;
+    p0.graph = p->graph;
     const ehl_status st = init_bucket(b, p0, ps, !ctx->direct);
     if (st != EHL_OK) {
       free_ctx(ctx);
@@ -496,7 +506,7 @@ static ehl_status cuda_status(cudaError_t e) {
 
 // bucket streams wait for the caller's stream (fork) and the caller's stream for them (join)
 static cudaError_t fork(ehl_ctx* ctx) {
-  if (ctx->direct) return cudaSuccess;
+  if (!ctx->own_streams) return cudaSuccess;
   cudaEvent_t e0;
   cudaError_t e = cudaEventCreateWithFlags(&e0, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->st);
@@ -506,7 +516,7 @@ static cudaError_t fork(ehl_ctx* ctx) {
   return e;
 }
 static cudaError_t join(ehl_ctx* ctx) {
-  if (ctx->direct) return cudaSuccess;
+  if (!ctx->own_streams) return cudaSuccess;
   cudaError_t e = cudaSuccess;
   for (Bucket* b : ctx->buckets) {
     if (e == cudaSuccess) e = cudaEventRecord(b->ev, b->c.st);
@@ -700,6 +710,64 @@ extern "C" ehl_status ehl_jacobian_apply(ehl_ctx* ctx, const double* P, const do
   return cuda_status(e);
 }
 
+// The final residual at the returned iterate and the done flags in hdone.
+static cudaError_t iterate_end(LineCtx* c, const double* rough, std::vector<int>& hdone) {
+  cudaError_t e = line_state(c, c->Pw, c->H0w, rough, nullptr, nullptr);
+  if (e == cudaSuccess) e = line_finalize(c, nullptr, nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hdone.data(), c->done, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  return e;
+}
+
+// Graph mode: the Newton step (without host checks, with the first kGraphTrials
+// line-search trials) is captured once per (P, H0, rough) and replayed; after each
+// replay one host check reads the done flags, and instances still searching get
+// the remaining trials eagerly.
+static cudaError_t iterate_graph(LineCtx* c, const double* rough, std::vector<int>& hdone) {
+  cudaError_t e = cudaSuccess;
+  if (!c->graph || c->g_P != c->Pw || c->g_H0 != c->H0w || c->g_rough != rough) {
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    const unsigned long long l0 = thread_launches();
+    e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    c->capturing = true;
+    const cudaError_t es = line_nk_step(c, c->Pw, c->H0w, rough);
+    c->capturing = false;
+    e = cudaStreamEndCapture(c->st, &g);
+    c->graph_launches = (long long)(thread_launches() - l0);
+    add_launches(-c->graph_launches);  // captured, not run
+    if (es != cudaSuccess) e = es;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph = nullptr;
+      return e;
+    }
+    c->g_P = c->Pw;
+    c->g_H0 = c->H0w;
+    c->g_rough = rough;
+  }
+  for (int it = 0; it < c->max_iter && e == cudaSuccess; ++it) {
+    e = cudaGraphLaunch(c->graph, c->st);
+    if (e != cudaSuccess) break;
+    add_launches(c->graph_launches);
+    e = line_nk_finish(c, c->Pw, c->H0w, rough, kGraphTrials);
+    if (e != cudaSuccess) break;
+    e = cudaMemcpyAsync(hdone.data(), c->done, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    bool all = true;
+    for (int v : hdone) all = all && (v != 0);
+    if (all) break;
+  }
+  if (e == cudaSuccess) e = iterate_end(c, rough, hdone);
+  return e;
+}
+
 // Outer iterations of one LineCtx from (c->Pw, c->H0w) until every instance is
 // done or max_iter; ends with the residual at the returned iterate and the
 // done flags in hdone.
@@ -710,6 +778,7 @@ static cudaError_t iterate(LineCtx* c, const double* rough, std::vector<int>& hd
   if (e == cudaSuccess) e = cudaMemsetAsync(c->best, 0x7f, sizeof(double) * c->n_inst, c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stall, 0, sizeof(int) * c->n_inst, c->st);
   hdone.assign(c->n_inst, 0);
+  if (e == cudaSuccess && c->method == 1 && c->use_graph) return iterate_graph(c, rough, hdone);
   const int check_every = 8;
   for (int it = 0; it < c->max_iter && e == cudaSuccess; ++it) {
     e = (c->method == 0) ? line_paper_iteration(c, c->Pw, c->H0w, rough) : line_nk_step(c, c->Pw, c->H0w, rough);

@@ -460,6 +460,39 @@ static bool all_set(LineCtx* c, const int* a, const int* b2, cudaError_t& e) {
   return true;
 }
 
+// Line-search trials [t0, t1): trial point, its residual, merit and acceptance;
+// with check, stop as soon as every instance is done or has accepted.
+static cudaError_t line_nk_trials(LineCtx* c, double* P, double* H0, const double* rough, int t0, int t1,
+                                  bool check) {
+  NkBuf& b = *(NkBuf*)c->nk;
+  const int ni = c->n_inst, N = c->N;
+  const dim3 gn((N + 255) / 256, ni);
+  cudaError_t e = cudaSuccess;
+  for (int trial = t0; trial < t1; ++trial) {
+    k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.lsdone, b.skip, ni);
+    note_launch();
+    k_nk_trial<<<gn, 256, 0, c->st>>>(b, P, H0, b.skip, N);
+    note_launch();
+    e = line_state(c, b.Pt, b.H0t, rough, b.skip, nullptr);
+    if (e == cudaSuccess) e = line_finalize(c, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    k_nk_merit<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->R, c->red, c->dg, b.skip, P, H0, N);
+    note_launch();
+    if (check) {
+      if (all_set(c, c->done, b.lsdone, e)) break;
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t line_nk_finish(LineCtx* c, double* P, double* H0, const double* rough, int first_trial) {
+  NkBuf& b = *(NkBuf*)c->nk;
+  cudaError_t e = cudaSuccess;
+  if (all_set(c, c->done, b.lsdone, e) || e != cudaSuccess) return e;
+  return line_nk_trials(c, P, H0, rough, first_trial, 64, true);
+}
+
 // One Newton step for every instance that is not done.
 cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough) {
   NkBuf& b = *(NkBuf*)c->nk;
@@ -490,13 +523,14 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
     note_launch();
     k_nk_arnoldi<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, b.skip, c->rhs, N);
     note_launch();
-    if ((j + 1) % 8 == 0 && j + 1 < b.m) {
+    if (!c->capturing && (j + 1) % 8 == 0 && j + 1 < b.m) {
       if (all_set(c, c->done, b.gm_conv, e)) break;
       if (e != cudaSuccess) return e;
     }
   }
   k_nk_update<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->done, N);
   note_launch();
+  if (c->capturing) return line_nk_trials(c, P, H0, rough, 0, kGraphTrials, false);
   std::vector<int> tk, tc;
   std::vector<double> tphin, trtol;
   if (c->trace) {
@@ -513,19 +547,8 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
       e = cudaMemcpyAsync(trtol.data(), b.rtol, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->st);
     if (e != cudaSuccess) return e;
   }
-  for (int trial = 0; trial < 64; ++trial) {
-    k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.lsdone, b.skip, ni);
-    note_launch();
-    k_nk_trial<<<gn, 256, 0, c->st>>>(b, P, H0, b.skip, N);
-    note_launch();
-    e = line_state(c, b.Pt, b.H0t, rough, b.skip, nullptr);
-    if (e == cudaSuccess) e = line_finalize(c, nullptr, nullptr);
-    if (e != cudaSuccess) return e;
-    k_nk_merit<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->R, c->red, c->dg, b.skip, P, H0, N);
-    note_launch();
-    if (all_set(c, c->done, b.lsdone, e)) break;
-    if (e != cudaSuccess) return e;
-  }
+  e = line_nk_trials(c, P, H0, rough, 0, 64, true);
+  if (e != cudaSuccess) return e;
   if (c->trace) {
     const int nt = (int)tk.size();
     std::vector<double> tt(nt), tred(4 * nt);

@@ -30,6 +30,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "df64.cuh"
 #include "ehl_internal.h"
 
@@ -715,6 +717,37 @@ size_t paqif_factor_store_bytes(int n_sys, int n, int beta) {
   return padded * (size_t)s * (size_t)fl * sizeof(float4);
 }
 
+// the dynamic shared-memory size of both kernels, set once per device
+template <int B>
+static cudaError_t p3_attrs() {
+  static std::atomic<unsigned long long> set{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (set.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  const int smem = (int)p3_smem<B>();
+  e = cudaFuncSetAttribute(paqif3_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(paqif3_solve_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess && bit) set.fetch_or(bit, std::memory_order_release);
+  return e;
+}
+
+cudaError_t paqif_prepare(int beta) {
+  switch (beta) {
+    case 1: return p3_attrs<1>();
+    case 2: return p3_attrs<2>();
+    case 3: return p3_attrs<3>();
+    case 4: return p3_attrs<4>();
+    case 5: return p3_attrs<5>();
+    case 6: return p3_attrs<6>();
+    case 7: return p3_attrs<7>();
+    case 8: return p3_attrs<8>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int B>
 static cudaError_t launch3(const PaqifLaunch& L, cudaStream_t st, void* fstore, bool solve_only) {
   Paqif3Args a;
@@ -733,15 +766,12 @@ static cudaError_t launch3(const PaqifLaunch& L, cudaStream_t st, void* fstore, 
   const size_t smem = p3_smem<B>();
   const int per = p3_per_cta<B>();
   const int grid = (L.n_sys + per - 1) / per;
-  cudaError_t e;
+  cudaError_t e = p3_attrs<B>();
+  if (e != cudaSuccess) return e;
   if (solve_only) {
-    e = cudaFuncSetAttribute(paqif3_solve_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     paqif3_solve_kernel<B><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
     note_launch();
   } else {
-    e = cudaFuncSetAttribute(paqif3_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     paqif3_kernel<B><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
     note_launch();
   }

@@ -61,8 +61,8 @@ def test_params_struct_layout_matches_defaults():
     assert (p.switch_eps_h, p.dist_weight, p.c_h0, p.omega) == (0.6, 0.5, 0.05, 1.0)
     assert (p.method, p.tol, p.max_iter, p.krylov_dim, p.h_init) == (1, 1e-8, 200, 40, 0.05)
     assert (p.levels, p.coarse_min_nodes, p.coarse_tol) == (-1, 65, 1e-4)
-    assert (p.precond_blocks, p.precision) == (1, 0)
-    assert ctypes.sizeof(p) == _ffi.EhlParams.precision.offset + 4
+    assert (p.precond_blocks, p.precision, p.graph) == (1, 0, 0)
+    assert ctypes.sizeof(p) == (_ffi.EhlParams.graph.offset + 4 + 7) // 8 * 8  # tail padding to 8 bytes
 
 
 @pytest.mark.parametrize("field,value", [("nx", 4), ("halfband", 9), ("M", -1.0), ("xb", -5.0), ("method", 7),
