@@ -162,6 +162,8 @@ typedef struct {
                         /*   blocks dropped), r the largest divisor of nx - 2 not above    */
                         /*   precond_blocks with blocks of at least 32 rows; 1: one system */
   int precision;        /* method 1: arithmetic of the Krylov products K v (line and point) */
+                        /*   and, in line contact, of the PAQIF preconditioner (>= 1:       */
+                        /*   float32 sweeps)                                               */
                         /*   (the residual stays float64, so the converged answer does     */
                         /*   not depend on it): 0 double-float Toeplitz kernel; with one   */
                         /*   grid spacing per grid size, a float32-output GEMM of all     */

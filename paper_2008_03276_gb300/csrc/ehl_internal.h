@@ -31,6 +31,7 @@ struct PaqifLaunch {
   double* x;
   int* iters;
   int* info;
+  bool f32 = false;  // float32 sweeps (modes 0 and 1): a preconditioner, not a solve to 1e-12
 };
 
 // Bytes of the per-system Z-stack (padded to whole CTAs); 0 for a bad beta.

@@ -447,6 +447,7 @@ static cudaError_t paqif_on(LineCtx* c, const double* rhs, double* x, bool facto
   L.x = x;
   L.iters = nullptr;
   L.info = c->pq_info;
+  L.f32 = c->precision > 0;  // the mixed-precision path also runs its preconditioner in float32
   return factor ? launch_paqif_factor(L, b.fstore, c->st) : launch_paqif_resolve(L, b.fstore, c->st);
 }
 

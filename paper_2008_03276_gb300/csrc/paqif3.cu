@@ -105,9 +105,43 @@ __device__ __forceinline__ void cpa_wait() {
 __device__ __forceinline__ df f2df(float2 v) { return make_df(v.x, v.y); }
 __device__ __forceinline__ float2 df2f(df v) { return make_float2(v.hi, v.lo); }
 
-template <int B>
+// Arithmetic of the sweeps: double-float (F32 = false, about 48 bits) or plain
+// float32 in the hi word (F32 = true: the Krylov preconditioner of the mixed-
+// precision path, whose accuracy GMRES absorbs).  Storage is double-float in
+// both cases (lo = 0 for float32).
+template <bool F32>
+struct Ar {
+  static __device__ __forceinline__ df det2(df a, df d, df b, df c) { return df_det2(a, d, b, c); }
+  static __device__ __forceinline__ df mul(df a, df b) { return df_mul(a, b); }
+  static __device__ __forceinline__ df rcp(df a) { return df_rcp(a); }
+  static __device__ __forceinline__ df sub_two_prods(df s, df w0, df z0, df w1, df z1) {
+    return df_sub_two_prods(s, w0, z0, w1, z1);
+  }
+  static __device__ __forceinline__ df sub(df a, df b) { return df_sub(a, b); }
+  static __device__ __forceinline__ df fma(df a, df b, df c) { return df_fma(a, b, c); }
+  static __device__ __forceinline__ df from_double(double x) { return df_from_double(x); }
+  static __device__ __forceinline__ double to_double(df a) { return df_to_double(a); }
+};
+template <>
+struct Ar<true> {
+  static __device__ __forceinline__ df det2(df a, df d, df b, df c) {
+    return make_df(__fmaf_rn(a.hi, d.hi, -__fmul_rn(b.hi, c.hi)), 0.f);
+  }
+  static __device__ __forceinline__ df mul(df a, df b) { return make_df(__fmul_rn(a.hi, b.hi), 0.f); }
+  static __device__ __forceinline__ df rcp(df a) { return make_df(__frcp_rn(a.hi), 0.f); }
+  static __device__ __forceinline__ df sub_two_prods(df s, df w0, df z0, df w1, df z1) {
+    return make_df(__fmaf_rn(-w1.hi, z1.hi, __fmaf_rn(-w0.hi, z0.hi, s.hi)), 0.f);
+  }
+  static __device__ __forceinline__ df sub(df a, df b) { return make_df(__fsub_rn(a.hi, b.hi), 0.f); }
+  static __device__ __forceinline__ df fma(df a, df b, df c) { return make_df(__fmaf_rn(a.hi, b.hi, c.hi), 0.f); }
+  static __device__ __forceinline__ df from_double(double x) { return make_df((float)x, 0.f); }
+  static __device__ __forceinline__ double to_double(df a) { return (double)a.hi; }
+};
+
+template <int B, bool F32>
 struct P3 {
   using C = C3<B>;
+  using A = Ar<F32>;
 
   static __device__ __forceinline__ int row_of(int side, int t, int s) { return side ? s + t : s - 1 - t; }
   static __device__ __forceinline__ int wrap(int x) { return x >= C::W ? x - C::W : x; }
@@ -133,7 +167,7 @@ struct P3 {
         const int t = side ? r - s : s - 1 - r;
         double* dst = &sm.u.ring[side][t & (C::RB - 1)][col];
         if (CONVERT) {
-          const df v = df_from_double(*dst);
+          const df v = A::from_double(*dst);
           *reinterpret_cast<float2*>(dst) = make_float2(v.hi, v.lo);
         } else {
           cpa8(dst, bsys + (size_t)r * C::BW + col);
@@ -143,7 +177,7 @@ struct P3 {
         const int t = side ? r - s : s - 1 - r;
         double* dst = &sm.rrhs[side][t & (C::RB - 1)];
         if (CONVERT) {
-          const df v = df_from_double(*dst);
+          const df v = A::from_double(*dst);
           *reinterpret_cast<float2*>(dst) = make_float2(v.hi, v.lo);
           sm.ract[side][t & (C::RB - 1)] = a.act ? __ldcg(a.act + (size_t)dsys * n + r) : 0;
         } else {
@@ -236,16 +270,16 @@ struct P3 {
       };
       const df pa = f2df(sm.S[sp][sp]), pb = f2df(sm.S[sp][sq]);
       const df pc = f2df(sm.S[sq][sp]), pd = f2df(sm.S[sq][sq]);
-      df det = df_det2(pa, pd, pb, pc);
+      df det = A::det2(pa, pd, pb, pc);
       const float scale = fabsf(pa.hi * pd.hi) + fabsf(pb.hi * pc.hi);
       if (!(fabsf(det.hi) > 1e-13f * scale) || !(scale > 0.f)) {
         if (flag == 0) flag = EHL_INFO_SINGULAR;
         if (!(fabsf(det.hi) > 0.f)) det = make_df(1e-30f, 0.f);
       }
-      const df inv = df_rcp(det);
+      const df inv = A::rcp(det);
       if (fst && u == 0) {  // Pi^-1 = inv [[d, -b], [-c, a]]
-        const df i00 = df_mul(pd, inv), i01 = df_neg(df_mul(pb, inv));
-        const df i10 = df_neg(df_mul(pc, inv)), i11 = df_mul(pa, inv);
+        const df i00 = A::mul(pd, inv), i01 = df_neg(A::mul(pb, inv));
+        const df i10 = df_neg(A::mul(pc, inv)), i11 = A::mul(pa, inv);
         fst[(size_t)k * C::FL + C::NO] = make_float4(i00.hi, i00.lo, i01.hi, i01.lo);
         fst[(size_t)k * C::FL + C::NO + 1] = make_float4(i10.hi, i10.lo, i11.hi, i11.lo);
       }
@@ -268,8 +302,8 @@ struct P3 {
         const bool rowtask = (u + m * C::LS) < C::NO;
         // row:    w_p = inv (x1 d - x2 c),  w_q = inv (x2 a - x1 b)
         // column: m_p = inv (x1 d - x2 b),  m_q = inv (x2 a - x1 c)
-        tr1[m] = df_mul(df_det2(tx1[m], pd, tx2[m], rowtask ? pc : pb), inv);
-        tr2[m] = df_mul(df_det2(tx2[m], pa, tx1[m], rowtask ? pb : pc), inv);
+        tr1[m] = A::mul(A::det2(tx1[m], pd, tx2[m], rowtask ? pc : pb), inv);
+        tr2[m] = A::mul(A::det2(tx2[m], pa, tx1[m], rowtask ? pb : pc), inv);
       }
 #pragma unroll
       for (int m = 0; m < C::R1; ++m) {
@@ -301,7 +335,7 @@ struct P3 {
         float2 uN[C::RU];
 #pragma unroll
         for (int m = 0; m < C::RU; ++m)
-          uN[m] = df2f(df_sub_two_prods(f2df(uS[m]), f2df(uW0[m]), f2df(uZp[m]), f2df(uW1[m]), f2df(uZq[m])));
+          uN[m] = df2f(A::sub_two_prods(f2df(uS[m]), f2df(uW0[m]), f2df(uZp[m]), f2df(uW1[m]), f2df(uZq[m])));
 #pragma unroll
         for (int m = 0; m < C::RU; ++m)
           if (upd_r[m] < C::NO) (&sm.S[0][0])[uslot[m]] = uN[m];
@@ -421,7 +455,7 @@ struct P3 {
         for (int r = r_lo + u; r <= r_hi; r += C::LS) {
           const int t = (side ? r - s : s - 1 - r) & (C::RB - 1);
           double* dst = &sm.rrhs[side][t];
-          const df v = df_from_double(*dst);
+          const df v = A::from_double(*dst);
           *reinterpret_cast<float2*>(dst) = make_float2(v.hi, v.lo);
           sm.ract[side][t] = a.act ? __ldcg(a.act + (size_t)dsys * n + r) : 0;
         }
@@ -468,11 +502,11 @@ struct P3 {
       if (u < C::NO) {
         const int so = u < B ? wrap(base + u) : C::W + wrap(base + u - B);
         const float4 wv = lv[u];
-        F[so * C::NC] = df2f(df_sub_two_prods(f2df(F[so * C::NC]), make_df(wv.x, wv.y), yp, make_df(wv.z, wv.w), yq));
+        F[so * C::NC] = df2f(A::sub_two_prods(f2df(F[so * C::NC]), make_df(wv.x, wv.y), yp, make_df(wv.z, wv.w), yq));
       } else if (u == C::NO) {
         const float4 r0 = lv[C::NO], r1 = lv[C::NO + 1];
-        const df cp = df_sub_two_prods(df_zero(), df_neg(make_df(r0.x, r0.y)), yp, df_neg(make_df(r0.z, r0.w)), yq);
-        const df cq = df_sub_two_prods(df_zero(), df_neg(make_df(r1.x, r1.y)), yp, df_neg(make_df(r1.z, r1.w)), yq);
+        const df cp = A::sub_two_prods(df_zero(), df_neg(make_df(r0.x, r0.y)), yp, df_neg(make_df(r0.z, r0.w)), yq);
+        const df cq = A::sub_two_prods(df_zero(), df_neg(make_df(r1.x, r1.y)), yp, df_neg(make_df(r1.z, r1.w)), yq);
         stk[(size_t)k * C::SL + C::NO] = make_float4(cp.hi, cp.lo, cq.hi, cq.lo);
       }
       __syncwarp();
@@ -518,7 +552,7 @@ struct P3 {
     df pend_x = df_zero();
     int pend_row = -1;
     auto store_x = [&](df xv, int row) {
-      double d = df_to_double(xv);
+      double d = A::to_double(xv);
       if (!isfinite(d) && flag == 0) flag = EHL_INFO_NONFINITE;
       if (a.mode == 1) d = d > 0.0 ? d : 0.0;
       if (real && row < n) xs[row] = d;
@@ -537,7 +571,7 @@ struct P3 {
       if (u < 2) {
         const float4 cv = sm.u.stk[v & (C::RB - 1)][C::NO];  // folded rhs column: Pi^-1 y
         const df c = u ? make_df(cv.z, cv.w) : make_df(cv.x, cv.y);
-        const df xv = df_sub(c, f2df(sm.acc[km][u]));
+        const df xv = A::sub(c, f2df(sm.acc[km][u]));
         sm.xpq[u] = df2f(xv);
         sm.acc[km][u] = make_float2(0.f, 0.f);
         // the float64 conversion and store of the previous level run here, off
@@ -559,7 +593,7 @@ struct P3 {
           const int slot = kn % C::W;
           const df acc = f2df(sm.acc[slot][side]);
           sm.acc[slot][side] =
-              df2f(df_sub_two_prods(acc, df_neg(m1), f2df(sm.xpq[0]), df_neg(m2), f2df(sm.xpq[1])));
+              df2f(A::sub_two_prods(acc, df_neg(m1), f2df(sm.xpq[0]), df_neg(m2), f2df(sm.xpq[1])));
         }
       }
       __syncwarp();
@@ -578,12 +612,12 @@ struct P3 {
     int changed = 0;
     if (real) {
       for (int i = u; i < n; i += C::LS) {
-        df w = df_neg(df_from_double(a.rhs[(size_t)dsys * n + i]));
+        df w = df_neg(A::from_double(a.rhs[(size_t)dsys * n + i]));
 #pragma unroll
         for (int q = 0; q < C::BW; ++q) {
           const int c = i - B + q;
           if (c >= 0 && c < n)
-            w = df_fma(df_from_double(__ldg(bsys + (size_t)i * C::BW + q)), df_from_double(__ldcg(xs + c)), w);
+            w = A::fma(A::from_double(__ldg(bsys + (size_t)i * C::BW + q)), A::from_double(__ldcg(xs + c)), w);
         }
         const int old = __ldcg(as + i);
         const double xi = __ldcg(xs + i);
@@ -606,7 +640,7 @@ struct P3 {
 // no other global stores, so every warp barrier and shuffle sees a full warp.
 // Mode 2 runs active-set steps until no group of the warp changes its set (a
 // converged group re-solves with the same set, reproducing the same x).
-template <int B>
+template <int B, bool F32>
 __global__ void __launch_bounds__(32 * C3<B>::WARPS, 4) paqif3_kernel(Paqif3Args a) {
   using C = C3<B>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -621,11 +655,11 @@ __global__ void __launch_bounds__(32 * C3<B>::WARPS, 4) paqif3_kernel(Paqif3Args
   bool more = real;
   const int max_solves = (a.mode == 2) ? kPaqifMaxActiveSetSteps : 1;
   for (int it = 0; it < max_solves; ++it) {
-    P3<B>::factor(sm, a, dsys, ssys, u, flag);
-    P3<B>::z_solve(sm, a, dsys, ssys, real, u, flag);
+    P3<B, F32>::factor(sm, a, dsys, ssys, u, flag);
+    P3<B, F32>::z_solve(sm, a, dsys, ssys, real, u, flag);
     if (more) ++solves;
     if (a.mode != 2) break;
-    if (!P3<B>::active_set_update(a, dsys, real, u)) more = false;
+    if (!P3<B, F32>::active_set_update(a, dsys, real, u)) more = false;
     if (!__any_sync(0xffffffffu, more)) break;
   }
   // the first nonzero flag among the group's lanes
@@ -644,7 +678,7 @@ __global__ void __launch_bounds__(32 * C3<B>::WARPS, 4) paqif3_kernel(Paqif3Args
 
 // Solve only, with the factorization stored by a factor launch (same systems,
 // same band): the W0 sweep for the new rhs, then the Z0 sweep.
-template <int B>
+template <int B, bool F32>
 __global__ void __launch_bounds__(32 * C3<B>::WARPS, 4) paqif3_solve_kernel(Paqif3Args a) {
   using C = C3<B>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -656,8 +690,8 @@ __global__ void __launch_bounds__(32 * C3<B>::WARPS, 4) paqif3_solve_kernel(Paqi
   const int dsys = real ? ssys : a.n_sys - 1;
   if (__all_sync(0xffffffffu, !real)) return;
   int flag = 0;
-  P3<B>::w_sweep(sm, a, dsys, ssys, u);
-  P3<B>::z_solve(sm, a, dsys, ssys, real, u, flag);
+  P3<B, F32>::w_sweep(sm, a, dsys, ssys, u);
+  P3<B, F32>::z_solve(sm, a, dsys, ssys, real, u, flag);
   int f = flag;
 #pragma unroll
   for (int off = C::LS / 2; off > 0; off >>= 1) {
@@ -727,9 +761,13 @@ static cudaError_t p3_attrs() {
   const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
   if (bit && (set.load(std::memory_order_acquire) & bit)) return cudaSuccess;
   const int smem = (int)p3_smem<B>();
-  e = cudaFuncSetAttribute(paqif3_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(paqif3_kernel<B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(paqif3_solve_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(paqif3_solve_kernel<B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(paqif3_kernel<B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(paqif3_solve_kernel<B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess && bit) set.fetch_or(bit, std::memory_order_release);
   return e;
 }
@@ -768,11 +806,18 @@ static cudaError_t launch3(const PaqifLaunch& L, cudaStream_t st, void* fstore, 
   const int grid = (L.n_sys + per - 1) / per;
   cudaError_t e = p3_attrs<B>();
   if (e != cudaSuccess) return e;
+  const bool f32 = L.f32 && L.mode != 2;
   if (solve_only) {
-    paqif3_solve_kernel<B><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
+    if (f32)
+      paqif3_solve_kernel<B, true><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
+    else
+      paqif3_solve_kernel<B, false><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
     note_launch();
   } else {
-    paqif3_kernel<B><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
+    if (f32)
+      paqif3_kernel<B, true><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
+    else
+      paqif3_kernel<B, false><<<grid, 32 * C3<B>::WARPS, smem, st>>>(a);
     note_launch();
   }
   return cudaGetLastError();
