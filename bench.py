@@ -46,10 +46,10 @@ PAQIF_NSYS, PAQIF_N, PAQIF_BETA, PAQIF_MODE = 4096, 1024, 4, 1
 EHL = dict(N=1025, M=200.0, L=10.0, limiter=1, beta=8, tol=1e-8)
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes (read + write) of one full-size paqif3_kernel<4> launch from the ncu
+# DRAM bytes (read + write) of one full-size paqif3_kernel<4, double-float> launch from the ncu
 # capture summarised in profiles/, valid only for the kernel sources with these
 # sha256 prefixes; any other source reports traffic = null.
-PAQIF_TRAFFIC = {("03fe5598e85142b3", "4addd33d7cfa0c6e"): 601213440 + 328103680}
+PAQIF_TRAFFIC = {("97392e4659d05644", "4addd33d7cfa0c6e"): 601079296 + 328132608}
 
 
 def paqif_traffic():
@@ -235,7 +235,8 @@ def run_ours(args):
         _, Hp, _ = ctx.residual(sol["P"], sol["H0"])
         rs_m = out_m[3].abs().cpu().numpy()
         mixed = {"precision": "Krylov products K v as a float32 GEMM emulated on BF16 tensor cores "
-                              "(cuBLAS, 3xBF16 split); residual, PAQIF and update in float64 / double-float",
+                              "(cuBLAS, 3xBF16 split) and float32 PAQIF preconditioner sweeps; residual, "
+                              "line search and update in float64",
                  "value": round(world * B / (ms_m * 1e-3), 3), "unit": "converged solves/s", "ms": round(ms_m, 3),
                  "all_converged": int(out_m[4]) == 0, "max_final_residual": float(rs_m.max()),
                  "H_rel_err_vs_plain": float((Hm - Hp).abs().max() / Hp.abs().max())}
@@ -322,7 +323,8 @@ def run_ours(args):
 
 # ------------------------------------------------------------- the other configs
 PRECISION = {0: "Krylov products in double-float (plain path)",
-             2: "Krylov products as float32 GEMMs emulated on BF16 tensor cores (cuBLAS); residual float64"}
+             2: "Krylov products as float32 GEMMs emulated on BF16 tensor cores (cuBLAS), float32 PAQIF "
+                "preconditioner sweeps in line contact; residual float64"}
 
 def _timed(torch, fn, reps=1, warm=1):
     """CUDA-event time (ms, best of reps) of fn() after warm calls, and fn's last result."""
