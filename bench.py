@@ -46,10 +46,10 @@ PAQIF_NSYS, PAQIF_N, PAQIF_BETA, PAQIF_MODE = 4096, 1024, 4, 1
 EHL = dict(N=1025, M=200.0, L=10.0, limiter=1, beta=8, tol=1e-8)
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes (read + write) of one full-size paqif3_kernel<4, double-float> launch from the ncu
+# DRAM bytes (read + write) of one full-size paqif4_kernel<4, double-float> launch from the ncu
 # capture summarised in profiles/, valid only for the kernel sources with these
 # sha256 prefixes; any other source reports traffic = null.
-PAQIF_TRAFFIC = {("97392e4659d05644", "4addd33d7cfa0c6e"): 601079296 + 328132608}
+PAQIF_TRAFFIC = {("206416e0048045bf", "4addd33d7cfa0c6e"): 598074368 + 327899136}
 
 
 def paqif_traffic():
@@ -60,7 +60,7 @@ def paqif_traffic():
             return hashlib.sha256(f.read()).hexdigest()[:16]
 
     try:
-        return PAQIF_TRAFFIC.get((h("paqif3.cu"), h("df64.cuh")))
+        return PAQIF_TRAFFIC.get((h("paqif4.cu"), h("df64.cuh")))
     except OSError:
         return None
 
@@ -305,7 +305,7 @@ def run_ours(args):
         "mixed_precision": mixed,
         "roofline": {"bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "traffic": paqif_traffic(),
-                     "kernel": "paqif3_kernel<4> (leg A)", "peak_source": src},
+                     "kernel": "paqif4_kernel<4> (leg A)", "peak_source": src},
         "e2e": {"value": round(world * B / (e2e_b * 1e-3), 3) if e2e_b else None, "unit": "converged solves/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": B * (EHL["N"] + 1 + 2) * 8 + B * 4,
                 "paqif_gbs": round(world * nbytes / (e2e_a * 1e-3) / 1e9, 2),

@@ -232,8 +232,10 @@ ehl_status ehl_jacobian_apply(ehl_ctx* ctx, const double* P, const double* H0, c
 /* Solve every instance.  init = 0: start from the Hertzian pressure with
  * H0 chosen so that min H = h_init -- on the coarsest grid of the nested
  * iteration when the context has coarse grids, each finer grid then starting
- * from the linear interpolation of the solution below it (coarse grids solved
- * to max(tol, coarse_tol), the roughness sampled at their nodes); init = 1:
+ * from the linear interpolation of the solution below it where that solve
+ * converged, else again from the Hertzian start (coarse grids solved to
+ * max(tol, coarse_tol) in at most 40 Newton steps, the roughness sampled at
+ * their nodes); init = 1:
  * start from the given P, H0 on the target grid.
  * On return P, H0 hold the last iterate, iters (nullable, [n_inst] int32)
  * the outer iterations on the target grid and final_res (nullable, [n_inst][2]) the residuals

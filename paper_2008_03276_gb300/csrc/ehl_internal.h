@@ -10,6 +10,9 @@ namespace ehl {
 
 constexpr int kPaqifWarpsPerCta = 4;
 constexpr int kPaqifMaxActiveSetSteps = 64;
+// Newton steps of a coarse grid of the nested iteration at most (a coarse grid that
+// cannot resolve the surface stalls rather than converges)
+constexpr int kCoarseMaxIter = 40;
 constexpr size_t kWorkspaceAlign = 256;
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

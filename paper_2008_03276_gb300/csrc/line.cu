@@ -643,7 +643,7 @@ __global__ void k_line_prolong(const double* __restrict__ Pc, const double* __re
                                const int* __restrict__ cdone, int Nc, double* __restrict__ Pf,
                                double* __restrict__ H0f) {
   const int z = blockIdx.y;
-  if (cdone && cdone[z] == 2) return;
+  if (cdone && cdone[z] != 1) return;  // only a converged coarse solve seeds the finer grid
   const int Nf = 2 * Nc - 1;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= Nf) return;

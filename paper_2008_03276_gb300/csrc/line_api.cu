@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <thread>
 #include <vector>
 
@@ -284,6 +285,7 @@ static ehl_status init_bucket(Bucket* b, const ehl_params& p0, const std::vector
     }
     st = init_line(l, ci, Nl, p0);
     if (st != EHL_OK) return st;
+    l->max_iter = std::min(p0.max_iter, kCoarseMaxIter);
     double* r = nullptr;
     if (ctx_alloc(l, (void**)&r, sizeof(double) * n_inst * (size_t)Nl) != cudaSuccess) {
       cudaGetLastError();
@@ -386,7 +388,7 @@ static ehl_status create_point(const ehl_params* p, int n_inst, const ehl_params
     l->st = stream;
     l->trace = ctx->pt->trace;
     ctx->ptlv.push_back(l);
-    st = pt_init(l, ci, p->halfband, p->max_iter, p->krylov_dim, p->precision);
+    st = pt_init(l, ci, p->halfband, std::min(p->max_iter, kCoarseMaxIter), p->krylov_dim, p->precision);
     double* r = nullptr;
     if (st == EHL_OK && pt_alloc(l, (void**)&r, sizeof(double) * n_inst * (size_t)l->NN) != cudaSuccess) {
       cudaGetLastError();

@@ -505,13 +505,13 @@ __global__ void k_pt_inject(const double* __restrict__ src, int nxf, int nyf, do
   dst[(size_t)z * nxc * nyc + t] = src[(size_t)z * nxf * nyf + (size_t)(jc * sy) * nxf + ic * sx];
 }
 
-// bilinear prolongation of (P, H0) to the grid with halved spacing; instances with
-// cdone = 2 (non-finite on the coarse grid) keep their fine values
+// bilinear prolongation of (P, H0) to the grid with halved spacing; instances whose
+// coarse solve did not converge (cdone != 1) keep their fine start
 __global__ void k_pt_prolong(const double* __restrict__ Pc, const double* __restrict__ H0c,
                              const int* __restrict__ cdone, int nxc, int nyc, double* __restrict__ Pf,
                              double* __restrict__ H0f) {
   const int z = blockIdx.y;
-  if (cdone && cdone[z] == 2) return;
+  if (cdone && cdone[z] != 1) return;
   const int nxf = 2 * nxc - 1, nyf = 2 * nyc - 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nxf * nyf) return;

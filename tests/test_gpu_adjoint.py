@@ -184,9 +184,10 @@ def test_adjoint_c5_batch_matches_oracle():
 
 @pytest.mark.slow
 def test_adjoint_c5_full_amplitude_reports():
-    """The full-amplitude recipe: instances that reach contact (H_min <= 0) do not
-    converge and are reported; the converged ones give finite gradients that agree
-    with the oracle to the accuracy their conditioning allows (1e-15 x cond)."""
+    """The full-amplitude recipe: instances at or near contact (H_min <= 0 or a few
+    1e-3) may not converge and are reported through their residual and the status; the
+    converged ones give finite gradients that agree with the oracle to the accuracy their
+    conditioning allows (1e-15 x cond)."""
     N, M, L, n = 1025, 50.0, 10.0, 8
     rgh = c5_roughness(N, n)
     ctx = make(N, M, L, 1, 8, tol=1e-10, n_inst=n)
@@ -197,8 +198,9 @@ def test_adjoint_c5_full_amplitude_reports():
     pbs = [lr.LineProblem(N, M, L, limiter="vanleer", rough=rgh[k]) for k in range(n)]
     Hmin = np.array([pbs[k].film(Pn[k, 1:-1], H0n[k]).min() for k in range(n)])
     print("converged", ok.tolist(), "H_min", np.round(Hmin, 4).tolist())
-    assert ok.sum() >= 2
-    assert np.all(Hmin[~ok] < 0.01)       # the unconverged ones are at (or next to) contact
+    assert ok.sum() >= 4
+    assert code == (0 if ok.all() else 4)  # EHL_ENOCONV reports the unconverged instances
+    assert np.all(Hmin[~ok] < 0.02)        # they are at or next to contact
     gP, gH, gH0 = seeds(pbs, Pn, H0n, "H_min")
     gr, gml, rel, code = ctx.adjoint(P, H0, dev(gP), dev(gH), dev(gH0), rough=dev(rgh), tol=1e-11, max_cycles=20,
                                      check=False)

@@ -19,8 +19,9 @@ def dev(a):
 
 
 def make(n, M=20.0, L=10.0, limiter=0, beta=2, tol=1e-11, n_inst=1, per=None, levels=-1, **kw):
-    q = dict(nx=n, ny=n, limiter=limiter, halfband=beta, method=1, tol=tol, max_iter=80, krylov_dim=40,
-             levels=levels, coarse_min_nodes=17, **kw)
+    q = dict(nx=n, ny=n, limiter=limiter, halfband=beta, method=1, tol=tol, max_iter=80, levels=levels,
+             coarse_min_nodes=17)
+    q.update({"krylov_dim": 40, **kw})
     p = ops.default_params(2, M=M, L=L, **q)
     per_inst = None if per is None else [ops.default_params(2, **q, **d) for d in per]
     return ops.Context(p, n_inst=n_inst, per_inst=per_inst)
@@ -125,7 +126,9 @@ def test_point_solve_matches_oracle(oracle_33, levels, beta, precision):
 @pytest.mark.slow
 def test_point_solve_129_properties():
     n = 129
-    ctx = make(n, M=100.0, L=10.0, limiter=1, beta=4, tol=1e-8)
+    # the x-line preconditioner leaves the y-coupling to GMRES: at 129^2 a 40-vector basis is
+    # marginal (the Newton iteration can stall at |Phi| ~ 1e-11), the library default is 100
+    ctx = make(n, M=100.0, L=10.0, limiter=1, beta=4, tol=1e-8, krylov_dim=100)
     P, H0, iters, res, code = ctx.solve(check=False)
     print(f"129^2: code {code} iters {iters.tolist()} res {res.tolist()}")
     assert code == 0
@@ -187,13 +190,16 @@ def test_point_adjoint_129_vs_resolved_differences():
         _, H, _ = cx.residual(Pp, H0p, dev(rgx[None]))
         return float(H[0, cj, ci].cpu())
 
-    d = 1e-6
-    for node in ((cj, ci), (cj + 3, ci - 4)):
+    # a re-solve to tol 1e-12 reproduces H_c to a few 1e-11 (its rounding floor: 2.8e-11
+    # measured), so a central difference with step d carries an error up to eps_h / d: the
+    # small off-centre gradient (1e-3 of the central one) takes a wider step
+    eps_h = 5e-11
+    for node, d in (((cj, ci), 1e-6), ((cj + 3, ci - 4), 1e-4)):
         rp, rm = rg.copy(), rg.copy()
         rp[node] += d
         rm[node] -= d
         fd = (hc(rp) - hc(rm)) / (2 * d)
-        assert abs(fd - gr[node]) <= 1e-5 * abs(fd) + 1e-7 * np.max(np.abs(gr)), (node, fd, gr[node])
+        assert abs(fd - gr[node]) <= 1e-5 * abs(fd) + eps_h / d, (node, fd, gr[node])
     # M enters smoothly; a wider step keeps the re-solves' rounding floor (~1e-11 in H_c) out of the difference
     dm = 1e-4
     fd = (hc(rg, M_=M * (1 + dm)) - hc(rg, M_=M * (1 - dm))) / (2 * dm * M)
