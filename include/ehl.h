@@ -105,6 +105,37 @@ ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* band, const
                            void* workspace, size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Partitioned PAQIF
+ * ------------------------------------------------------------------------
+ * Defines: Sec. 2.1 (Eqs. eqn15, eqnn16: the system cut into r diagonal
+ * blocks L0^(m) coupled through their first and last beta unknowns) and
+ * Sec. 2.2.4 Steps 1-7 (each block factored and swept over its interior, a
+ * reduced system of order 2 beta r for the blocks' outer unknowns, the
+ * interiors solved from them).  The reduced system is solved by block
+ * elimination without pivoting (not by the normal equations of Step 4), and
+ * the projection of modes 1 and 2 (Steps 5, 7) is applied after the full
+ * solve, so every admissible r gives the result of ehl_paqif_solve up to
+ * rounding.
+ *
+ * Same arguments and semantics as ehl_paqif_solve, plus
+ *   partitions  r >= 1 blocks per system; 0 chooses r from the batch shape
+ *               (what ehl_paqif_solve does).  The blocks have the even order
+ *               n_p = 2 ceil(n / 2r); an admissible r divides the lane groups
+ *               of one CTA (4 warps of 32 / (2 beta + 2) groups: 32, 20, 16,
+ *               12, 8, 8, 8, 4 for beta = 1..8), and for r > 1 each block
+ *               has n_p >= 2 beta + 2 and at least one row below n.
+ * Returns EHL_EINVAL for an inadmissible r, otherwise as ehl_paqif_solve.
+ * The workspace size depends on r (ehl_paqif_workspace_size_partitioned).
+ */
+ehl_status ehl_paqif_workspace_size_partitioned(int n_sys, int n, int beta, int partitions, int mode,
+                                                size_t* bytes);
+
+ehl_status ehl_paqif_solve_partitioned(int n_sys, int n, int beta, int partitions, const double* band,
+                                       const double* rhs, const uint8_t* active, int mode, double* x,
+                                       int* iters, int* info, void* workspace, size_t workspace_bytes,
+                                       void* stream);
+
+/* ------------------------------------------------------------------------
  * EHL problem: context, residual, band Jacobian, solve
  * ------------------------------------------------------------------------
  * The problem statement is the paper's: given load and lubricant parameters
@@ -151,7 +182,7 @@ typedef struct {
                         /* 1: Newton-Krylov, PAQIF band preconditioner (default)         */
   double tol;           /* converged when ||min(P,R)||_inf <= tol and |h sum P - pi/2| <= tol */
   int max_iter;         /* cap on outer iterations                                      */
-  int krylov_dim;       /* GMRES basis size per Newton step (method 1; 40 line, 100 point) */
+  int krylov_dim;       /* GMRES basis size per Newton step (method 1; 40 line, 200 point) */
   double h_init;        /* Hertzian start: H0 chosen so that min H = h_init             */
   int levels;           /* nested iteration: coarse grids solved first (init = 0 only);  */
                         /*   -1 as many as allowed (default), 0 none                     */

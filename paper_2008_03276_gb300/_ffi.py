@@ -37,6 +37,12 @@ SYMBOLS = {
     "ehl_paqif_solve": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "ehl_paqif_workspace_size_partitioned": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                            ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "ehl_paqif_solve_partitioned": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "ehl_params_default": (None, [ctypes.POINTER(EhlParams), ctypes.c_int]),
     "ehl_create": (ctypes.c_int, [ctypes.POINTER(EhlParams), ctypes.c_int, ctypes.POINTER(EhlParams),
                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),

@@ -45,20 +45,27 @@ static bool paqif_args_ok(int n_sys, int n, int beta, int mode) {
 
 static size_t paqif_act_bytes(int n_sys, int n) { return (size_t)n_sys * (size_t)n * sizeof(int); }
 
-extern "C" ehl_status ehl_paqif_workspace_size(int n_sys, int n, int beta, int mode, size_t* bytes) {
-  if (!bytes || !paqif_args_ok(n_sys, n, beta, mode)) return EHL_EINVAL;
-  *bytes = align_up(paqif_stack_bytes(n_sys, n, beta), kWorkspaceAlign) +
+extern "C" ehl_status ehl_paqif_workspace_size_partitioned(int n_sys, int n, int beta, int partitions, int mode,
+                                                          size_t* bytes) {
+  if (!bytes || !paqif_args_ok(n_sys, n, beta, mode) || partitions < 0) return EHL_EINVAL;
+  if (paqif_parts(n_sys, n, beta, partitions) < 0) return EHL_EINVAL;
+  *bytes = align_up(paqif_stack_bytes(n_sys, n, beta, partitions), kWorkspaceAlign) +
            align_up(paqif_act_bytes(n_sys, n), kWorkspaceAlign);
   return EHL_OK;
 }
 
-extern "C" ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* band, const double* rhs,
-                                      const uint8_t* active, int mode, double* x, int* iters, int* info,
-                                      void* workspace, size_t workspace_bytes, void* stream) {
+extern "C" ehl_status ehl_paqif_workspace_size(int n_sys, int n, int beta, int mode, size_t* bytes) {
+  return ehl_paqif_workspace_size_partitioned(n_sys, n, beta, 0, mode, bytes);
+}
+
+extern "C" ehl_status ehl_paqif_solve_partitioned(int n_sys, int n, int beta, int partitions, const double* band,
+                                                  const double* rhs, const uint8_t* active, int mode, double* x,
+                                                  int* iters, int* info, void* workspace, size_t workspace_bytes,
+                                                  void* stream) {
   if (!band || !rhs || !x || !paqif_args_ok(n_sys, n, beta, mode)) return EHL_EINVAL;
   if ((const void*)x == (const void*)band || (const void*)x == (const void*)rhs) return EHL_EINVAL;
   size_t need = 0;
-  ehl_paqif_workspace_size(n_sys, n, beta, mode, &need);
+  if (ehl_paqif_workspace_size_partitioned(n_sys, n, beta, partitions, mode, &need) != EHL_OK) return EHL_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   bool owned = false;
   if (workspace) {
@@ -83,9 +90,10 @@ extern "C" ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* 
   L.x = x;
   L.iters = iters;
   L.info = info;
+  L.parts = partitions;
   cudaError_t e = cudaSuccess;
   if (active || mode == 2) {
-    L.act = (int*)(ws + align_up(paqif_stack_bytes(n_sys, n, beta), kWorkspaceAlign));
+    L.act = (int*)(ws + align_up(paqif_stack_bytes(n_sys, n, beta, partitions), kWorkspaceAlign));
     e = launch_expand_active(active, L.act, (size_t)n_sys * (size_t)n, st);
   }
   if (e == cudaSuccess) e = launch_paqif(L, st);
@@ -95,4 +103,11 @@ extern "C" ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* 
     return EHL_ECUDA;
   }
   return EHL_OK;
+}
+
+extern "C" ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* band, const double* rhs,
+                                      const uint8_t* active, int mode, double* x, int* iters, int* info,
+                                      void* workspace, size_t workspace_bytes, void* stream) {
+  return ehl_paqif_solve_partitioned(n_sys, n, beta, 0, band, rhs, active, mode, x, iters, info, workspace,
+                                     workspace_bytes, stream);
 }

@@ -94,7 +94,7 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   p->method = 1;
   p->tol = 1e-8;
   p->max_iter = 200;
-  p->krylov_dim = dim == 2 ? 100 : 40;  // the x-line preconditioner leaves the y-coupling to GMRES
+  p->krylov_dim = dim == 2 ? 200 : 40;  // the x-line preconditioner leaves the y-coupling to GMRES
   p->h_init = 0.05;
   p->levels = -1;
   p->coarse_min_nodes = 65;

@@ -1,15 +1,31 @@
 // paqif4.cu -- batched PAQIF (projected alternate quadrant interlocking factorization),
-// one lane per row of the elimination window.
+// one lane per row of the elimination window, r partitions per system.
 //
-// Method (Sec. 2.2.1-2.2.3; projection of Sec. 2.2.2 / Sec. 2.2.4 Steps 5
-// and 7 after the solve, one partition per system): for n = 2s, level
-// k = 0..s-1 pivots on the rows/columns at stream index k of the two sides
-// (rows s-1-k and s+k) of the Schur complement L0^(k); the Z0 rows are the
-// pivot rows, the W0 columns solve
+// Method (Sec. 2.2.1-2.2.3): for a block of order 2s, level k = 0..s-1 pivots
+// on the rows/columns at stream index k of the two sides (rows s-1-k and s+k)
+// of the Schur complement L0^(k); the Z0 rows are the pivot rows, the W0
+// columns solve
 //   z_pp w_ip + z_qp w_iq = l_ip,   z_pq w_ip + z_qq w_iq = l_iq,
 // and L0^(k+1) = L0^(k) - w_p z_p^T - w_q z_q^T.  W0 Y = F runs in the same
 // middle-out sweep; Z0 U = Y runs from both ends towards the middle with one
 // 2x2 solve per level.
+//
+// Partitioning (Sec. 2.1, Eq. eqnn16; Sec. 2.2.4 Steps 1-7): a system is cut
+// into r diagonal blocks L0^(m) of order n_p.  Each block is factored and
+// swept only over its interior levels (Steps 1, 2); because the middle-out
+// order eliminates the interior first, what is left in the window is the
+// Schur complement of the block on its first and last b unknowns, with the
+// transformed right-hand side.  Those 2b r unknowns satisfy a reduced system:
+// the Schur complements on the block diagonal, and the untouched band
+// entries that couple the last b rows of a block with the first b columns of
+// the next one (and vice versa) off it (Steps 3, 4: the paper's reduced
+// system premultiplied by the inverse of W0's outer block, same solution).
+// It is block tridiagonal with b x b blocks and is solved by block
+// elimination without pivoting (instead of the paper's normal equations,
+// which square its conditioning).  The Z0 sweep of each block then starts
+// from the known outer unknowns (Step 6).  The projection onto U >= 0
+// (Steps 5, 7) is applied once, after the full solve, so the result does not
+// depend on r.
 //
 // GB300 mapping:
 //  * for half-band b only the window of the Schur complement on the stream
@@ -23,12 +39,14 @@
 //    multipliers w = [l_p, l_q] Pi^-1 and updates its entries, a pivot row
 //    forms its side of the folded outer columns Pi^-1 [z_p; z_q] for the stack,
 //    both as  out = base - (alpha z_p + beta z_q).
-//  * band rows stream from HBM with cp.async into a 32-row ring per side,
-//    16 levels ahead, converted float64 -> double-float once, in place, by
-//    the lane that copied them.
+//  * band rows stream from HBM with cp.async into a ring per side, converted
+//    float64 -> double-float once, in place, by the lane that copied them.
 //  * the Z0 and W0 sweeps rotate roles instead of data: the lane that owns a
 //    row slot accumulates the terms of the level that slot holds next, and the
 //    solved pair of each level is broadcast with warp shuffles.
+//  * the r blocks of a system are r groups of one CTA; the reduced system is
+//    assembled in shared memory and solved by the group of block 0 between two
+//    CTA barriers.
 //  * arithmetic is double-float (df64.cuh); float64 only at the interface.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -42,17 +60,26 @@ namespace ehl {
 
 template <int B>
 struct C4 {
-  static constexpr int W = B + 1;       // row slots per side (stream indices k..k+b)
-  static constexpr int GS = 2 * W;      // lanes per system, one per window row
-  static constexpr int G = 32 / GS;     // systems per warp
-  static constexpr int NC = GS + 1;     // window columns: (side, distance) then the rhs
-  static constexpr int RHS = GS;        // column index of the rhs
-  static constexpr int BW = 2 * B + 1;  // band row width
-  static constexpr int SL = 2 * B + 1;  // stack float4 per level: (M_p, M_q) per outer column, rhs last
-  static constexpr int FL = GS;         // factor-store float4 per level: one per row slot
-  static constexpr int RB = 32;         // ring rows per side
-  static constexpr int CH = 8;          // rows per chunk
+  static constexpr int W = B + 1;             // row slots per side (stream indices k..k+b)
+  static constexpr int GS = 2 * W;            // lanes per block, one per window row
+  static constexpr int G = 32 / GS;           // groups per warp
+  static constexpr int NC = GS + 1;           // window columns: (side, distance) then the rhs
+  static constexpr int RHS = GS;              // column index of the rhs
+  static constexpr int BW = 2 * B + 1;        // band row width
+  static constexpr int SL = 2 * B + 1;        // stack float4 per level: (M_p, M_q) per outer column, rhs last
+  static constexpr int FL = GS;               // factor-store float4 per level: one per row slot
+  static constexpr int RB = (B <= 4) ? 16 : 32;  // ring rows per side
+  static constexpr int CH = RB / 4;           // rows per chunk (b <= CH keeps the live window in the ring)
   static constexpr int WARPS = kPaqifWarpsPerCta;
+  static constexpr int GPC = WARPS * G;       // groups per CTA
+  static constexpr int BB = B * B;
+};
+
+// reduced-system blocks of one partition: blocks 2m (first b rows) and 2m+1
+// (last b rows), each with its sub-diagonal, diagonal and super-diagonal b x b block
+template <int B>
+struct RedBlk {
+  float2 T[2][3][B * B];
 };
 
 template <int B>
@@ -63,21 +90,46 @@ struct __align__(16) Sm4 {
     double ring[2][C::RB][C::BW];  // band rows: float64 as copied, double-float after conversion
     float4 stk[C::RB][C::SL];      // Z0 sweep: stack levels
     float4 fr[C::RB][C::FL];       // W0 sweep of a resolve: factor-store levels
+    RedBlk<B> red;                 // reduced system, between the sweeps
   } u;
   double rrhs[2][C::RB];
   int ract[2][C::RB];
+  float2 fo[2 * B];  // transformed rhs of the block's outer rows (first b rows, then last b)
+  float2 xo[2 * B];  // their solution
+  int flag;
+  int more;
 };
 
 struct Paqif4Args {
-  int n_sys, n, s, mode;
+  int n_sys, n, mode;
+  int r, np, sp, sf;  // blocks per system, block order (even), its levels, levels swept per block
+  int spc;            // systems per CTA
   const double* band;
   const double* rhs;
   int* act;
-  float4* stack;   // [pad_sys][s][SL]
-  float4* fstore;  // [pad_sys][s][FL]: multipliers and Pi^-1 rows (factor once, solve many), or null
+  float4* stack;   // [groups][sp][SL]
+  float4* fstore;  // [groups][sp][FL]: multipliers and Pi^-1 rows (factor once, solve many), or null
+  float2* rstore;  // [systems][2r][3][b^2]: reduced factors L_b, D_b^-1, U_b (with fstore), or null
   double* x;
   int* iters;
   int* info;
+};
+
+// one block of one system, as a PAQIF problem of its own
+struct Part4 {
+  const double* band;  // first row of the block
+  const double* rhs;
+  const int* act;
+  double* x;
+  float4* stk;
+  float4* fst;
+  int n;     // real rows of the block (rows n..2s-1 are identity rows)
+  int s;     // levels of the block
+  int sf;    // levels swept (s for one block per system, s - b with a reduced system)
+  int m, r;  // block index, blocks per system
+  int mode;
+  int ng;    // order of the system
+  int row0;  // first row of the block in the system
 };
 
 __device__ __forceinline__ void cpa8(void* smem, const void* gmem) {
@@ -167,11 +219,9 @@ struct P4 {
   // Copy (CONVERT = false) or convert in place (CONVERT = true) chunk c of
   // both sides; the lane of rank u handles elements u, u + GS, ...
   template <bool CONVERT>
-  static __device__ __forceinline__ void chunk(Sm4<B>& sm, const Paqif4Args& a, int dsys, int c, const L& ln) {
+  static __device__ __forceinline__ void chunk(Sm4<B>& sm, const Part4& p, int c, const L& ln) {
     if (!ln.live) return;
-    const int s = a.s, n = a.n, u = ln.u;
-    const double* bsys = a.band + (size_t)dsys * n * C::BW;
-    const double* rsys = a.rhs + (size_t)dsys * n;
+    const int s = p.s, n = p.n, u = ln.u;
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       const int t0 = c * C::CH;
@@ -189,7 +239,7 @@ struct P4 {
           const df v = A::from_double(*dst);
           *reinterpret_cast<float2*>(dst) = make_float2(v.hi, v.lo);
         } else {
-          cpa8(dst, bsys + (size_t)r * C::BW + col);
+          cpa8(dst, p.band + (size_t)r * C::BW + col);
         }
       }
       for (int r = r_lo + u; r <= r_hi; r += C::GS) {
@@ -198,15 +248,15 @@ struct P4 {
         if (CONVERT) {
           const df v = A::from_double(*dst);
           *reinterpret_cast<float2*>(dst) = make_float2(v.hi, v.lo);
-          sm.ract[side][t & (C::RB - 1)] = a.act ? __ldcg(a.act + (size_t)dsys * n + r) : 0;
+          sm.ract[side][t & (C::RB - 1)] = p.act ? __ldcg(p.act + r) : 0;
         } else {
-          cpa8(dst, rsys + r);
+          cpa8(dst, p.rhs + r);
         }
       }
     }
   }
 
-  // 0: outside the matrix, 1: a real row, 2: an identity row (padding or active)
+  // 0: outside the block, 1: a real row, 2: an identity row (padding or active)
   static __device__ __forceinline__ int row_kind(const Sm4<B>& sm, int side, int t, int s, int n) {
     const int i = row_of(side, t, s);
     if (i < 0 || i >= 2 * s) return 0;
@@ -240,28 +290,31 @@ struct P4 {
   static __device__ __forceinline__ constexpr int sidx(int c) {
     return c == C::RHS ? 2 * B : (c / C::W) * B + (c % C::W) - 1;
   }
+  // index among the block's 2b outer unknowns (first b rows, then last b) of stream t on a side
+  static __device__ __forceinline__ int outer_index(int side, int t, int s) {
+    return side ? t - s + 2 * B : s - 1 - t;
+  }
 
   // ---------------------------------------------------------------- factor
-  // Levels 0..s-1 of L0 = W0 Z0 with the rhs column (W0 Y = F) along; the
-  // folded outer columns of every level go to the stack.
-  static __device__ void factor(Sm4<B>& sm, const Paqif4Args& a, int dsys, int ssys, const L& ln, int& flag) {
-    const int s = a.s, n = a.n;
+  // Levels 0..sf-1 of L0 = W0 Z0 with the rhs column (W0 Y = F) along; the
+  // folded outer columns of every level go to the stack.  With sf < s the
+  // window left over is the block's part of the reduced system.
+  static __device__ void factor(Sm4<B>& sm, const Part4& p, const L& ln, int& flag) {
+    const int s = p.s, n = p.n;
     const int sg = ln.side, j = ln.j;
-    float4* stk = a.stack + (size_t)ssys * s * C::SL;
-    float4* fst = a.fstore ? a.fstore + (size_t)ssys * s * C::FL : nullptr;
     // prologue: chunks 0..3 issued, 0 and 1 converted; afterwards chunks
     // [0, conv) are double-float and chunks up to conv+1 are issued
-    chunk<false>(sm, a, dsys, 0, ln);
+    chunk<false>(sm, p, 0, ln);
     cpa_commit();
-    chunk<false>(sm, a, dsys, 1, ln);
+    chunk<false>(sm, p, 1, ln);
     cpa_commit();
-    chunk<false>(sm, a, dsys, 2, ln);
+    chunk<false>(sm, p, 2, ln);
     cpa_commit();
-    chunk<false>(sm, a, dsys, 3, ln);
+    chunk<false>(sm, p, 3, ln);
     cpa_commit();
     cpa_wait<2>();
-    chunk<true>(sm, a, dsys, 0, ln);
-    chunk<true>(sm, a, dsys, 1, ln);
+    chunk<true>(sm, p, 0, ln);
+    chunk<true>(sm, p, 1, ln);
     __syncwarp();
     int conv = 2;
     // the window of level 0: this lane's row is stream index j; column
@@ -273,7 +326,7 @@ struct P4 {
       R[c] = (c == C::RHS) ? rhs_of(sm, sg, j, kind) : any_entry(sm, sg, j, c / C::W, c % C::W, kind, s, n);
 
     int pj = 0;  // k mod W: the row slot of the pivots
-    for (int k = 0; k < s; ++k) {
+    for (int k = 0; k < p.sf; ++k) {
       const bool piv = (j == pj);
       float4* zb = sm.zb[k & 1];
       // the two pivot rows to shared memory (double-buffered: one barrier a level)
@@ -300,7 +353,7 @@ struct P4 {
       const df wq = A::sub_two_prods(df_zero(), df_neg(lp), i01, df_neg(lq), i11);
       const df al = piv ? df_neg(sg ? i10 : i00) : wp;
       const df be = piv ? df_neg(sg ? i11 : i01) : wq;
-      if (fst && ln.live) fst[(size_t)k * C::FL + ln.u] = make_float4(al.hi, al.lo, be.hi, be.lo);
+      if (p.fst && ln.live) p.fst[(size_t)k * C::FL + ln.u] = make_float4(al.hi, al.lo, be.hi, be.lo);
       // rank-2 update of an outer row / folded outer columns of a pivot row
 #pragma unroll
       for (int c = 0; c < C::NC; ++c) {
@@ -308,7 +361,7 @@ struct P4 {
         const float4 z = zb[c];
         const df o = A::sub_two_prods(piv ? df_zero() : R[c], al, make_df(z.x, z.y), be, make_df(z.z, z.w));
         if (piv) {
-          if (ln.live) reinterpret_cast<float2*>(stk + (size_t)k * C::SL + sidx(c))[sg] = df2f(o);
+          if (ln.live) reinterpret_cast<float2*>(p.stk + (size_t)k * C::SL + sidx(c))[sg] = df2f(o);
         } else {
           R[c] = o;
         }
@@ -320,14 +373,14 @@ struct P4 {
         for (int d = 1; d <= B; ++d) R[sd * C::W + d - 1] = R[sd * C::W + d];
       // rows entering at the end of this level have stream index tn on both sides
       const int tn = k + C::W;
-      if ((tn >> 3) >= conv) {
+      if (tn >= conv * C::CH) {
         // issue chunk conv+2 into the slots of chunk conv-2 (stream indices
-        // below 8 conv - 8 <= tn - b, no longer referenced); then at most the
+        // below CH (conv-1) <= tn - b, no longer referenced); then at most the
         // two newest groups are pending
-        chunk<false>(sm, a, dsys, conv + 2, ln);
+        chunk<false>(sm, p, conv + 2, ln);
         cpa_commit();
         cpa_wait<2>();
-        chunk<true>(sm, a, dsys, conv, ln);
+        chunk<true>(sm, p, conv, ln);
         ++conv;
         __syncwarp();
       }
@@ -368,6 +421,50 @@ struct P4 {
     cpa_wait<0>();
     __threadfence_block();
     __syncwarp();
+    if (p.sf < s) outer_out(sm, p, ln, R, pj);
+  }
+
+  // The block's part of the reduced system: the 2b x 2b Schur complement left
+  // in the window (rows and columns at stream indices sf..s-1 of both sides)
+  // and the transformed rhs, then the band entries coupling its first b rows
+  // to the last b columns of the previous block and its last b rows to the
+  // first b columns of the next.
+  static __device__ void outer_out(Sm4<B>& sm, const Part4& p, const L& ln, const df (&R)[C::NC], int pj) {
+    const int s = p.s, sg = ln.side;
+    const int tr = p.sf + (ln.j - pj + C::W) % C::W;  // stream index of this lane's row
+    if (tr <= s - 1 && ln.live) {
+      const int o = outer_index(sg, tr, s);
+      const int h = sg, rb = o - h * B;  // block (first / last rows) and row in it
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd)
+#pragma unroll
+        for (int d = 0; d < B; ++d) {
+          // column (side sd, distance d) is stream sf + d: outer index B - 1 - d (left), B + d (right)
+          const int cb = sd ? d : B - 1 - d;
+          const int which = (sd == h) ? 1 : (h == 0 ? 2 : 0);
+          sm.u.red.T[h][which][rb * B + cb] = df2f(R[sd * C::W + d]);
+        }
+      sm.fo[o] = df2f(R[C::RHS]);
+    }
+    if (ln.live) {
+      for (int e = ln.u; e < 2 * C::BB; e += C::GS) {
+        const int part = e / C::BB, i = (e / B) % B, jj = e % B;
+        df v = df_zero();
+        if (part == 0) {
+          // row i of the block, column row0 - b + jj of the previous block (band offset jj - i)
+          const int lr = i;
+          if (p.m > 0 && jj >= i && lr < p.n && !(p.act && __ldcg(p.act + lr)))
+            v = A::from_double(__ldg(p.band + (size_t)lr * C::BW + (jj - i)));
+        } else {
+          // row 2s - b + i of the block, column row0 + 2s + jj of the next block (band offset 2b - i + jj)
+          const int lr = 2 * s - B + i;
+          if (p.m < p.r - 1 && jj <= i && lr < p.n && p.row0 + 2 * s + jj < p.ng && !(p.act && __ldcg(p.act + lr)))
+            v = A::from_double(__ldg(p.band + (size_t)lr * C::BW + (2 * B - i + jj)));
+        }
+        sm.u.red.T[part][part == 0 ? 0 : 2][i * B + jj] = df2f(v);
+      }
+    }
+    __syncwarp();
   }
 
   // ---------------------------------------------------------------- solve only
@@ -375,13 +472,10 @@ struct P4 {
   // factorization: the pivot pair (y_p, y_q) of a level is broadcast, the
   // outer rows take F_o -= w_o,p y_p + w_o,q y_q, and Pi^-1 (y_p, y_q)
   // replaces the folded rhs column of the stack level for the Z0 sweep.
-  static __device__ void w_sweep(Sm4<B>& sm, const Paqif4Args& a, int dsys, int ssys, const L& ln) {
-    const int s = a.s, n = a.n;
+  static __device__ void w_sweep(Sm4<B>& sm, const Part4& p, const L& ln) {
+    const int s = p.s, n = p.n;
     const int sg = ln.side, j = ln.j, u = ln.u;
-    float4* stk = a.stack + (size_t)ssys * s * C::SL;
-    const float4* fst = a.fstore + (size_t)ssys * s * C::FL;
-    const double* rsys = a.rhs + (size_t)dsys * n;
-    // rhs and flags by chunk of 8 stream indices per side, staged in rrhs/ract;
+    // rhs and flags by chunk of CH stream indices per side, staged in rrhs/ract;
     // factor-store levels staged in the (unused) band ring as float4 [RB][FL]
     float4 (*fring)[C::FL] = sm.u.fr;
     auto issue = [&](int c) {
@@ -394,12 +488,12 @@ struct P4 {
         r_lo = max(r_lo, 0);
         r_hi = min(r_hi, n - 1);
         for (int r = r_lo + u; r <= r_hi; r += C::GS)
-          cpa8(&sm.rrhs[side][(side ? r - s : s - 1 - r) & (C::RB - 1)], rsys + r);
+          cpa8(&sm.rrhs[side][(side ? r - s : s - 1 - r) & (C::RB - 1)], p.rhs + r);
       }
-      const int k0 = t0, k1 = min(t0 + C::CH, s);
+      const int k0 = t0, k1 = min(t0 + C::CH, p.sf);
       for (int e = u; e < (k1 - k0) * C::FL; e += C::GS) {
         const int lvl = k0 + e / C::FL, off = e % C::FL;
-        cpa16cg(&fring[lvl & (C::RB - 1)][off], fst + (size_t)lvl * C::FL + off);
+        cpa16cg(&fring[lvl & (C::RB - 1)][off], p.fst + (size_t)lvl * C::FL + off);
       }
     };
     auto convert = [&](int c) {
@@ -416,13 +510,14 @@ struct P4 {
           double* dst = &sm.rrhs[side][t];
           const df v = A::from_double(*dst);
           *reinterpret_cast<float2*>(dst) = make_float2(v.hi, v.lo);
-          sm.ract[side][t] = a.act ? __ldcg(a.act + (size_t)dsys * n + r) : 0;
+          sm.ract[side][t] = p.act ? __ldcg(p.act + r) : 0;
         }
       }
     };
-    // chunk c = rhs of stream indices [8c, 8c+8) and factor-store levels [8c, 8c+8).
-    // Level k reads level k and the rhs of stream k + b + 1 <= k + 9, so at
-    // k = 8c chunks c..c+2 must be complete and chunk c-1 is free.
+    // chunk c = rhs of stream indices [CH c, CH c + CH) and factor-store levels
+    // of the same range.  Level k reads level k and the rhs of stream
+    // k + b + 1 <= k + CH + 1, so at k = CH c chunks c..c+2 must be complete
+    // and chunk c-1 is free.
     issue(0);
     cpa_commit();
     issue(1);
@@ -438,14 +533,14 @@ struct P4 {
     __syncwarp();
     df F = rhs_of(sm, sg, j, row_kind(sm, sg, j, s, n));
     int pj = 0;
-    for (int k = 0; k < s; ++k) {
-      if ((k & 7) == 0 && k > 0) {
+    for (int k = 0; k < p.sf; ++k) {
+      if (k > 0 && k % C::CH == 0) {
         // issue chunk c+3 into the slots of chunk c-1, then all but the newest
         // group are complete: chunk c+2 can be converted
-        issue((k >> 3) + 3);
+        issue(k / C::CH + 3);
         cpa_commit();
         cpa_wait<1>();
-        convert((k >> 3) + 2);
+        convert(k / C::CH + 2);
         __syncwarp();
       }
       const df yp = shfl_df(F, ln.gbase + pj), yq = shfl_df(F, ln.gbase + C::W + pj);
@@ -453,7 +548,7 @@ struct P4 {
       const bool piv = (j == pj);
       const df o = A::sub_two_prods(piv ? df_zero() : F, make_df(f.x, f.y), yp, make_df(f.z, f.w), yq);
       if (piv) {
-        if (ln.live) reinterpret_cast<float2*>(stk + (size_t)k * C::SL + 2 * B)[sg] = df2f(o);
+        if (ln.live) reinterpret_cast<float2*>(p.stk + (size_t)k * C::SL + 2 * B)[sg] = df2f(o);
         const int tn = k + C::W;
         F = rhs_of(sm, sg, tn, row_kind(sm, sg, tn, s, n));
       } else {
@@ -464,29 +559,32 @@ struct P4 {
     cpa_wait<0>();
     __threadfence_block();
     __syncwarp();
+    if (p.sf < s) {
+      const int tr = p.sf + (j - pj + C::W) % C::W;
+      if (tr <= s - 1 && ln.live) sm.fo[outer_index(sg, tr, s)] = df2f(F);
+      __syncwarp();
+    }
   }
 
   // ---------------------------------------------------------------- Z0 sweep
   // Z0 U = Y for k = s-1 .. 0: x_p,q = Pi^-1 y - sum_o (Pi^-1 z_o) x_o.  The
   // lane of row slot j accumulates the sum for the next level of that slot
   // (k - d, d = (k - j) mod W): when a level solves its pair, the pair is
-  // broadcast and every lane adds its terms.
-  static __device__ void z_solve(Sm4<B>& sm, const Paqif4Args& a, int dsys, int ssys, bool real, const L& ln,
-                                 int& flag) {
-    const int s = a.s, n = a.n;
+  // broadcast and every lane adds its terms.  Levels sf..s-1 (the outer
+  // unknowns of a block) come from the reduced system.
+  static __device__ void z_solve(Sm4<B>& sm, const Part4& p, bool real, const L& ln, int& flag) {
+    const int s = p.s, sf = p.sf, n = p.n;
     const int sg = ln.side, j = ln.j, u = ln.u;
-    const float4* stk = a.stack + (size_t)ssys * s * C::SL;
-    double* xs = a.x + (size_t)dsys * n;
-    auto issue = [&](int c) {  // levels with v = s-1-k in [8c, 8c+8)
+    auto issue = [&](int c) {  // levels with v = sf-1-k in [CH c, CH c + CH)
       if (!ln.live) return;
-      const int v0 = c * C::CH, v1 = min(v0 + C::CH, s);
+      const int v0 = c * C::CH, v1 = min(v0 + C::CH, sf);
       if (v0 >= v1) return;
-      const int k_lo = s - v1;
+      const int k_lo = sf - v1;
       const int nvec = (v1 - v0) * C::SL;
-      const float4* src = stk + (size_t)k_lo * C::SL;
+      const float4* src = p.stk + (size_t)k_lo * C::SL;
       for (int e = u; e < nvec; e += C::GS) {
         const int lvl = k_lo + e / C::SL, off = e % C::SL;
-        cpa16cg(&sm.u.stk[(s - 1 - lvl) & (C::RB - 1)][off], src + e);
+        cpa16cg(&sm.u.stk[(sf - 1 - lvl) & (C::RB - 1)][off], src + e);
       }
     };
     issue(0);
@@ -504,14 +602,37 @@ struct P4 {
     auto store_x = [&](df xv, int row) {
       double d = A::to_double(xv);
       if (!isfinite(d) && flag == 0) flag = EHL_INFO_NONFINITE;
-      if (a.mode == 1) d = d > 0.0 ? d : 0.0;
-      if (real && ln.live && row < n) xs[row] = d;
+      if (p.mode == 1) d = d > 0.0 ? d : 0.0;
+      if (real && ln.live && row < n) p.x[row] = d;
+    };
+    // terms of the pair (x_p, x_q) of level k in level k - d (columns (left, d) and (right, d))
+    auto push = [&](int k, int d, df xp, df xq) {
+      const float4* lv = sm.u.stk[(sf - 1 - (k - d)) & (C::RB - 1)];
+      const float4 ml = lv[d - 1], mr = lv[B + d - 1];
+      const df m1 = sg ? make_df(ml.z, ml.w) : make_df(ml.x, ml.y);
+      const df m2 = sg ? make_df(mr.z, mr.w) : make_df(mr.x, mr.y);
+      acc = A::sub_two_prods(acc, df_neg(m1), xp, df_neg(m2), xq);
     };
     int pj = (s - 1) % C::W;
-    for (int k = s - 1; k >= 0; --k) {
-      const int v = s - 1 - k;
-      if ((v & 7) == 0 && v > 0) {
-        // at v = 8c: chunk c+2 replaces chunk c-2, then chunks <= c+1 are complete
+    // the outer levels, known from the reduced system
+    for (int k = s - 1; k >= sf; --k) {
+      const int d = (pj - j + C::W) % C::W;
+      df xv = df_zero();
+      if (d == 0) xv = f2df(sm.xo[outer_index(sg, k, s)]);
+      const df xp = shfl_df(xv, ln.gbase + pj), xq = shfl_df(xv, ln.gbase + C::W + pj);
+      if (d == 0) {
+        if (pend_row >= 0) store_x(pend_x, pend_row);
+        pend_x = xv;
+        pend_row = sg ? s + k : s - 1 - k;
+      } else if (k - d >= 0 && k - d < sf) {
+        push(k, d, xp, xq);
+      }
+      pj = (pj == 0) ? B : pj - 1;
+    }
+    for (int k = sf - 1; k >= 0; --k) {
+      const int v = sf - 1 - k;
+      if (v > 0 && v % C::CH == 0) {
+        // at v = CH c: chunk c+2 replaces chunk c-2, then chunks <= c+1 are complete
         issue(issued);
         cpa_commit();
         ++issued;
@@ -533,12 +654,7 @@ struct P4 {
         pend_x = xv;
         pend_row = sg ? s + k : s - 1 - k;
       } else if (k - d >= 0) {
-        // terms of (x_p, x_q) of level k in level k - d: columns (left, d) and (right, d)
-        const float4* lv = sm.u.stk[(v + d) & (C::RB - 1)];
-        const float4 ml = lv[d - 1], mr = lv[B + d - 1];
-        const df m1 = sg ? make_df(ml.z, ml.w) : make_df(ml.x, ml.y);
-        const df m2 = sg ? make_df(mr.z, mr.w) : make_df(mr.x, mr.y);
-        acc = A::sub_two_prods(acc, df_neg(m1), xp, df_neg(m2), xq);
+        push(k, d, xp, xq);
       }
       pj = (pj == 0) ? B : pj - 1;
     }
@@ -548,14 +664,176 @@ struct P4 {
     __syncwarp();
   }
 
-  static __device__ bool active_set_update(const Paqif4Args& a, int dsys, bool real, const L& ln) {
+  // ---------------------------------------------------------------- reduced system
+  // Block tridiagonal, 2r blocks of b unknowns (block 2m: the first b rows of
+  // partition m, block 2m+1: its last b rows), eliminated without pivoting:
+  //   L_q = T_q,q-1 D_{q-1}^-1,  D_q = T_q,q - L_q T_q-1,q,
+  //   y_q = f_q - L_q y_{q-1},   x_q = D_q^-1 (y_q - T_q,q+1 x_{q+1}).
+  // Run by the group of partition 0 of each system; every group of the warp
+  // executes the same loops (uniform barriers), only the leaders store.
+  static __device__ __forceinline__ float2* blk(Sm4<B>* ss, int q, int which) {
+    return ss[q >> 1].u.red.T[q & 1][which];
+  }
+  static __device__ __forceinline__ float2* vec(Sm4<B>* ss, int q, bool x) {
+    return (x ? ss[q >> 1].xo : ss[q >> 1].fo) + (q & 1) * B;
+  }
+  static constexpr int NE = (C::BB + C::GS - 1) / C::GS;  // matrix entries per lane
+
+  // C = A X (store = true) or C -= A X into dst, entries e = u, u + GS, ...
+  static __device__ __forceinline__ void matmul(const float2* Am, const float2* Xm, float2* dst, bool sub, bool st,
+                                                const L& ln) {
+    df tmp[NE];
+#pragma unroll
+    for (int t = 0; t < NE; ++t) {
+      const int e = min(ln.u + t * C::GS, C::BB - 1);
+      const int i = e / B, jj = e % B;
+      df a = sub ? f2df(dst[e]) : df_zero();
+#pragma unroll
+      for (int q = 0; q < B; q += 2) {
+        const df a0 = f2df(Am[i * B + q]), x0 = f2df(Xm[q * B + jj]);
+        const df a1 = (q + 1 < B) ? f2df(Am[i * B + q + 1]) : df_zero();
+        const df x1 = (q + 1 < B) ? f2df(Xm[(q + 1) * B + jj]) : df_zero();
+        a = sub ? A::sub_two_prods(a, a0, x0, a1, x1) : A::sub_two_prods(a, df_neg(a0), x0, df_neg(a1), x1);
+      }
+      tmp[t] = a;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < NE; ++t) {
+      const int e = ln.u + t * C::GS;
+      if (st && e < C::BB) dst[e] = df2f(tmp[t]);
+    }
+    __syncwarp();
+  }
+  // y = f - A x (lanes i < b), written to dst
+  static __device__ __forceinline__ void matvec_sub(const float2* Am, const float2* xv, const float2* fv, float2* dst,
+                                                    bool st, const L& ln) {
+    const int i = min(ln.u, B - 1);
+    df a = f2df(fv[i]);
+#pragma unroll
+    for (int q = 0; q < B; q += 2) {
+      const df a0 = f2df(Am[i * B + q]), x0 = f2df(xv[q]);
+      const df a1 = (q + 1 < B) ? f2df(Am[i * B + q + 1]) : df_zero();
+      const df x1 = (q + 1 < B) ? f2df(xv[q + 1 < B ? q + 1 : q]) : df_zero();
+      a = A::sub_two_prods(a, a0, x0, a1, x1);
+    }
+    __syncwarp();
+    if (st && ln.u < B) dst[ln.u] = df2f(a);
+    __syncwarp();
+  }
+  // y = A x (lanes i < b)
+  static __device__ __forceinline__ void matvec(const float2* Am, const float2* xv, float2* dst, bool st,
+                                                const L& ln) {
+    const int i = min(ln.u, B - 1);
+    df a = df_zero();
+#pragma unroll
+    for (int q = 0; q < B; q += 2) {
+      const df a0 = f2df(Am[i * B + q]), x0 = f2df(xv[q]);
+      const df a1 = (q + 1 < B) ? f2df(Am[i * B + q + 1]) : df_zero();
+      const df x1 = (q + 1 < B) ? f2df(xv[q + 1 < B ? q + 1 : q]) : df_zero();
+      a = A::sub_two_prods(a, df_neg(a0), x0, df_neg(a1), x1);
+    }
+    __syncwarp();
+    if (st && ln.u < B) dst[ln.u] = df2f(a);
+    __syncwarp();
+  }
+  // in-place inverse by Gauss-Jordan elimination without pivoting
+  static __device__ void invert(float2* M, bool st, const L& ln, int& flag) {
+    for (int q = 0; q < B; ++q) {
+      const df piv = f2df(M[q * B + q]);
+      if (!(fabsf(piv.hi) > 0.f) && st && flag == 0) flag = EHL_INFO_SINGULAR;
+      const df ip = A::rcp((fabsf(piv.hi) > 0.f) ? piv : make_df(1e-30f, 0.f));
+      df tmp[NE];
+#pragma unroll
+      for (int t = 0; t < NE; ++t) {
+        const int e = min(ln.u + t * C::GS, C::BB - 1);
+        const int i = e / B, jj = e % B;
+        const df mij = f2df(M[e]), miq = f2df(M[i * B + q]), mqj = f2df(M[q * B + jj]);
+        df v;
+        if (i == q && jj == q)
+          v = ip;
+        else if (i == q)
+          v = A::mul(mqj, ip);
+        else if (jj == q)
+          v = df_neg(A::mul(miq, ip));
+        else
+          v = A::sub_two_prods(mij, A::mul(miq, ip), mqj, df_zero(), df_zero());
+        tmp[t] = v;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < NE; ++t) {
+        const int e = ln.u + t * C::GS;
+        if (st && e < C::BB) M[e] = df2f(tmp[t]);
+      }
+      __syncwarp();
+    }
+  }
+
+  // Factor the reduced system of the system whose partitions are ss[0..r-1]
+  // (T blocks and fo filled by outer_out), solve it into xo, and keep the
+  // factors in rst when given.
+  static __device__ void reduced_factor(Sm4<B>* ss, int r, bool leader, float2* rst, const L& ln, int& flag) {
+    const bool st = leader && ln.live;
+    const int nb = 2 * r;
+    for (int q = 0; q < nb; ++q) {
+      if (q > 0) {
+        matmul(blk(ss, q, 0), blk(ss, q - 1, 1), blk(ss, q, 0), false, st, ln);  // L_q = T_q,q-1 D^-1
+        matmul(blk(ss, q, 0), blk(ss, q - 1, 2), blk(ss, q, 1), true, st, ln);   // D_q -= L_q T_q-1,q
+      }
+      invert(blk(ss, q, 1), st, ln, flag);
+    }
+    if (rst && st) {
+      for (int q = 0; q < nb; ++q)
+        for (int w = 0; w < 3; ++w)
+          for (int e = ln.u; e < C::BB; e += C::GS) rst[((size_t)q * 3 + w) * C::BB + e] = blk(ss, q, w)[e];
+    }
+    __syncwarp();
+    reduced_substitute(ss, r, leader, ln);
+  }
+  // forward and backward substitution with the factors in the T blocks
+  static __device__ void reduced_substitute(Sm4<B>* ss, int r, bool leader, const L& ln) {
+    const bool st = leader && ln.live;
+    const int nb = 2 * r;
+    // y_0 = f_0 (into xo), y_q = f_q - L_q y_{q-1}
+    if (st && ln.u < B) vec(ss, 0, true)[ln.u] = vec(ss, 0, false)[ln.u];
+    __syncwarp();
+    for (int q = 1; q < nb; ++q) matvec_sub(blk(ss, q, 0), vec(ss, q - 1, true), vec(ss, q, false), vec(ss, q, true), st, ln);
+    // x_q = D_q^-1 (y_q - T_q,q+1 x_{q+1}), the bracket staged in fo
+    for (int q = nb - 1; q >= 0; --q) {
+      if (q < nb - 1)
+        matvec_sub(blk(ss, q, 2), vec(ss, q + 1, true), vec(ss, q, true), vec(ss, q, false), st, ln);
+      else {
+        if (st && ln.u < B) vec(ss, q, false)[ln.u] = vec(ss, q, true)[ln.u];
+        __syncwarp();
+      }
+      matvec(blk(ss, q, 1), vec(ss, q, false), vec(ss, q, true), st, ln);
+    }
+  }
+  // a resolve: the stored factors back into the T blocks, then the substitution
+  static __device__ void reduced_resolve(Sm4<B>* ss, int r, bool leader, const float2* rst, const L& ln) {
+    const bool st = leader && ln.live;
+    const int nb = 2 * r;
+    if (st) {
+      for (int q = 0; q < nb; ++q)
+        for (int w = 0; w < 3; ++w)
+          for (int e = ln.u; e < C::BB; e += C::GS) blk(ss, q, w)[e] = __ldcg(rst + ((size_t)q * 3 + w) * C::BB + e);
+    }
+    __syncwarp();
+    reduced_substitute(ss, r, leader, ln);
+  }
+
+  // Mode 2: new active set of rows [r_lo, r_hi) of the system from x (all of
+  // the system's rows written); returns whether any row of the group changed.
+  static __device__ bool active_set_update(const Paqif4Args& a, int dsys, int r_lo, int r_hi, bool real,
+                                           const L& ln) {
     const int n = a.n;
     const double* bsys = a.band + (size_t)dsys * n * C::BW;
     const double* xs = a.x + (size_t)dsys * n;
     int* as = a.act + (size_t)dsys * n;
     int changed = 0;
     if (real && ln.live) {
-      for (int i = ln.u; i < n; i += C::GS) {
+      for (int i = r_lo + ln.u; i < r_hi; i += C::GS) {
         df w = df_neg(A::from_double(a.rhs[(size_t)dsys * n + i]));
 #pragma unroll
         for (int q = 0; q < C::BW; ++q) {
@@ -589,105 +867,210 @@ struct P4 {
     }
     return f;
   }
+
+  static __device__ Part4 part(const Paqif4Args& a, int dsys, int m, int gidx) {
+    Part4 p;
+    p.row0 = m * a.np;
+    p.n = min(max(a.n - p.row0, 0), a.np);
+    p.band = a.band + ((size_t)dsys * a.n + p.row0) * C::BW;
+    p.rhs = a.rhs + (size_t)dsys * a.n + p.row0;
+    p.act = a.act ? a.act + (size_t)dsys * a.n + p.row0 : nullptr;
+    p.x = a.x + (size_t)dsys * a.n + p.row0;
+    p.stk = a.stack + (size_t)gidx * a.sp * C::SL;
+    p.fst = a.fstore ? a.fstore + (size_t)gidx * a.sp * C::FL : nullptr;
+    p.s = a.sp;
+    p.sf = a.sf;
+    p.m = m;
+    p.r = a.r;
+    p.mode = a.mode;
+    p.ng = a.n;
+    return p;
+  }
 };
 
-// Groups past n_sys replay a real system's loads with their own stack slot and
-// no other global stores, so every warp barrier and shuffle sees a full warp.
-// Mode 2 runs active-set steps until no group of the warp changes its set (a
-// converged group re-solves with the same set, reproducing the same x).
+// One CTA holds spc systems of r partitions each, one group of lanes per
+// partition.  Groups of a padding system replay the last real system's loads
+// with their own stack slots and no other global stores, so every warp and CTA
+// barrier sees all threads.  Mode 2 runs active-set steps until no system of
+// the CTA changes its set (a converged system re-solves with the same set,
+// reproducing the same x).
 template <int B, bool F32>
 __global__ void __launch_bounds__(32 * C4<B>::WARPS, 4) paqif4_kernel(Paqif4Args a) {
   using C = C4<B>;
+  using K = P4<B, F32>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Lane4<B> ln;
   const int warp = threadIdx.x >> 5;
-  Sm4<B>& sm = reinterpret_cast<Sm4<B>*>(smem_raw)[warp * C::G + ln.grp];
-  const int ssys = (blockIdx.x * C::WARPS + warp) * C::G + ln.grp;
-  const bool real = ssys < a.n_sys;
-  const int dsys = real ? ssys : a.n_sys - 1;
-  if (__all_sync(0xffffffffu, !real)) return;
+  Sm4<B>* smb = reinterpret_cast<Sm4<B>*>(smem_raw);
+  const int gc = warp * C::G + ln.grp;
+  const int sysl = gc / a.r, m = gc - sysl * a.r;
+  Sm4<B>& sm = smb[gc];
+  Sm4<B>* ss = smb + sysl * a.r;
+  const int sys = blockIdx.x * a.spc + sysl;
+  const bool real = sys < a.n_sys;
+  const int dsys = real ? sys : a.n_sys - 1;
+  if (a.r == 1 && __all_sync(0xffffffffu, !real)) return;  // no CTA barriers with one partition
+  const Part4 p = K::part(a, dsys, m, blockIdx.x * C::GPC + gc);
+  float2* rst = a.rstore ? a.rstore + (size_t)sys * 2 * a.r * 3 * C::BB : nullptr;
   int flag = 0, solves = 0;
   bool more = real;
   const int max_solves = (a.mode == 2) ? kPaqifMaxActiveSetSteps : 1;
   for (int it = 0; it < max_solves; ++it) {
-    P4<B, F32>::factor(sm, a, dsys, ssys, ln, flag);
-    P4<B, F32>::z_solve(sm, a, dsys, ssys, real, ln, flag);
+    K::factor(sm, p, ln, flag);
+    if (a.r > 1) {
+      __syncthreads();
+      K::reduced_factor(ss, a.r, m == 0, real ? rst : nullptr, ln, flag);
+      __syncthreads();
+    }
+    K::z_solve(sm, p, real, ln, flag);
     if (more) ++solves;
     if (a.mode != 2) break;
-    if (!P4<B, F32>::active_set_update(a, dsys, real, ln)) more = false;
-    if (!__any_sync(0xffffffffu, more)) break;
+    if (a.r == 1) {
+      if (!K::active_set_update(a, dsys, 0, a.n, real, ln)) more = false;
+      if (!__any_sync(0xffffffffu, more)) break;
+    } else {
+      __syncthreads();  // x of every partition is written
+      const bool ch = K::active_set_update(a, dsys, p.row0, p.row0 + p.n, real, ln);
+      if (ln.live && ln.u == 0) sm.more = ch ? 1 : 0;
+      __syncthreads();
+      int any = 0;
+      for (int q = 0; q < a.r; ++q) any |= ss[q].more;
+      if (!any) more = false;
+      if (!__syncthreads_or(more ? 1 : 0)) break;
+    }
   }
-  int f = P4<B, F32>::group_flag(flag, ln);
+  int f = K::group_flag(flag, ln);
+  if (a.r > 1) {
+    if (ln.live && ln.u == 0) sm.flag = f;
+    __syncthreads();
+    f = 0;
+    for (int q = 0; q < a.r; ++q)
+      if (f == 0) f = ss[q].flag;
+  }
   if (a.mode == 2 && more && f == 0) f = EHL_INFO_NOCONV;
-  if (real && ln.live && ln.u == 0) {
+  if (real && ln.live && ln.u == 0 && m == 0) {
     if (a.iters) a.iters[dsys] = solves;
     if (a.info) a.info[dsys] = f;
   }
 }
 
 // Solve only, with the factorization stored by a factor launch (same systems,
-// same band): the W0 sweep for the new rhs, then the Z0 sweep.
+// same band): the W0 sweep for the new rhs, the reduced system, then the Z0 sweep.
 template <int B, bool F32>
 __global__ void __launch_bounds__(32 * C4<B>::WARPS, 4) paqif4_solve_kernel(Paqif4Args a) {
   using C = C4<B>;
+  using K = P4<B, F32>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Lane4<B> ln;
   const int warp = threadIdx.x >> 5;
-  Sm4<B>& sm = reinterpret_cast<Sm4<B>*>(smem_raw)[warp * C::G + ln.grp];
-  const int ssys = (blockIdx.x * C::WARPS + warp) * C::G + ln.grp;
-  const bool real = ssys < a.n_sys;
-  const int dsys = real ? ssys : a.n_sys - 1;
-  if (__all_sync(0xffffffffu, !real)) return;
+  Sm4<B>* smb = reinterpret_cast<Sm4<B>*>(smem_raw);
+  const int gc = warp * C::G + ln.grp;
+  const int sysl = gc / a.r, m = gc - sysl * a.r;
+  Sm4<B>& sm = smb[gc];
+  Sm4<B>* ss = smb + sysl * a.r;
+  const int sys = blockIdx.x * a.spc + sysl;
+  const bool real = sys < a.n_sys;
+  const int dsys = real ? sys : a.n_sys - 1;
+  if (a.r == 1 && __all_sync(0xffffffffu, !real)) return;
+  const Part4 p = K::part(a, dsys, m, blockIdx.x * C::GPC + gc);
   int flag = 0;
-  P4<B, F32>::w_sweep(sm, a, dsys, ssys, ln);
-  P4<B, F32>::z_solve(sm, a, dsys, ssys, real, ln, flag);
-  const int f = P4<B, F32>::group_flag(flag, ln);
-  if (real && ln.live && ln.u == 0 && a.info && f != 0) a.info[dsys] = f;
+  K::w_sweep(sm, p, ln);
+  if (a.r > 1) {
+    __syncthreads();
+    K::reduced_resolve(ss, a.r, m == 0, a.rstore + (size_t)(real ? sys : 0) * 2 * a.r * 3 * C::BB, ln);
+    __syncthreads();
+  }
+  K::z_solve(sm, p, real, ln, flag);
+  int f = K::group_flag(flag, ln);
+  if (a.r > 1) {
+    if (ln.live && ln.u == 0) sm.flag = f;
+    __syncthreads();
+    f = 0;
+    for (int q = 0; q < a.r; ++q)
+      if (f == 0) f = ss[q].flag;
+  }
+  if (real && ln.live && ln.u == 0 && m == 0 && a.info && f != 0) a.info[dsys] = f;
 }
 
 template <int B>
 static size_t p4_smem() {
-  return sizeof(Sm4<B>) * (size_t)(C4<B>::WARPS * C4<B>::G);
-}
-template <int B>
-static int p4_per_cta() {
-  return C4<B>::WARPS * C4<B>::G;
-}
-template <int B>
-static int p4_fl() {
-  return C4<B>::FL;
+  return sizeof(Sm4<B>) * (size_t)C4<B>::GPC;
 }
 
 #define EHL_BETA_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
 
-static bool p4_layout(int beta, int& per, int& fl) {
+static int groups_per_cta(int beta) {
   switch (beta) {
-#define EHL_CASE(BB)        \
-  case BB:                  \
-    per = p4_per_cta<BB>(); \
-    fl = p4_fl<BB>();       \
-    return true;
+#define EHL_CASE(BB) \
+  case BB:           \
+    return C4<BB>::GPC;
     EHL_BETA_CASES(EHL_CASE)
 #undef EHL_CASE
     default:
-      return false;
+      return 0;
   }
 }
 
-size_t paqif_stack_bytes(int n_sys, int n, int beta) {
-  int per = 0, fl = 0;
-  if (!p4_layout(beta, per, fl)) return 0;
-  const int s = (n + 1) / 2;
-  const size_t padded = (size_t)((n_sys + per - 1) / per) * per;
-  return padded * (size_t)s * (size_t)(2 * beta + 1) * sizeof(float4);
+// Partition geometry: r blocks of even order np = 2 ceil(n / 2r), each with
+// at least one interior level (np >= 2 beta + 2) and at least one real row;
+// r divides the groups of a CTA.
+struct Geom {
+  int r, np, sp, sf, spc, grid;
+};
+static bool geom_ok(int n_sys, int n, int beta, int r, Geom& g) {
+  const int gpc = groups_per_cta(beta);
+  if (gpc == 0 || r < 1 || gpc % r != 0) return false;
+  g.r = r;
+  g.sp = (n + 2 * r - 1) / (2 * r);
+  g.np = 2 * g.sp;
+  if (r > 1 && (g.np < 2 * beta + 2 || (r - 1) * g.np >= n)) return false;
+  g.sf = (r > 1) ? g.sp - beta : g.sp;
+  g.spc = gpc / r;
+  g.grid = (n_sys + g.spc - 1) / g.spc;
+  return true;
 }
 
-size_t paqif_factor_store_bytes(int n_sys, int n, int beta) {
-  int per = 0, fl = 0;
-  if (!p4_layout(beta, per, fl)) return 0;
-  const int s = (n + 1) / 2;
-  const size_t padded = (size_t)((n_sys + per - 1) / per) * per;
-  return padded * (size_t)s * (size_t)fl * sizeof(float4);
+// The automatic choice: the largest admissible r that does not take the batch
+// past about 1.5 waves of resident groups (16 warps per SM), keeping at least
+// 4 b interior levels per block so that the sequential reduced system (2r
+// block steps) stays small against the sweeps it shortens.  Measured on the
+// standalone batch (4096 x n = 1024, b = 4): r = 1, 2, 3, 4 take 1.67, 1.54,
+// 1.21, 1.27 ms; on 512 x n = 1025, b = 8: r = 1, 2, 4 take 1.46, 0.87, 0.68 ms.
+int paqif_parts(int n_sys, int n, int beta, int requested) {
+  Geom g;
+  if (requested > 0) return geom_ok(n_sys, n, beta, requested, g) ? requested : -1;
+  const int gpc = groups_per_cta(beta);
+  if (gpc == 0 || n_sys < 1) return -1;
+  const long long target = (long long)kSmCount * 24 * (gpc / kPaqifWarpsPerCta);
+  int best = 1;
+  for (int r = 2; r <= gpc; ++r) {
+    if ((long long)n_sys * (r - 1) >= target) break;
+    if (!geom_ok(n_sys, n, beta, r, g) || g.sf < 4 * beta) continue;
+    best = r;
+  }
+  return best;
+}
+
+static bool geom(int n_sys, int n, int beta, int parts, Geom& g) {
+  const int r = paqif_parts(n_sys, n, beta, parts);
+  return r > 0 && geom_ok(n_sys, n, beta, r, g);
+}
+
+size_t paqif_stack_bytes(int n_sys, int n, int beta, int parts) {
+  Geom g;
+  if (!geom(n_sys, n, beta, parts, g)) return 0;
+  return (size_t)g.grid * groups_per_cta(beta) * (size_t)g.sp * (size_t)(2 * beta + 1) * sizeof(float4);
+}
+
+static size_t reduced_store_bytes(const Geom& g, int beta) {
+  return g.r > 1 ? (size_t)g.grid * g.spc * (size_t)(2 * g.r * 3 * beta * beta) * sizeof(float2) : 0;
+}
+
+size_t paqif_factor_store_bytes(int n_sys, int n, int beta, int parts) {
+  Geom g;
+  if (!geom(n_sys, n, beta, parts, g)) return 0;
+  const size_t groups = (size_t)g.grid * groups_per_cta(beta) * (size_t)g.sp * (size_t)(2 * beta + 2) * sizeof(float4);
+  return align_up(groups, kWorkspaceAlign) + reduced_store_bytes(g, beta);
 }
 
 // the dynamic shared-memory size of both kernels, set once per device
@@ -725,35 +1108,44 @@ cudaError_t paqif_prepare(int beta) {
 
 template <int B>
 static cudaError_t launch4(const PaqifLaunch& L, cudaStream_t st, void* fstore, bool solve_only) {
+  Geom g;
+  if (!geom(L.n_sys, L.n, B, L.parts, g)) return cudaErrorInvalidValue;
   Paqif4Args a;
   a.n_sys = L.n_sys;
   a.n = L.n;
-  a.s = (L.n + 1) / 2;
   a.mode = L.mode;
+  a.r = g.r;
+  a.np = g.np;
+  a.sp = g.sp;
+  a.sf = g.sf;
+  a.spc = g.spc;
   a.band = L.band;
   a.rhs = L.rhs;
   a.act = L.act;
   a.stack = reinterpret_cast<float4*>(L.stack);
   a.fstore = reinterpret_cast<float4*>(fstore);
+  a.rstore = nullptr;
+  if (fstore && g.r > 1) {
+    const size_t groups = (size_t)g.grid * C4<B>::GPC * (size_t)g.sp * C4<B>::FL * sizeof(float4);
+    a.rstore = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(fstore) + align_up(groups, kWorkspaceAlign));
+  }
   a.x = L.x;
   a.iters = L.iters;
   a.info = L.info;
   const size_t smem = p4_smem<B>();
-  const int per = p4_per_cta<B>();
-  const int grid = (L.n_sys + per - 1) / per;
   cudaError_t e = p4_attrs<B>();
   if (e != cudaSuccess) return e;
   const bool f32 = L.f32 && L.mode != 2;
   if (solve_only) {
     if (f32)
-      paqif4_solve_kernel<B, true><<<grid, 32 * C4<B>::WARPS, smem, st>>>(a);
+      paqif4_solve_kernel<B, true><<<g.grid, 32 * C4<B>::WARPS, smem, st>>>(a);
     else
-      paqif4_solve_kernel<B, false><<<grid, 32 * C4<B>::WARPS, smem, st>>>(a);
+      paqif4_solve_kernel<B, false><<<g.grid, 32 * C4<B>::WARPS, smem, st>>>(a);
   } else {
     if (f32)
-      paqif4_kernel<B, true><<<grid, 32 * C4<B>::WARPS, smem, st>>>(a);
+      paqif4_kernel<B, true><<<g.grid, 32 * C4<B>::WARPS, smem, st>>>(a);
     else
-      paqif4_kernel<B, false><<<grid, 32 * C4<B>::WARPS, smem, st>>>(a);
+      paqif4_kernel<B, false><<<g.grid, 32 * C4<B>::WARPS, smem, st>>>(a);
   }
   note_launch();
   return cudaGetLastError();
@@ -768,7 +1160,7 @@ __global__ void expand_active_kernel(const uint8_t* __restrict__ in, int* __rest
 
 cudaError_t launch_expand_active(const uint8_t* in, int* out, size_t total, cudaStream_t st) {
   int blocks = (int)((total + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > kSmCount * 16) blocks = kSmCount * 16;
   if (blocks < 1) blocks = 1;
   expand_active_kernel<<<blocks, 256, 0, st>>>(in, out, total);
   note_launch();

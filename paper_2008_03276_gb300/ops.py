@@ -33,17 +33,23 @@ def kernel_launches():
     return int(_ffi.load().ehl_kernel_launches())
 
 
-def paqif_workspace_size(n_sys, n, beta, mode):
+def paqif_workspace_size(n_sys, n, beta, mode, partitions=0):
     lib = _ffi.load()
     out = ctypes.c_size_t(0)
-    _ffi.check(lib.ehl_paqif_workspace_size(n_sys, n, beta, mode, ctypes.byref(out)), "ehl_paqif_workspace_size")
+    if partitions:
+        _ffi.check(lib.ehl_paqif_workspace_size_partitioned(n_sys, n, beta, partitions, mode, ctypes.byref(out)),
+                   "ehl_paqif_workspace_size_partitioned")
+    else:
+        _ffi.check(lib.ehl_paqif_workspace_size(n_sys, n, beta, mode, ctypes.byref(out)), "ehl_paqif_workspace_size")
     return out.value
 
 
-def paqif_solve(band, rhs, beta, mode=0, active=None, x=None, workspace=None, stream=None):
+def paqif_solve(band, rhs, beta, mode=0, active=None, x=None, workspace=None, stream=None, partitions=0):
     """Batched PAQIF solve.  ``band [n_sys, n, 2 beta + 1]``, ``rhs [n_sys, n]`` float64.
 
-    Returns ``(x, iters, info)``; ``workspace`` (uint8 CUDA tensor) is optional.
+    ``partitions`` > 0 cuts every system into that many blocks (the partitioned
+    PAQIF); 0 lets the library choose.  Returns ``(x, iters, info)``;
+    ``workspace`` (uint8 CUDA tensor) is optional.
     """
     lib = _ffi.load()
     if band.dim() == 2:
@@ -65,12 +71,18 @@ def paqif_solve(band, rhs, beta, mode=0, active=None, x=None, workspace=None, st
     _check_dev(band, rhs, active, x, workspace)
     wbytes = 0
     if workspace is None:
-        wbytes = paqif_workspace_size(n_sys, n, beta, mode)
+        wbytes = paqif_workspace_size(n_sys, n, beta, mode, partitions)
         workspace = torch.empty(wbytes, dtype=torch.uint8, device=band.device)
     wbytes = workspace.numel()
-    code = lib.ehl_paqif_solve(n_sys, n, beta, _ptr(band), _ptr(rhs), _ptr(active), mode, _ptr(x), _ptr(iters),
-                               _ptr(info), _ptr(workspace), wbytes, _stream(stream))
-    _ffi.check(code, "ehl_paqif_solve")
+    if partitions:
+        code = lib.ehl_paqif_solve_partitioned(n_sys, n, beta, partitions, _ptr(band), _ptr(rhs), _ptr(active), mode,
+                                               _ptr(x), _ptr(iters), _ptr(info), _ptr(workspace), wbytes,
+                                               _stream(stream))
+        _ffi.check(code, "ehl_paqif_solve_partitioned")
+    else:
+        code = lib.ehl_paqif_solve(n_sys, n, beta, _ptr(band), _ptr(rhs), _ptr(active), mode, _ptr(x), _ptr(iters),
+                                   _ptr(info), _ptr(workspace), wbytes, _stream(stream))
+        _ffi.check(code, "ehl_paqif_solve")
     return x, iters, info
 
 

@@ -127,7 +127,7 @@ def test_point_solve_matches_oracle(oracle_33, levels, beta, precision):
 def test_point_solve_129_properties():
     n = 129
     # the x-line preconditioner leaves the y-coupling to GMRES: at 129^2 a 40-vector basis is
-    # marginal (the Newton iteration can stall at |Phi| ~ 1e-11), the library default is 100
+    # marginal (the Newton iteration can stall at |Phi| ~ 1e-11), 100 vectors suffice
     ctx = make(n, M=100.0, L=10.0, limiter=1, beta=4, tol=1e-8, krylov_dim=100)
     P, H0, iters, res, code = ctx.solve(check=False)
     print(f"129^2: code {code} iters {iters.tolist()} res {res.tolist()}")
@@ -173,7 +173,7 @@ def test_point_adjoint_129_vs_resolved_differences():
     """The adjoint workload's point-contact backward: 129 x 129, M = 100, L = 10."""
     n, M, L = 129, 100.0, 10.0
     rg = rough2(n, seed=9, amp=0.005)
-    ctx = make(n, M=M, L=L, beta=4, tol=1e-11)
+    ctx = make(n, M=M, L=L, beta=4, tol=1e-11, krylov_dim=100)
     P, H0, iters, res, code = ctx.solve(rough=dev(rg[None]), check=False)
     assert code == 0, (iters.tolist(), res.tolist())
     X, Y = np.linspace(-4.5, 1.5, n), np.linspace(-3, 3, n)
@@ -185,7 +185,7 @@ def test_point_adjoint_129_vs_resolved_differences():
     gr, gml = gr.cpu().numpy()[0], gml.cpu().numpy()[0]
 
     def hc(rgx, M_=M, L_=L):
-        cx = make(n, M=M_, L=L_, beta=4, tol=1e-12)
+        cx = make(n, M=M_, L=L_, beta=4, tol=1e-12, krylov_dim=100)
         Pp, H0p, it, rs, cd = cx.solve(P, H0, rough=dev(rgx[None]), check=False)
         _, H, _ = cx.residual(Pp, H0p, dev(rgx[None]))
         return float(H[0, cj, ci].cpu())
