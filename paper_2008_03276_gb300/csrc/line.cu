@@ -370,6 +370,69 @@ struct LineRowCtx {
                       def0 * (Pi - P[base + i - 1]) - ef0 * ((m == i) - (m == i - 1));
     return dC - dq / (h * h);
   }
+  // The 2b+1 band entries of row i of the exact Jacobian in double-float (the
+  // same terms as J_exact, on the FP32 pipes): the nodal quantities of the
+  // stencil nodes i-2..i+1 are read once per row, the kernel values once per
+  // entry.  Entries whose column leaves the interior are 0.
+  __device__ void J_exact_row(int i, int beta, double ef0, double ef1, double* out) const {
+    df a[4], ud[4], e3[4], ed[4];  // nodes j = i-2+t: -rho_j, drho_j H_j, -3 eps_j/H_j, eps_j (drho/rho - deta)_j
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int j = i - 2 + t;
+      if (j < 0) {
+        a[t] = ud[t] = e3[t] = ed[t] = df_zero();
+        continue;
+      }
+      const double rj = rho[base + j], Hj = H[base + j], ej = eps[base + j];
+      a[t] = df_from_double(-rj);
+      ud[t] = df_from_double(drho[base + j] * Hj);
+      e3[t] = df_from_double(-3.0 * ej / Hj);
+      ed[t] = df_from_double(ej * (drho[base + j] / rj - deta_rel[base + j]));
+    }
+    const df pa1 = df_from_double(psia[base + i]), pb1 = df_from_double(psib[base + i]);
+    const df pa0 = df_from_double(i - 1 >= 1 ? psia[base + i - 1] : 0.0);
+    const df pb0 = df_from_double(i - 1 >= 1 ? psib[base + i - 1] : 0.0);
+    const double Pi = P[base + i];
+    const df dp1 = df_from_double(P[base + i + 1] - Pi), dp0 = df_from_double(Pi - P[base + i - 1]);
+    const df f1 = df_from_double(ef1), f0 = df_from_double(ef0);
+    const df ih = df_from_double(1.0 / h), ih2 = df_from_double(1.0 / (h * h));
+    const df half = make_df(0.5f, 0.f);
+    const int n = N - 2;
+    for (int e = 0; e <= 2 * beta; ++e) {
+      const int m = i - beta + e;  // node of the column
+      if (m < 1 || m > n) {
+        out[e] = 0.0;
+        continue;
+      }
+      df u[4], ee[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int j = i - 2 + t;
+        int d = j - m;
+        d = d < 0 ? -d : d;
+        const df k = (j >= 0 && d < N) ? f2df_(gtab[base + d]) : df_zero();
+        u[t] = df_mul(a[t], k);
+        ee[t] = df_mul(e3[t], k);
+        if (j == m) {
+          u[t] = df_add(u[t], ud[t]);
+          ee[t] = df_add(ee[t], ed[t]);
+        }
+      }
+      // face derivatives dF_i, dF_{i-1} (limited; the first face is upwind only)
+      const df F1 = df_add(u[2], df_mul(half, df_add(df_mul(pa1, df_sub(u[2], u[1])), df_mul(pb1, df_sub(u[3], u[2])))));
+      const df F0 = (i - 1 == 0)
+                        ? u[1]
+                        : df_add(u[1], df_mul(half, df_add(df_mul(pa0, df_sub(u[1], u[0])), df_mul(pb0, df_sub(u[2], u[1])))));
+      const df dC = df_mul(df_sub(F1, F0), ih);
+      const df def1 = df_mul(half, df_add(ee[2], ee[3])), def0 = df_mul(half, df_add(ee[1], ee[2]));
+      df dq = df_sub(df_mul(def1, dp1), df_mul(def0, dp0));
+      const int s1 = (m == i + 1) - (m == i), s0 = (m == i) - (m == i - 1);
+      if (s1) dq = s1 > 0 ? df_add(dq, f1) : df_sub(dq, f1);
+      if (s0) dq = s0 > 0 ? df_sub(dq, f0) : df_add(dq, f0);
+      out[e] = df_to_double(df_sub(dC, df_mul(dq, ih2)));
+    }
+  }
+  __device__ static df f2df_(float2 v) { return make_df(v.x, v.y); }
   // exact and frozen dR_i/dH0
   __device__ double JH_exact(int i, double ef0, double ef1) const {
     auto dUh = [&](int j) { return rho[base + j]; };
@@ -437,11 +500,9 @@ __global__ void k_line_jac_band(const LineInst* __restrict__ inst, LineRowCtx c,
     // row scale d = max(|J_ii|, |J_i|_max / 10) over the band: |J_ii| alone can pass
     // through zero in the Hertzian zone, where the row is carried by its neighbours
     double rmax = 0.0, jii = 0.0;
+    q.J_exact_row(i, beta, ef0, ef1, row);
     for (int j = 0; j < bw; ++j) {
-      const int col = r - beta + j;
-      double v = 0.0;
-      if (col >= 0 && col < n) v = q.J_exact(i, col + 1, ef0, ef1);
-      row[j] = v;
+      const double v = row[j];
       rmax = fmax(rmax, fabs(v));
       if (j == beta) jii = v;
     }
@@ -737,6 +798,9 @@ cudaError_t line_mixed_init(LineCtx* c, int precision) {
   if (e != cudaSuccess) return e;
   cublasSetWorkspace(c->blas, ws, wsb);
   cublasSetMathMode(c->blas, CUBLAS_DEFAULT_MATH);
+  // precision 2 asks for the BF16x9 tensor-core emulation: cuBLAS's default strategy picks a
+  // SIMT SGEMM for these shapes (N x n_inst x N), the eager one the emulated kernels
+  if (precision == 2) cublasSetEmulationStrategy(c->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
   k_line_kfull<<<(unsigned)((NN + 255) / 256), 256, 0, c->st>>>(c->gtab64, c->Kf, c->N);
   note_launch();
   c->precision = precision;

@@ -73,6 +73,8 @@ struct C4 {
   static constexpr int WARPS = kPaqifWarpsPerCta;
   static constexpr int GPC = WARPS * G;       // groups per CTA
   static constexpr int BB = B * B;
+  // resident CTAs per SM the register budget is set for (shared memory allows 5 up to b = 4)
+  static constexpr int MINB = (B <= 4) ? 5 : 4;
 };
 
 // reduced-system blocks of one partition: blocks 2m (first b rows) and 2m+1
@@ -895,7 +897,7 @@ struct P4 {
 // the CTA changes its set (a converged system re-solves with the same set,
 // reproducing the same x).
 template <int B, bool F32>
-__global__ void __launch_bounds__(32 * C4<B>::WARPS, 4) paqif4_kernel(Paqif4Args a) {
+__global__ void __launch_bounds__(32 * C4<B>::WARPS, C4<B>::MINB) paqif4_kernel(Paqif4Args a) {
   using C = C4<B>;
   using K = P4<B, F32>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -957,7 +959,7 @@ __global__ void __launch_bounds__(32 * C4<B>::WARPS, 4) paqif4_kernel(Paqif4Args
 // Solve only, with the factorization stored by a factor launch (same systems,
 // same band): the W0 sweep for the new rhs, the reduced system, then the Z0 sweep.
 template <int B, bool F32>
-__global__ void __launch_bounds__(32 * C4<B>::WARPS, 4) paqif4_solve_kernel(Paqif4Args a) {
+__global__ void __launch_bounds__(32 * C4<B>::WARPS, C4<B>::MINB) paqif4_solve_kernel(Paqif4Args a) {
   using C = C4<B>;
   using K = P4<B, F32>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1030,23 +1032,46 @@ static bool geom_ok(int n_sys, int n, int beta, int r, Geom& g) {
   return true;
 }
 
-// The automatic choice: the largest admissible r that does not take the batch
-// past about 1.5 waves of resident groups (16 warps per SM), keeping at least
-// 4 b interior levels per block so that the sequential reduced system (2r
-// block steps) stays small against the sweeps it shortens.  Measured on the
-// standalone batch (4096 x n = 1024, b = 4): r = 1, 2, 3, 4 take 1.67, 1.54,
-// 1.21, 1.27 ms; on 512 x n = 1025, b = 8: r = 1, 2, 4 take 1.46, 0.87, 0.68 ms.
+template <int B>
+static int p4_resident_ctas() {  // CTAs per SM: the register budget, then 227 KB of shared memory
+  const int by_smem = (int)((227u * 1024u) / p4_smem<B>());
+  return by_smem < C4<B>::MINB ? by_smem : C4<B>::MINB;
+}
+static int resident_ctas(int beta) {
+  switch (beta) {
+#define EHL_CASE(BB) \
+  case BB:           \
+    return p4_resident_ctas<BB>();
+    EHL_BETA_CASES(EHL_CASE)
+#undef EHL_CASE
+    default:
+      return 1;
+  }
+}
+
+// The automatic choice: among the admissible r that keep the batch within two
+// rounds of resident groups, the one with the shortest chain per group -- its
+// sweep levels (sf) plus the reduced system of its system (2r block steps of
+// about b levels each).  Measured with 20 warps per SM resident: the standalone
+// batch (4096 x n = 1024, b = 4) takes 1.76, 1.21, 1.24, 1.12, 1.21 ms for
+// r = 1, 2, 3, 4, 6 (the choice: 4); 512 x n = 1025 at b = 8 (16 warps per SM)
+// 1.46, 0.87, 0.68 ms for r = 1, 2, 4 (the choice: 4).
 int paqif_parts(int n_sys, int n, int beta, int requested) {
   Geom g;
   if (requested > 0) return geom_ok(n_sys, n, beta, requested, g) ? requested : -1;
   const int gpc = groups_per_cta(beta);
-  if (gpc == 0 || n_sys < 1) return -1;
-  const long long target = (long long)kSmCount * 24 * (gpc / kPaqifWarpsPerCta);
+  if (gpc == 0 || n_sys < 1 || !geom_ok(n_sys, n, beta, 1, g)) return -1;
+  const long long resident = (long long)kSmCount * resident_ctas(beta) * gpc;
   int best = 1;
+  long long best_chain = g.sf;
   for (int r = 2; r <= gpc; ++r) {
-    if ((long long)n_sys * (r - 1) >= target) break;
-    if (!geom_ok(n_sys, n, beta, r, g) || g.sf < 4 * beta) continue;
-    best = r;
+    if ((long long)n_sys * r > 2 * resident) break;
+    if (!geom_ok(n_sys, n, beta, r, g)) continue;
+    const long long chain = g.sf + 2LL * beta * r;
+    if (chain < best_chain) {
+      best = r;
+      best_chain = chain;
+    }
   }
   return best;
 }

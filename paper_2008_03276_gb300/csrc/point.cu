@@ -680,6 +680,7 @@ ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int 
     }
     if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) return EHL_ECUDA;
     cublasSetStream(c->blas, c->st);
+    if (precision == 2) cublasSetEmulationStrategy(c->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
     k_pt_tall<<<(unsigned)((tall + 255) / 256), 256, 0, c->st>>>(c->gtab64, c->Tall, c->nx, c->ny);
     note_launch();
     c->precision = precision;
