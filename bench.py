@@ -49,7 +49,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one full-size paqif4_kernel<4, double-float> launch from the ncu
 # capture summarised in profiles/, valid only for the kernel sources with these
 # sha256 prefixes; any other source reports traffic = null.
-PAQIF_TRAFFIC = {("206416e0048045bf", "4addd33d7cfa0c6e"): 598074368 + 327899136}
+PAQIF_TRAFFIC = {("b8f71043a647d947", "4addd33d7cfa0c6e"): 561059328 + 307227648}
 
 
 def paqif_traffic():
