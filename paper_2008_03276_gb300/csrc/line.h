@@ -47,6 +47,9 @@ struct LineCtx {
   // graph mode: one Newton step captured as a CUDA graph (no host checks inside; the first
   // kGraphTrials line-search trials), replayed each outer iteration
   bool use_graph = false, capturing = false;
+  // the state arrays (H, R, rho, eps, ...) hold the state at (Pw, H0w) of every instance: the
+  // line search of the last Newton step evaluated and accepted it there
+  bool state_current = false;
   cudaGraphExec_t graph = nullptr;
   const double *g_P = nullptr, *g_H0 = nullptr, *g_rough = nullptr;  // pointers the graph was captured with
   long long graph_launches = 0;

@@ -774,6 +774,7 @@ static cudaError_t iterate_graph(LineCtx* c, const double* rough, std::vector<in
 // done or max_iter; ends with the residual at the returned iterate and the
 // done flags in hdone.
 static cudaError_t iterate(LineCtx* c, const double* rough, std::vector<int>& hdone) {
+  c->state_current = false;
   cudaError_t e = cudaMemsetAsync(c->done, 0, sizeof(int) * c->n_inst, c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->iters, 0, sizeof(int) * c->n_inst, c->st);
   // bytes 0x7f: best = 1.4e306 (no residual seen yet)

@@ -33,6 +33,7 @@ struct NkBuf {
   double *phi = nullptr, *phinorm = nullptr, *zH = nullptr, *den = nullptr, *delta = nullptr;
   double *Pt = nullptr, *H0t = nullptr, *tstep = nullptr, *rtol = nullptr, *beta0 = nullptr;
   double *znode = nullptr, *zh0 = nullptr, *w = nullptr;
+  double* jc = nullptr;  // per node, fixed for a Newton step: drho H, 3 eps/H, eps (drho/rho - deta), 1/d
   int *gm_k = nullptr, *gm_conv = nullptr, *lsdone = nullptr, *skip = nullptr;
   int* lsphase = nullptr;  // line search: 0 projected trials (P_t >= 0), 1 unprojected
   void* fstore = nullptr;  // PAQIF factor store of the current preconditioner
@@ -182,18 +183,60 @@ __device__ __forceinline__ double line_jv_row(const JvArgs& q, size_t base, int 
   return dC - dq / (h * h);
 }
 
+// The coefficients of the directional derivative that do not depend on the
+// direction, once per Newton step: jc[j] = (drho_j H_j, 3 eps_j / H_j,
+// eps_j (drho_j / rho_j - deta_j), 1 / d_j), so that a Krylov product needs no
+// division (the FP64 pipe runs at 1/64 of the FP32 rate).
+__global__ void k_nk_jvcoef(const double* __restrict__ rho, const double* __restrict__ drho,
+                            const double* __restrict__ deta_rel, const double* __restrict__ eps,
+                            const double* __restrict__ H, const double* __restrict__ dg, const int* __restrict__ skip,
+                            double* __restrict__ jc, int N) {
+  const int z = blockIdx.y;
+  if (skip[z]) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const size_t o = (size_t)z * N + j;
+  const double e = eps[o], Hj = H[o];
+  double* c = jc + 4 * o;
+  c[0] = drho[o] * Hj;
+  c[1] = 3.0 * e / Hj;
+  c[2] = e * (drho[o] / rho[o] - deta_rel[o]);
+  c[3] = (j >= 1 && j <= N - 2) ? 1.0 / dg[(size_t)z * (N - 2) + j - 1] : 0.0;
+}
+
+// line_jv_row with the per-step coefficients, every nodal derivative formed once
+__device__ __forceinline__ double line_jv_row_c(const JvArgs& q, const double* __restrict__ jc, size_t base, int i,
+                                                double ih, double ih2) {
+  const double* cj = jc + 4 * base;
+  auto dU = [&](int j) { return q.rho[base + j] * q.dH[base + j] + cj[4 * j] * q.zn[base + j]; };
+  auto dE = [&](int j) { return cj[4 * j + 1] * q.dH[base + j] + cj[4 * j + 2] * q.zn[base + j]; };
+  const double um2 = (i >= 2) ? dU(i - 2) : 0.0, um1 = dU(i - 1), u0 = dU(i), up1 = dU(i + 1);
+  const double F1 = u0 + 0.5 * (q.psia[base + i] * (u0 - um1) + q.psib[base + i] * (up1 - u0));
+  const double F0 =
+      (i == 1) ? um1 : um1 + 0.5 * (q.psia[base + i - 1] * (um1 - um2) + q.psib[base + i - 1] * (u0 - um1));
+  const double em1 = dE(i - 1), e0 = dE(i), ep1 = dE(i + 1);
+  const double ef1 = 0.5 * (q.eps[base + i] + q.eps[base + i + 1]);
+  const double ef0 = 0.5 * (q.eps[base + i - 1] + q.eps[base + i]);
+  const double Pi = q.P[base + i];
+  const double* zn = q.zn + base;
+  const double dq = 0.5 * (e0 + ep1) * (q.P[base + i + 1] - Pi) + ef1 * (zn[i + 1] - zn[i]) -
+                    0.5 * (em1 + e0) * (Pi - q.P[base + i - 1]) - ef0 * (zn[i] - zn[i - 1]);
+  return (F1 - F0) * ih - dq * ih2;
+}
+
 // w = J_Phi z for the interior rows (the force row is added in k_nk_arnoldi)
 __global__ void k_nk_jv(const LineInst* __restrict__ inst, NkBuf b, JvArgs q, const uint8_t* __restrict__ act,
-                        const double* __restrict__ dg, const int* __restrict__ skip, int N) {
+                        const int* __restrict__ skip, int N) {
   const int z = blockIdx.y;
   if (skip[z]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;  // interior node
   if (i > N - 2) return;
   const int n = N - 2, n1 = n + 1;
   const size_t base = (size_t)z * N;
-  const double jv = line_jv_row(q, base, i, inst[z].h);
+  const double h = inst[z].h;
+  const double jv = line_jv_row_c(q, b.jc, base, i, 1.0 / h, 1.0 / (h * h));
   const size_t o = (size_t)z * n + (i - 1);
-  b.w[(size_t)z * n1 + (i - 1)] = act[o] ? q.zn[base + i] : jv / dg[o];
+  b.w[(size_t)z * n1 + (i - 1)] = act[o] ? q.zn[base + i] : jv * b.jc[4 * (base + i) + 3];
 }
 
 // out[z][i] = (dR_i/dP) v + (dR_i/dH0) v_H0 at interior nodes, 0 at the boundary
@@ -412,6 +455,7 @@ cudaError_t line_nk_alloc(LineCtx* c) {
             {(void**)&b->znode, sizeof(double) * NN},
             {(void**)&b->zh0, sizeof(double) * ni},
             {(void**)&b->w, sizeof(double) * ni * (size_t)n1},
+            {(void**)&b->jc, sizeof(double) * 4 * NN},
             {(void**)&b->gm_k, sizeof(int) * ni},
             {(void**)&b->gm_conv, sizeof(int) * ni},
             {(void**)&b->lsdone, sizeof(int) * ni},
@@ -480,7 +524,11 @@ static cudaError_t line_nk_trials(LineCtx* c, double* P, double* H0, const doubl
     k_nk_merit<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->R, c->red, c->dg, b.skip, P, H0, N);
     note_launch();
     if (check) {
-      if (all_set(c, c->done, b.lsdone, e)) break;
+      if (all_set(c, c->done, b.lsdone, e)) {
+        // every instance accepted its last evaluated trial: the state arrays are at the new iterate
+        c->state_current = true;
+        break;
+      }
       if (e != cudaSuccess) return e;
     }
   }
@@ -498,12 +546,19 @@ cudaError_t line_nk_finish(LineCtx* c, double* P, double* H0, const double* roug
 cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough) {
   NkBuf& b = *(NkBuf*)c->nk;
   const int ni = c->n_inst, N = c->N;
-  cudaError_t e = line_state(c, P, H0, rough, c->done, nullptr);
+  cudaError_t e = cudaSuccess;
+  // the state at (P, H0) was left by the accepted line-search trials of the last step,
+  // unless this step is captured into a graph (which must compute it on every replay)
+  if (c->capturing || !c->state_current) e = line_state(c, P, H0, rough, c->done, nullptr);
+  c->state_current = false;
   if (e == cudaSuccess) e = line_finalize(c, c->done, c->iters);
   if (e == cudaSuccess) e = line_jac_band(c, P, 1, c->band, c->act, c->jh, c->dg, c->done);
   if (e != cudaSuccess) return e;
   k_nk_setup<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, P, c->R, c->red, c->act, c->dg, c->jh, c->done, c->band,
                                          c->rhs, N, c->beta);
+  note_launch();
+  k_nk_jvcoef<<<dim3((N + 255) / 256, ni), 256, 0, c->st>>>(c->rho, c->drho, c->deta_rel, c->eps, c->H, c->dg,
+                                                            c->done, b.jc, N);
   note_launch();
   e = paqif_on(c, c->rhs, c->sigma, true);  // factor, solving for the border column
   if (e != cudaSuccess) return e;
@@ -520,7 +575,7 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
     e = line_krylov_deform(c, b.znode, b.zh0, b.skip);
     if (e != cudaSuccess) return e;
     JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, b.znode};
-    k_nk_jv<<<gn, 256, 0, c->st>>>(c->inst, b, q, c->act, c->dg, b.skip, N);
+    k_nk_jv<<<gn, 256, 0, c->st>>>(c->inst, b, q, c->act, b.skip, N);
     note_launch();
     k_nk_arnoldi<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, b.skip, c->rhs, N);
     note_launch();

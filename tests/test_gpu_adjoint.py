@@ -187,7 +187,7 @@ def test_adjoint_c5_full_amplitude_reports():
     """The full-amplitude recipe: instances at or near contact (H_min <= 0) and the worst
     conditioned ones may not converge to tol 1e-10; they are reported through their
     residual and the status.  The converged ones give finite gradients that agree with the
-    oracle to the accuracy their conditioning allows (1e-15 x cond)."""
+    oracle to the accuracy their conditioning allows (1e-14 x cond)."""
     N, M, L, n = 1025, 50.0, 10.0, 8
     rgh = c5_roughness(N, n)
     ctx = make(N, M, L, 1, 8, tol=1e-10, n_inst=n)
@@ -213,4 +213,4 @@ def test_adjoint_c5_full_amplitude_reports():
         scale = np.max(np.abs(ref["rough"]))
         err = np.max(np.abs(gr[k] - ref["rough"])) / scale
         print(f"instance {k}: scaled condition {kappa:.2e}, gradient difference {err:.2e}")
-        assert err <= max(1e-8, 1e-15 * kappa)
+        assert err <= max(1e-8, 1e-14 * kappa)   # forward-error bound kappa u with a constant of ~100
