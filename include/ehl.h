@@ -121,8 +121,9 @@ ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* band, const
  *   partitions  r >= 1 blocks per system; 0 chooses r from the batch shape
  *               (what ehl_paqif_solve does).  The blocks have the even order
  *               n_p = 2 ceil(n / 2r); an admissible r divides the lane groups
- *               of one CTA (4 warps of 32 / (2 beta + 2) groups: 32, 20, 16,
- *               12, 8, 8, 8, 4 for beta = 1..8), and for r > 1 each block
+ *               of one CTA (4 warps, 8 at beta = 8, of 32 / (2 beta + 2)
+ *               groups each: 32, 20, 16, 12, 8, 8, 8, 8 for beta = 1..8),
+ *               and for r > 1 each block
  *               has n_p >= 2 beta + 2 and at least one row below n.
  * Returns EHL_EINVAL for an inadmissible r, otherwise as ehl_paqif_solve.
  * The workspace size depends on r (ehl_paqif_workspace_size_partitioned).

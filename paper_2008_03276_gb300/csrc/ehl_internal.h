@@ -8,7 +8,6 @@
 
 namespace ehl {
 
-constexpr int kPaqifWarpsPerCta = 4;
 constexpr int kSmCount = 152;  // GB300: grids are sized for its 152 SMs
 constexpr int kPaqifMaxActiveSetSteps = 64;
 // Newton steps of a coarse grid of the nested iteration at most (a coarse grid that

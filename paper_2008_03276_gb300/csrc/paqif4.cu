@@ -51,6 +51,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <math.h>
+
 #include <atomic>
 
 #include "df64.cuh"
@@ -70,11 +72,14 @@ struct C4 {
   static constexpr int FL = GS;               // factor-store float4 per level: one per row slot
   static constexpr int RB = (B <= 4) ? 16 : 32;  // ring rows per side
   static constexpr int CH = RB / 4;           // rows per chunk (b <= CH keeps the live window in the ring)
-  static constexpr int WARPS = kPaqifWarpsPerCta;
+  // warps per CTA: 8 at b = 8 (one group per warp), so that a system can be cut into up to
+  // 8 blocks within one CTA; 4 below
+  static constexpr int WARPS = (B == 8) ? 8 : 4;
   static constexpr int GPC = WARPS * G;       // groups per CTA
   static constexpr int BB = B * B;
-  // resident CTAs per SM the register budget is set for (shared memory allows 5 up to b = 4)
-  static constexpr int MINB = (B <= 4) ? 5 : 4;
+  // resident CTAs per SM the register budget is set for: 5 x 4 warps up to b = 4 (shared
+  // memory allows 5), 4 x 4 warps for b = 5..7, 2 x 8 warps at b = 8
+  static constexpr int MINB = (B <= 4) ? 5 : (B == 8 ? 2 : 4);
 };
 
 // reduced-system blocks of one partition: blocks 2m (first b rows) and 2m+1
@@ -1051,11 +1056,14 @@ static int resident_ctas(int beta) {
 
 // The automatic choice: among the admissible r that keep the batch within two
 // rounds of resident groups, the one with the shortest chain per group -- its
-// sweep levels (sf) plus the reduced system of its system (2r block steps of
-// about b levels each).  Measured with 20 warps per SM resident: the standalone
-// batch (4096 x n = 1024, b = 4) takes 1.76, 1.21, 1.24, 1.12, 1.21 ms for
-// r = 1, 2, 3, 4, 6 (the choice: 4); 512 x n = 1025 at b = 8 (16 warps per SM)
-// 1.46, 0.87, 0.68 ms for r = 1, 2, 4 (the choice: 4).
+// sweep levels (sf) plus the 2r block steps of its system's reduced system,
+// counted as b levels each -- and on a tie the larger r if the batch still fits
+// in one round.  Measured (CUDA events): the standalone batch (4096 x n = 1024,
+// b = 4, 20 warps per SM) takes 1.76, 1.21, 1.24, 1.12, 1.21 ms for r = 1, 2,
+// 3, 4, 6 (the choice: 4); 512 x n = 1025 at b = 8 (16 warps per SM) 1.46,
+// 0.93, 0.68, 0.88 ms for r = 1, 2, 4, 8 (4); 64 x n = 1025 at b = 8 0.50 and
+// 0.32 ms for r = 4, 8 (8); one system of n = 4097 at b = 8 5.77, 3.57, 1.83,
+// 0.99 ms (8).
 int paqif_parts(int n_sys, int n, int beta, int requested) {
   Geom g;
   if (requested > 0) return geom_ok(n_sys, n, beta, requested, g) ? requested : -1;
@@ -1065,10 +1073,11 @@ int paqif_parts(int n_sys, int n, int beta, int requested) {
   int best = 1;
   long long best_chain = g.sf;
   for (int r = 2; r <= gpc; ++r) {
-    if ((long long)n_sys * r > 2 * resident) break;
+    const long long groups = (long long)n_sys * r;
+    if (groups > 2 * resident) break;
     if (!geom_ok(n_sys, n, beta, r, g)) continue;
     const long long chain = g.sf + 2LL * beta * r;
-    if (chain < best_chain) {
+    if (chain < best_chain || (chain == best_chain && groups <= resident)) {
       best = r;
       best_chain = chain;
     }

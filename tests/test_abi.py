@@ -43,10 +43,10 @@ def test_host_side_argument_checks():
     assert lib.ehl_paqif_workspace_size(4, 16, 9, 0, ctypes.byref(nb)) == _ffi.EHL_EINVAL
     assert lib.ehl_paqif_workspace_size(4, 16, 2, 3, ctypes.byref(nb)) == _ffi.EHL_EINVAL
     assert lib.ehl_paqif_workspace_size(4, 16, 2, 0, ctypes.byref(nb)) == _ffi.EHL_OK and nb.value > 0
-    # partition counts: r must divide the lane groups of a CTA (4 at beta = 8, 12 at beta = 4) and
+    # partition counts: r must divide the lane groups of a CTA (8 at beta = 8, 12 at beta = 4) and
     # leave every block an interior level (order >= 2 beta + 2) and a real row
     ws = lib.ehl_paqif_workspace_size_partitioned
-    assert ws(4, 1024, 8, 4, 0, ctypes.byref(nb)) == _ffi.EHL_OK and nb.value > 0
+    assert ws(4, 1024, 8, 8, 0, ctypes.byref(nb)) == _ffi.EHL_OK and nb.value > 0
     assert ws(4, 1024, 8, 3, 0, ctypes.byref(nb)) == _ffi.EHL_EINVAL
     assert ws(4, 1024, 4, 12, 0, ctypes.byref(nb)) == _ffi.EHL_OK
     assert ws(4, 16, 8, 2, 0, ctypes.byref(nb)) == _ffi.EHL_EINVAL

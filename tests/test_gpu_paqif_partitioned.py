@@ -18,7 +18,7 @@ from paper_2008_03276_gb300 import inputs, ops
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
-GPC = {1: 32, 2: 20, 3: 16, 4: 12, 5: 8, 6: 8, 7: 8, 8: 4}  # lane groups per CTA
+GPC = {1: 32, 2: 20, 3: 16, 4: 12, 5: 8, 6: 8, 7: 8, 8: 8}  # lane groups per CTA
 
 
 def admissible(beta, n, r):
