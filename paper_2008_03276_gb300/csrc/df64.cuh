@@ -140,6 +140,14 @@ __device__ __forceinline__ df df_from_double(double d) {
   unsigned sign = hw & 0x80000000u;
   int e = (int)((hw >> 20) & 0x7ffu);
   df r;
+  if (e >= 949 && e < 1151) {
+    // |d| in [2^-74, 2^128): hi and the scale of lo are normal floats (one multiply, no branches)
+    const int fe0 = e - 896;
+    r.hi = __uint_as_float(sign | ((unsigned)fe0 << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    const float lo0 = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), __uint_as_float((unsigned)(fe0 - 52) << 23));
+    r.lo = __uint_as_float(__float_as_uint(lo0) | sign);
+    return r;
+  }
   if (e == 0x7ff) {  // Inf / NaN
     r.hi = __uint_as_float(sign | 0x7f800000u | (((hw & 0xfffffu) | lw) ? 0x400000u : 0u));
     r.lo = 0.f;

@@ -367,11 +367,8 @@ struct P4 {
         if (c == 0 || c == C::W) continue;
         const float4 z = zb[c];
         const df o = A::sub_two_prods(piv ? df_zero() : R[c], al, make_df(z.x, z.y), be, make_df(z.z, z.w));
-        if (piv) {
-          if (ln.live) reinterpret_cast<float2*>(p.stk + (size_t)k * C::SL + sidx(c))[sg] = df2f(o);
-        } else {
-          R[c] = o;
-        }
+        if (piv && ln.live) reinterpret_cast<float2*>(p.stk + (size_t)k * C::SL + sidx(c))[sg] = df2f(o);
+        R[c] = o;  // a pivot row's registers are replaced by the incoming row below
       }
       // the columns move one step towards the pivot
 #pragma unroll
@@ -607,9 +604,9 @@ struct P4 {
     df pend_x = df_zero();
     int pend_row = -1;
     auto store_x = [&](df xv, int row) {
-      double d = A::to_double(xv);
-      if (!isfinite(d) && flag == 0) flag = EHL_INFO_NONFINITE;
-      if (p.mode == 1) d = d > 0.0 ? d : 0.0;
+      // the sign and finiteness of hi + lo are those of hi (|lo| <= ulp(hi) / 2)
+      if (!isfinite(xv.hi) && flag == 0) flag = EHL_INFO_NONFINITE;
+      const double d = (p.mode == 1 && !(xv.hi > 0.f)) ? 0.0 : A::to_double(xv);
       if (real && ln.live && row < n) p.x[row] = d;
     };
     // terms of the pair (x_p, x_q) of level k in level k - d (columns (left, d) and (right, d))
