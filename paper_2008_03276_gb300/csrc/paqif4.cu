@@ -332,9 +332,9 @@ struct P4 {
     for (int c = 0; c < C::NC; ++c)
       R[c] = (c == C::RHS) ? rhs_of(sm, sg, j, kind) : any_entry(sm, sg, j, c / C::W, c % C::W, kind, s, n);
 
-    int pj = 0;  // k mod W: the row slot of the pivots
+    int off = j;  // this lane's row is stream index k + off (0: a pivot row)
     for (int k = 0; k < p.sf; ++k) {
-      const bool piv = (j == pj);
+      const bool piv = (off == 0);
       float4* zb = sm.zb[k & 1];
       // the two pivot rows to shared memory (double-buffered: one barrier a level)
       if (piv && ln.live) {
@@ -375,8 +375,10 @@ struct P4 {
       for (int sd = 0; sd < 2; ++sd)
 #pragma unroll
         for (int d = 1; d <= B; ++d) R[sd * C::W + d - 1] = R[sd * C::W + d];
-      // rows entering at the end of this level have stream index tn on both sides
+      // rows entering at the end of this level have stream index tn on both sides; away from
+      // the block's ends every column the incoming row and column touch lies inside it
       const int tn = k + C::W;
+      const bool inner = (tn < s) && (s + tn < n);
       if (tn >= conv * C::CH) {
         // issue chunk conv+2 into the slots of chunk conv-2 (stream indices
         // below CH (conv-1) <= tn - b, no longer referenced); then at most the
@@ -402,7 +404,7 @@ struct P4 {
           } else if (c / C::W == sg) {
             const int d = c % C::W;
             if (kn == 1) {
-              if (col_in(sg, k + 1 + d, s, n)) v = band_at(sm, sg, tn, sg ? d : 2 * B - d);
+              if (inner || col_in(sg, k + 1 + d, s, n)) v = band_at(sm, sg, tn, sg ? d : 2 * B - d);
             } else if (kn == 2 && d == B) {
               v = make_df(1.f, 0.f);
             }
@@ -414,18 +416,18 @@ struct P4 {
         // the incoming column of this side (stream tn) at distance b: the
         // row (stream tr = tn - dd) meets it at band[b - dd] on the left,
         // band[b + dd] on the right
-        const int dd = C::W - (j - pj + C::W) % C::W;
+        const int dd = C::W - off;
         df v = df_zero();
-        if (kind == 1 && col_in(sg, tn, s, n)) v = band_at(sm, sg, tn - dd, sg ? B + dd : B - dd);
+        if (kind == 1 && (inner || col_in(sg, tn, s, n))) v = band_at(sm, sg, tn - dd, sg ? B + dd : B - dd);
         R[B] = sg ? df_zero() : v;
         R[C::W + B] = sg ? v : df_zero();
       }
-      pj = (pj == B) ? 0 : pj + 1;
+      off = (off == 0) ? B : off - 1;
     }
     cpa_wait<0>();
     __threadfence_block();
     __syncwarp();
-    if (p.sf < s) outer_out(sm, p, ln, R, pj);
+    if (p.sf < s) outer_out(sm, p, ln, R, off);
   }
 
   // The block's part of the reduced system: the 2b x 2b Schur complement left
@@ -433,9 +435,9 @@ struct P4 {
   // and the transformed rhs, then the band entries coupling its first b rows
   // to the last b columns of the previous block and its last b rows to the
   // first b columns of the next.
-  static __device__ void outer_out(Sm4<B>& sm, const Part4& p, const L& ln, const df (&R)[C::NC], int pj) {
+  static __device__ void outer_out(Sm4<B>& sm, const Part4& p, const L& ln, const df (&R)[C::NC], int off) {
     const int s = p.s, sg = ln.side;
-    const int tr = p.sf + (ln.j - pj + C::W) % C::W;  // stream index of this lane's row
+    const int tr = p.sf + off;  // stream index of this lane's row
     if (tr <= s - 1 && ln.live) {
       const int o = outer_index(sg, tr, s);
       const int h = sg, rb = o - h * B;  // block (first / last rows) and row in it
@@ -618,9 +620,9 @@ struct P4 {
       acc = A::sub_two_prods(acc, df_neg(m1), xp, df_neg(m2), xq);
     };
     int pj = (s - 1) % C::W;
+    int d = (pj - j + C::W) % C::W;  // this lane's next level is k - d
     // the outer levels, known from the reduced system
     for (int k = s - 1; k >= sf; --k) {
-      const int d = (pj - j + C::W) % C::W;
       df xv = df_zero();
       if (d == 0) xv = f2df(sm.xo[outer_index(sg, k, s)]);
       const df xp = shfl_df(xv, ln.gbase + pj), xq = shfl_df(xv, ln.gbase + C::W + pj);
@@ -632,6 +634,7 @@ struct P4 {
         push(k, d, xp, xq);
       }
       pj = (pj == 0) ? B : pj - 1;
+      d = (d == 0) ? B : d - 1;
     }
     for (int k = sf - 1; k >= 0; --k) {
       const int v = sf - 1 - k;
@@ -643,7 +646,6 @@ struct P4 {
         cpa_wait<1>();
         __syncwarp();
       }
-      const int d = (pj - j + C::W) % C::W;  // this lane's next level is k - d
       df xv = df_zero();
       if (d == 0) {
         const float4 cv = sm.u.stk[v & (C::RB - 1)][2 * B];  // folded rhs column: Pi^-1 y
@@ -661,6 +663,7 @@ struct P4 {
         push(k, d, xp, xq);
       }
       pj = (pj == 0) ? B : pj - 1;
+      d = (d == 0) ? B : d - 1;
     }
     if (pend_row >= 0) store_x(pend_x, pend_row);
     cpa_wait<0>();
