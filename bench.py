@@ -49,7 +49,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one full-size paqif4_kernel<4, double-float> launch from the ncu
 # capture summarised in profiles/, valid only for the kernel sources with these
 # sha256 prefixes; any other source reports traffic = null.
-PAQIF_TRAFFIC = {("b8f71043a647d947", "4addd33d7cfa0c6e"): 561059328 + 307227648}
+PAQIF_TRAFFIC = {("5a3f92cdc7006ae7", "6a71297bc569ed85"): 563905536 + 308637952}
 
 
 def paqif_traffic():

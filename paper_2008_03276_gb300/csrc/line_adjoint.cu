@@ -112,7 +112,8 @@ __global__ void k_adj_prepare(const LineInst* __restrict__ inst, double* __restr
   if (!act[o]) {
     const double d = dg[o];
     double* row = band + o * bw;
-    for (int j = 0; j < bw; ++j) row[j] /= d;
+    const double rd = 1.0 / d;  // one float64 division per row
+    for (int j = 0; j < bw; ++j) row[j] *= rd;
     cb[o] = jh[o] / d;
   } else {
     cb[o] = 0.0;

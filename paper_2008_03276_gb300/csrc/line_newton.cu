@@ -80,9 +80,11 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_setup(const LineInst* __restric
       ph = Pi;
       rhs[o] = 0.0;
     } else {
-      ph = Ri / d;
+      ph = Ri / d;  // as in k_nk_merit, so the line search compares like with like
+      // the preconditioner's band: one division per row, not per entry (FP64 runs at 1/64 rate)
+      const double rd = 1.0 / d;
       double* row = band + o * bw;
-      for (int j = 0; j < bw; ++j) row[j] /= d;
+      for (int j = 0; j < bw; ++j) row[j] *= rd;
       rhs[o] = jh[o] / d;
     }
     phi[r] = ph;
@@ -93,7 +95,8 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_setup(const LineInst* __restric
   ss = block_sum(ss, sh) + f * f;
   const double nrm = sqrt(ss);
   double* v0 = b.V + (size_t)z * (b.m + 1) * n1;
-  for (int r = threadIdx.x; r < n1; r += kNkBlock) v0[r] = nrm > 0.0 ? -phi[r] / nrm : 0.0;
+  const double rn = nrm > 0.0 ? -1.0 / nrm : 0.0;
+  for (int r = threadIdx.x; r < n1; r += kNkBlock) v0[r] = phi[r] * rn;
   if (threadIdx.x == 0) {
     b.phinorm[z] = nrm;
     b.beta0[z] = nrm;

@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(kNB) k_pn_setup(PtView v, const double* __rest
     } else {
       const double d = v.dg[o];
       double* row = v.band + o * w;
-      for (int t = 0; t < w; ++t) row[t] /= d;
+      const double rd = 1.0 / d;  // one float64 division per row
+      for (int t = 0; t < w; ++t) row[t] *= rd;
       v.rhs[o] = v.jh[o] / d;
       ph = v.R[node] / d;
     }
@@ -725,7 +726,8 @@ __global__ void k_pa_prepare(PtView v, PtAdj a) {
   if (!v.act[o]) {
     const double d = v.dg[o];
     double* row = v.band + o * w;
-    for (int t = 0; t < w; ++t) row[t] /= d;
+    const double rd = 1.0 / d;
+    for (int t = 0; t < w; ++t) row[t] *= rd;
     a.cb[o] = v.jh[o] / d;
   } else {
     a.cb[o] = 0.0;
