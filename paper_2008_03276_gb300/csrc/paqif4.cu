@@ -712,36 +712,39 @@ struct P4 {
     }
     __syncwarp();
   }
-  // y = f - A x (lanes i < b), written to dst
+  // y = f - A x, row i by the lane pair (2i, 2i+1): each lane takes every other term, the
+  // pair adds its halves with one shuffle (the reduced solve's dependent chain is b/2 terms)
   static __device__ __forceinline__ void matvec_sub(const float2* Am, const float2* xv, const float2* fv, float2* dst,
                                                     bool st, const L& ln) {
-    const int i = min(ln.u, B - 1);
-    df a = f2df(fv[i]);
+    const int i = min(ln.u >> 1, B - 1), h = ln.u & 1;
+    df a = h ? df_zero() : f2df(fv[i]);
 #pragma unroll
-    for (int q = 0; q < B; q += 2) {
-      const df a0 = f2df(Am[i * B + q]), x0 = f2df(xv[q]);
-      const df a1 = (q + 1 < B) ? f2df(Am[i * B + q + 1]) : df_zero();
-      const df x1 = (q + 1 < B) ? f2df(xv[q + 1 < B ? q + 1 : q]) : df_zero();
+    for (int q = 0; q < B; q += 4) {
+      const int q0 = q + h, q1 = q + 2 + h;
+      const df a0 = (q0 < B) ? f2df(Am[i * B + q0]) : df_zero(), x0 = (q0 < B) ? f2df(xv[q0]) : df_zero();
+      const df a1 = (q1 < B) ? f2df(Am[i * B + q1]) : df_zero(), x1 = (q1 < B) ? f2df(xv[q1]) : df_zero();
       a = A::sub_two_prods(a, a0, x0, a1, x1);
     }
+    a = df_add(a, make_df(__shfl_xor_sync(0xffffffffu, a.hi, 1), __shfl_xor_sync(0xffffffffu, a.lo, 1)));
     __syncwarp();
-    if (st && ln.u < B) dst[ln.u] = df2f(a);
+    if (st && h == 0 && (ln.u >> 1) < B) dst[ln.u >> 1] = df2f(a);
     __syncwarp();
   }
-  // y = A x (lanes i < b)
+  // y = A x, by lane pairs as above
   static __device__ __forceinline__ void matvec(const float2* Am, const float2* xv, float2* dst, bool st,
                                                 const L& ln) {
-    const int i = min(ln.u, B - 1);
+    const int i = min(ln.u >> 1, B - 1), h = ln.u & 1;
     df a = df_zero();
 #pragma unroll
-    for (int q = 0; q < B; q += 2) {
-      const df a0 = f2df(Am[i * B + q]), x0 = f2df(xv[q]);
-      const df a1 = (q + 1 < B) ? f2df(Am[i * B + q + 1]) : df_zero();
-      const df x1 = (q + 1 < B) ? f2df(xv[q + 1 < B ? q + 1 : q]) : df_zero();
+    for (int q = 0; q < B; q += 4) {
+      const int q0 = q + h, q1 = q + 2 + h;
+      const df a0 = (q0 < B) ? f2df(Am[i * B + q0]) : df_zero(), x0 = (q0 < B) ? f2df(xv[q0]) : df_zero();
+      const df a1 = (q1 < B) ? f2df(Am[i * B + q1]) : df_zero(), x1 = (q1 < B) ? f2df(xv[q1]) : df_zero();
       a = A::sub_two_prods(a, df_neg(a0), x0, df_neg(a1), x1);
     }
+    a = df_add(a, make_df(__shfl_xor_sync(0xffffffffu, a.hi, 1), __shfl_xor_sync(0xffffffffu, a.lo, 1)));
     __syncwarp();
-    if (st && ln.u < B) dst[ln.u] = df2f(a);
+    if (st && h == 0 && (ln.u >> 1) < B) dst[ln.u >> 1] = df2f(a);
     __syncwarp();
   }
   // in-place inverse by Gauss-Jordan elimination without pivoting
