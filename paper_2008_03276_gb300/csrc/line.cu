@@ -798,8 +798,8 @@ cudaError_t line_mixed_init(LineCtx* c, int precision) {
   if (e != cudaSuccess) return e;
   cublasSetWorkspace(c->blas, ws, wsb);
   cublasSetMathMode(c->blas, CUBLAS_DEFAULT_MATH);
-  // precision 2 asks for the BF16x9 tensor-core emulation: cuBLAS's default strategy picks a
-  // SIMT SGEMM for these shapes (N x n_inst x N), the eager one the emulated kernels
+  // precision 2 asks for the BF16x9 tensor-core emulation with the eager strategy (cuBLAS
+  // still runs SIMT SGEMM kernels for these shapes, N x n_inst x N with odd N)
   if (precision == 2) cublasSetEmulationStrategy(c->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
   k_line_kfull<<<(unsigned)((NN + 255) / 256), 256, 0, c->st>>>(c->gtab64, c->Kf, c->N);
   note_launch();
@@ -814,8 +814,8 @@ void line_mixed_free(LineCtx* c) {
 
 // dH = -K v + zh0 for the Krylov vectors: the double-float Toeplitz kernel, or
 // with precision > 0 one float32-output GEMM K [N x N] . V [N x n_inst] of the
-// whole bucket (precision 1 float32, 2 float32 emulated on BF16 tensor cores,
-// 3 TF32, 4 BF16 tensor cores).
+// whole bucket (precision 1 float32, 2 float32 with the BF16x9 emulation
+// requested -- cuBLAS runs SIMT SGEMM kernels for these shapes --, 3 TF32, 4 BF16).
 cudaError_t line_krylov_deform(LineCtx* c, const double* V, const double* zh0, const int* skip) {
   if (c->precision <= 0) {
     cudaError_t e = line_deform(c, V, c->N, skip);

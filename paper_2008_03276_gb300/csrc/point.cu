@@ -175,8 +175,9 @@ __global__ void k_pt_film(const PointInst* __restrict__ inst, const void* __rest
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= NN) return;
   double D;
-  if (p64 == 2) {  // one float32 product [n_inst][NN] (the GEMM path)
-    D = (double)reinterpret_cast<const float*>(partial)[(size_t)z * NN + t];
+  if (p64 == 2) {  // one float32 product [n_inst][ny][ldc] (the GEMM path; ksplit carries ldc)
+    const int ldc = ksplit, jj = t / q.nx, ii = t - jj * q.nx;
+    D = (double)reinterpret_cast<const float*>(partial)[((size_t)z * q.ny + jj) * ldc + ii];
   } else if (p64) {
     const double* pd = reinterpret_cast<const double*>(partial);
     D = 0.0;
@@ -555,25 +556,35 @@ void pt_free(PtCtx* c) {
   c->blas = nullptr;
 }
 
-// T_all[i + (d nx + k) nx] = T[d][|i - k|]  (column-major nx x (nx ny), float32)
-__global__ void k_pt_tall(const double* __restrict__ gtab64, float* __restrict__ Tall, int nx, int ny) {
+// leading dimension of a GEMM operand: a multiple of 8 floats
+static size_t pt_ld8(size_t x) { return (x + 7) / 8 * 8; }
+
+// T_all[i + (d nx + k) ldt] = T[d][|i - k|]  (column-major nx x (nx ny), float32, leading
+// dimension ldt = nx rounded up to 8 floats: 32-byte aligned columns)
+__global__ void k_pt_tall(const double* __restrict__ gtab64, float* __restrict__ Tall, int nx, int ny, int ldt) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t total = (size_t)nx * nx * ny;
+  const size_t total = (size_t)ldt * nx * ny;
   if (t >= total) return;
-  const int i = (int)(t % nx);
-  const size_t col = t / nx;
+  const int i = (int)(t % ldt);
+  const size_t col = t / ldt;
   const int d = (int)(col / nx), k = (int)(col % nx);
-  Tall[t] = (float)gtab64[(size_t)d * nx + (i > k ? i - k : k - i)];
+  Tall[t] = (i < nx) ? (float)gtab64[(size_t)d * nx + (i > k ? i - k : k - i)] : 0.f;
 }
 
-// Q[(d nx + k) + j (nx ny)] = V[j][k] (d = 0) or V[j-d][k] + V[j+d][k] (rows outside the grid are 0)
-__global__ void k_pt_qmat(const double* __restrict__ V, float* __restrict__ Q, int nx, int ny) {
+// Q[(d nx + k) + j ldq] = V[j][k] (d = 0) or V[j-d][k] + V[j+d][k] (rows outside the grid are 0);
+// ldq = nx ny rounded up to 8 floats
+__global__ void k_pt_qmat(const double* __restrict__ V, float* __restrict__ Q, int nx, int ny, int ldq) {
   const int z = blockIdx.y;
   const size_t NN = (size_t)nx * ny;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= NN * ny) return;
-  const int j = (int)(t / NN);
-  const size_t rem = t % NN;
+  if (t >= (size_t)ldq * ny) return;
+  const int j = (int)(t / ldq);
+  const size_t rem = t % ldq;
+  float* Qz = Q + (size_t)z * ldq * ny;
+  if (rem >= NN) {
+    Qz[t] = 0.f;
+    return;
+  }
   const int d = (int)(rem / nx), k = (int)(rem % nx);
   const double* Vz = V + (size_t)z * NN;
   double s;
@@ -582,7 +593,7 @@ __global__ void k_pt_qmat(const double* __restrict__ V, float* __restrict__ Q, i
   } else {
     s = (j - d >= 0 ? Vz[(size_t)(j - d) * nx + k] : 0.0) + (j + d < ny ? Vz[(size_t)(j + d) * nx + k] : 0.0);
   }
-  Q[(size_t)z * NN * ny + t] = (float)s;
+  Qz[t] = (float)s;
 }
 
 static PtRow pt_row(PtCtx* c, const double* P) {
@@ -671,17 +682,18 @@ ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int 
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && precision > 0 && insts[0].m.elastic) {
-    const size_t tall = (size_t)c->nx * c->nx * c->ny, q = (size_t)c->NN * c->ny * ni;
+    const size_t ldt = pt_ld8(c->nx), ldq = pt_ld8((size_t)c->NN);
+    const size_t tall = ldt * c->nx * c->ny, q = ldq * c->ny * ni, dn = ldt * c->ny * ni;
     if (pt_alloc(c, (void**)&c->Tall, sizeof(float) * tall) != cudaSuccess ||
         pt_alloc(c, (void**)&c->Qf, sizeof(float) * q) != cudaSuccess ||
-        pt_alloc(c, (void**)&c->Df, sizeof(float) * NNt) != cudaSuccess) {
+        pt_alloc(c, (void**)&c->Df, sizeof(float) * dn) != cudaSuccess) {
       cudaGetLastError();
       return EHL_ENOMEM;
     }
     if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) return EHL_ECUDA;
     cublasSetStream(c->blas, c->st);
     if (precision == 2) cublasSetEmulationStrategy(c->blas, CUBLAS_EMULATION_STRATEGY_EAGER);
-    k_pt_tall<<<(unsigned)((tall + 255) / 256), 256, 0, c->st>>>(c->gtab64, c->Tall, c->nx, c->ny);
+    k_pt_tall<<<(unsigned)((tall + 255) / 256), 256, 0, c->st>>>(c->gtab64, c->Tall, c->nx, c->ny, (int)ldt);
     note_launch();
     c->precision = precision;
     e = cudaGetLastError();
@@ -750,11 +762,13 @@ cudaError_t pt_start(PtCtx* c, double* P, double* H0, const double* rough) {
 }
 
 // The Krylov products with precision > 0: per instance one GEMM T_all [nx x nx ny] . Q [nx ny x ny]
-// (precision 1 float32, 2 float32 emulated on BF16 tensor cores, 3 TF32, 4 BF16), float32 output.
+// (precision 1 float32, 2 float32 with the BF16x9 emulation requested, 3 TF32, 4 BF16), float32
+// output.  cuBLAS runs SIMT SGEMM kernels for precision 2 at these shapes (measured kernel names).
 static cudaError_t pt_deform_gemm(PtCtx* c, const double* zn, const int* skip, const double* zh0) {
-  const size_t NN = c->NN, qn = NN * c->ny;
+  const int ldt = (int)pt_ld8(c->nx), ldq = (int)pt_ld8((size_t)c->NN);
+  const size_t qn = (size_t)ldq * c->ny;
   dim3 g((unsigned)((qn + 255) / 256), c->n_inst);
-  k_pt_qmat<<<g, 256, 0, c->st>>>(zn, c->Qf, c->nx, c->ny);
+  k_pt_qmat<<<g, 256, 0, c->st>>>(zn, c->Qf, c->nx, c->ny, ldq);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -764,12 +778,12 @@ static cudaError_t pt_deform_gemm(PtCtx* c, const double* zn, const int* skip, c
   if (c->precision == 4) ct = CUBLAS_COMPUTE_32F_FAST_16BF;
   const float one = 1.0f, zero = 0.0f;
   const int m = c->nx, n = c->ny, k = c->nx * c->ny;
-  if (cublasGemmStridedBatchedEx(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, c->Tall, CUDA_R_32F, m, 0,
-                                 c->Qf, CUDA_R_32F, k, (long long)qn, &zero, c->Df, CUDA_R_32F, m, (long long)NN,
-                                 c->n_inst, ct, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+  if (cublasGemmStridedBatchedEx(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, c->Tall, CUDA_R_32F, ldt, 0,
+                                 c->Qf, CUDA_R_32F, ldq, (long long)qn, &zero, c->Df, CUDA_R_32F, ldt,
+                                 (long long)ldt * c->ny, c->n_inst, ct, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
     return cudaErrorUnknown;
   const dim3 gn((c->NN + kPtNode - 1) / kPtNode, c->n_inst);
-  k_pt_film<<<gn, kPtNode, 0, c->st>>>(c->inst, c->Df, 1, 2, zh0, nullptr, skip, c->dH, c->n_inst, 1);
+  k_pt_film<<<gn, kPtNode, 0, c->st>>>(c->inst, c->Df, ldt, 2, zh0, nullptr, skip, c->dH, c->n_inst, 1);
   note_launch();
   return cudaGetLastError();
 }
