@@ -49,7 +49,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one full-size paqif4_kernel<4, double-float> launch from the ncu
 # capture summarised in profiles/, valid only for the kernel sources with these
 # sha256 prefixes; any other source reports traffic = null.
-PAQIF_TRAFFIC = {("5a3f92cdc7006ae7", "6a71297bc569ed85"): 563905536 + 308637952}
+PAQIF_TRAFFIC = {("4b1ea1a7239ddc3e", "6a71297bc569ed85"): 563319296 + 309675776}
 
 
 def paqif_traffic():
