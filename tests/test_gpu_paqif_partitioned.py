@@ -128,3 +128,19 @@ def test_partitioned_full_size_standalone_batch():
         x, _, info = run(band, rhs, beta, 1, r)
         assert np.all(info == 0)
         assert np.max(np.abs(x[pick] - ref)) <= TOL * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("beta,r", [(2, 4), (4, 3), (8, 2)])
+def test_partitioned_matches_the_stepwise_oracle(beta, r):
+    """Against the dense walk-through of Sec. 2.2.4 Steps 1-7 (oracle/aqif_ref.py) on blocks of
+    the same order as the kernel's (n divisible by 2r)."""
+    from oracle import aqif_ref as aq
+
+    n = 2 * r * 24
+    band, rhs = inputs.dd_band_systems(3, n, beta, seed=31 + beta)
+    x, _, info = run(band, rhs, beta, 1, r)
+    assert np.all(info == 0)
+    for s in range(3):
+        A = pr.band_to_dense(band[s], beta)
+        ref = aq.paqif_partitioned(A, rhs[s], beta, r, mode=1)
+        assert np.max(np.abs(x[s] - ref)) <= TOL * np.max(np.abs(ref))
