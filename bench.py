@@ -49,7 +49,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one full-size paqif4_kernel<4, double-float> launch from the ncu
 # capture summarised in profiles/, valid only for the kernel sources with these
 # sha256 prefixes; any other source reports traffic = null.
-PAQIF_TRAFFIC = {("4b1ea1a7239ddc3e", "6a71297bc569ed85"): 563319296 + 309675776}
+PAQIF_TRAFFIC = {("7ec492ea359502ff", "6a71297bc569ed85"): 564364800 + 309009152}
 
 
 def paqif_traffic():

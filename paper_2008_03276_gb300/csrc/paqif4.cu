@@ -603,13 +603,34 @@ struct P4 {
     __syncwarp();
     int issued = 3;
     df acc = df_zero();
-    df pend_x = df_zero();
-    int pend_row = -1;
-    auto store_x = [&](df xv, int row) {
-      // the sign and finiteness of hi + lo are those of hi (|lo| <= ulp(hi) / 2)
-      if (!isfinite(xv.hi) && flag == 0) flag = EHL_INFO_NONFINITE;
-      const double d = (p.mode == 1 && !(xv.hi > 0.f)) ? 0.0 : A::to_double(xv);
-      if (real && ln.live && row < n) p.x[row] = d;
+    // The solution leaves in float64, a conversion on the FP64 pipe (1/64 of the FP32 rate)
+    // that costs a warp instruction's full time however few lanes are active.  So the pair
+    // solved at level k (sweep position v = s-1-k) is kept in double-float in the rhs ring,
+    // free during this sweep, and every RB levels all lanes of the group convert and store
+    // the rows it holds: rows v of the left side, 2s-1-v of the right.
+    float2(*xb)[C::RB] = reinterpret_cast<float2(*)[C::RB]>(sm.rrhs);
+    auto flush = [&](int base, int cnt) {  // positions base .. base+cnt-1 of both sides
+      __syncwarp();
+      if (ln.live) {
+#pragma unroll
+        for (int e = u; e < 2 * C::RB; e += C::GS) {
+          const int side = e / C::RB, i = e % C::RB;
+          if (i < cnt) {
+            // the sign and finiteness of hi + lo are those of hi (|lo| <= ulp(hi) / 2)
+            const df xv = f2df(xb[side][i]);
+            const int row = side ? 2 * s - 1 - (base + i) : base + i;
+            if (!isfinite(xv.hi) && flag == 0) flag = EHL_INFO_NONFINITE;
+            const double dv = (p.mode == 1 && !(xv.hi > 0.f)) ? 0.0 : A::to_double(xv);
+            if (real && row < n) p.x[row] = dv;
+          }
+        }
+      }
+      __syncwarp();
+    };
+    auto keep = [&](int k, int dk, df xv) {  // after the level's pair is known (dk == 0: solved here)
+      const int v = s - 1 - k;
+      if (dk == 0 && ln.live) xb[sg][v & (C::RB - 1)] = df2f(xv);
+      if ((v & (C::RB - 1)) == C::RB - 1) flush(v - (C::RB - 1), C::RB);
     };
     // terms of the pair (x_p, x_q) of level k in level k - d (columns (left, d) and (right, d))
     auto push = [&](int k, int d, df xp, df xq) {
@@ -626,13 +647,8 @@ struct P4 {
       df xv = df_zero();
       if (d == 0) xv = f2df(sm.xo[outer_index(sg, k, s)]);
       const df xp = shfl_df(xv, ln.gbase + pj), xq = shfl_df(xv, ln.gbase + C::W + pj);
-      if (d == 0) {
-        if (pend_row >= 0) store_x(pend_x, pend_row);
-        pend_x = xv;
-        pend_row = sg ? s + k : s - 1 - k;
-      } else if (k - d >= 0 && k - d < sf) {
-        push(k, d, xp, xq);
-      }
+      if (d != 0 && k - d >= 0 && k - d < sf) push(k, d, xp, xq);
+      keep(k, d, xv);
       pj = (pj == 0) ? B : pj - 1;
       d = (d == 0) ? B : d - 1;
     }
@@ -653,19 +669,12 @@ struct P4 {
         acc = df_zero();
       }
       const df xp = shfl_df(xv, ln.gbase + pj), xq = shfl_df(xv, ln.gbase + C::W + pj);
-      if (d == 0) {
-        // the float64 conversion and store of the previous level run here, off
-        // the path that the next level waits on
-        if (pend_row >= 0) store_x(pend_x, pend_row);
-        pend_x = xv;
-        pend_row = sg ? s + k : s - 1 - k;
-      } else if (k - d >= 0) {
-        push(k, d, xp, xq);
-      }
+      if (d != 0 && k - d >= 0) push(k, d, xp, xq);
+      keep(k, d, xv);
       pj = (pj == 0) ? B : pj - 1;
       d = (d == 0) ? B : d - 1;
     }
-    if (pend_row >= 0) store_x(pend_x, pend_row);
+    if (((s - 1) & (C::RB - 1)) != C::RB - 1) flush((s - 1) & ~(C::RB - 1), ((s - 1) & (C::RB - 1)) + 1);
     cpa_wait<0>();
     __threadfence_block();
     __syncwarp();
