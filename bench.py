@@ -140,6 +140,25 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(vals, world, device):
+    """Each value's maximum over all ranks: a job's time is that of its slowest rank.
+
+    None (a leg that did not run) stays None; the same legs run on every rank.
+    """
+    if world <= 1:
+        return list(vals)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([-1.0 if v is None else float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [None if v is None else float(m) for v, m in zip(vals, t.tolist())]
+
+
+def job_rate(world, units_per_rank, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time (ms)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def ehl_params(ops):
     return ops.default_params(1, nx=EHL["N"], M=EHL["M"], L=EHL["L"], limiter=EHL["limiter"], halfband=EHL["beta"],
                               method=1, tol=EHL["tol"], max_iter=60, krylov_dim=40)
@@ -210,15 +229,7 @@ def run_ours(args):
     ta = [e[0].elapsed_time(e[1]) for e in ev]
     tb = [e[1].elapsed_time(e[2]) for e in ev]
     ms_a, ms_b = sum(ta) / len(ta), sum(tb) / len(tb)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_a, ms_b], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_a, ms_b = float(t[0]), float(t[1])
-    ms = ms_a + ms_b
     nbytes = paqif_bytes(n_sys, PAQIF_N, PAQIF_BETA)
-    gbs = nbytes / (ms_a * 1e-3) / 1e9
-    hbm, src = peaks()
     ehl_ok, ehl_iters, ehl_res = None, None, None
     if ctx is not None:
         ehl_ok = int(sol["code"]) == 0
@@ -234,6 +245,7 @@ def run_ours(args):
         pm = ehl_params(ops)
         pm.precision = 2
         ctx_m = ops.Context(pm, n_inst=B)
+        barrier()
         ms_m, out_m = _timed(torch, lambda: ctx_m.solve(check=False), reps=2)
         _, Hm, _ = ctx_m.residual(out_m[0], out_m[1])
         _, Hp, _ = ctx.residual(sol["P"], sol["H0"])
@@ -242,10 +254,12 @@ def run_ours(args):
                               "emulation requested; cuBLAS runs SIMT SGEMM kernels for these shapes, "
                               "tensor pipe idle) and float32 PAQIF preconditioner sweeps; residual, line "
                               "search and update in float64",
-                 "value": round(world * B / (ms_m * 1e-3), 3), "unit": "converged solves/s", "ms": round(ms_m, 3),
+                 "value": None, "unit": "converged solves/s", "ms": None,
                  "all_converged": int(out_m[4]) == 0, "max_final_residual": float(rs_m.max()),
                  "H_rel_err_vs_plain": float((Hm - Hp).abs().max() / Hp.abs().max())}
         del ctx_m
+    else:
+        ms_m = None
     # end to end through the public API with pinned host buffers, copies inside the timed region
     e2e_b = None
     if ctx is not None:
@@ -254,6 +268,8 @@ def run_ours(args):
         it_p = torch.empty(B, dtype=torch.int32).pin_memory()
         res_p = torch.empty((B, 2), dtype=torch.float64).pin_memory()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
             P, H0, iters, res, _ = ctx.solve(check=False)
@@ -269,6 +285,8 @@ def run_ours(args):
     x_p = torch.empty(rhs_p.shape, dtype=torch.float64).pin_memory()
     band_d, rhs_d = torch.empty_like(band), torch.empty_like(rhs)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
         band_d.copy_(band_p, non_blocking=True)
@@ -279,9 +297,17 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_a = e0.elapsed_time(e1) / args.steps
 
+    # every timed figure is the slowest rank's (the collective runs on all ranks)
+    ms_a, ms_b, ms_m, e2e_a, e2e_b = max_over_ranks([ms_a, ms_b, ms_m, e2e_a, e2e_b], world, dev)
     if rank != 0:
         return None
-    solves = world * B / (ms_b * 1e-3) if B > 0 else None
+    ms = ms_a + ms_b
+    gbs = nbytes / (ms_a * 1e-3) / 1e9
+    hbm, src = peaks()
+    if mixed is not None:
+        mixed["value"] = round(job_rate(world, B, ms_m), 3)
+        mixed["ms"] = round(ms_m, 3)
+    solves = job_rate(world, B, ms_b) if B > 0 else None
     line = {
         "metric": METRIC,
         "value": round(solves, 3) if solves is not None else None,
@@ -311,9 +337,9 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "traffic": paqif_traffic(),
                      "kernel": "paqif4_kernel<4> (leg A)", "peak_source": src},
-        "e2e": {"value": round(world * B / (e2e_b * 1e-3), 3) if e2e_b else None, "unit": "converged solves/s",
+        "e2e": {"value": round(job_rate(world, B, e2e_b), 3) if e2e_b else None, "unit": "converged solves/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": B * (EHL["N"] + 1 + 2) * 8 + B * 4,
-                "paqif_gbs": round(world * nbytes / (e2e_a * 1e-3) / 1e9, 2),
+                "paqif_gbs": round(job_rate(world, nbytes, e2e_a) / 1e9, 2),
                 "paqif_h2d_bytes_per_step": band_h.nbytes + rhs_h.nbytes, "paqif_d2h_bytes_per_step": rhs_h.nbytes},
         "gpu_launches": launches,
         "clocks": clk.summary(),
