@@ -230,12 +230,13 @@ def run_ours(args):
     tb = [e[1].elapsed_time(e[2]) for e in ev]
     ms_a, ms_b = sum(ta) / len(ta), sum(tb) / len(tb)
     nbytes = paqif_bytes(n_sys, PAQIF_N, PAQIF_BETA)
-    ehl_ok, ehl_iters, ehl_res = None, None, None
+    ehl_ok, ehl_iters, ehl_res, ehl_iter_sum = None, None, None, None
     if ctx is not None:
         ehl_ok = int(sol["code"]) == 0
         it = sol["iters"].cpu().numpy()
         rs = sol["res"].cpu().numpy()
         ehl_iters = [int(it.min()), int(it.max())]
+        ehl_iter_sum = int(it.sum())
         ehl_res = float(np.max(np.abs(rs)))
 
     # the same batch with the Krylov products as one float32 GEMM per Krylov step (the residual
@@ -325,7 +326,9 @@ def run_ours(args):
             "workload": "high-load line contact: batch of converged solves N=1025, M=200, L=10, van Leer, "
                         "beta=8, tol 1e-8, plus the standalone PAQIF batch (4096 x n=1024, beta=4, mode 1)",
             "ehl_batch": B, "ehl_N": EHL["N"], "ehl_M": EHL["M"], "ehl_L": EHL["L"], "ehl_beta": EHL["beta"],
-            "ehl_ms": round(ms_b, 3), "ehl_newton_iters_min_max": ehl_iters, "ehl_max_final_residual": ehl_res,
+            "ehl_ms": round(ms_b, 3), "ehl_newton_iters_min_max": ehl_iters,
+            "ehl_newton_iters_per_s": round(job_rate(world, ehl_iter_sum, ms_b), 1) if ehl_iter_sum else None,
+            "ehl_max_final_residual": ehl_res,
             "ehl_all_converged": ehl_ok,
             "paqif_n_sys": n_sys, "paqif_n": PAQIF_N, "paqif_beta": PAQIF_BETA, "paqif_mode": PAQIF_MODE,
             "paqif_parity_ok": paqif_ok,

@@ -121,7 +121,7 @@ def test_paper_band_jacobian_matches_oracle(c1_ref, limiter, beta):
         ref, ract = lr.jacobian_band(pb, P, H0, beta)
         assert np.array_equal(act, ract)
         # the distributed entries J_f(c) - w (J_f(c-1) + J_f(c+1)) cancel terms as large as the
-        # frozen row itself: judge the rounding against the frozen row's magnitude
+        # frozen row itself: measure the rounding against the frozen row's magnitude
         Jf = lr.jacobian_frozen(pb, P, H0)
         mag = (1 + 2 * pb.dist_weight) * np.max(np.abs(Jf), axis=1, keepdims=True)
         cond = limiter_conditioning(pb, P, H0)[:, None]
