@@ -17,16 +17,23 @@ the partitioned method have a reference of their own:
   (Step 3); the reduced system of order 2 beta r for the first and last beta
   unknowns of every block in the paper's form, Z0's outer rows plus W0^-1's
   outer block times the coupling blocks L_-, L_+ (Step 4); the interiors from
-  Z0 U_M = Y_M - Z0[M, outer] U_outer (Step 6).  The reduced system is solved
-  directly (numpy LU), not through the normal equations of Step 4, and the
-  projection of Steps 5 and 7 is applied once after the full solve (the
-  readings of the paper the GPU path takes).
+  Z0 U_M = Y_M - Z0[M, outer] U_outer (Step 6).  By default the reduced system
+  is solved directly (numpy LU), not through the normal equations of Step 4,
+  and the projection of Steps 5 and 7 is applied once after the full solve
+  (the readings of the paper the GPU path takes).  The paper's own forms are
+  options: ``reduced="normal"`` forms R_d^T R_d U_d = R_d^T F_d and solves it
+  by Cholesky (Step 4), ``projection="steps"`` projects the outer unknowns
+  before the interiors are solved from them (Step 5) and the interiors after
+  (Step 7).
 
 Dense and O(n^3): small sizes only.  Pins (tests/test_oracle_aqif.py): W0 Z0
 reproduces the matrix; W0 has unit diagonal and the zero pattern of
 Sec. 2.2.1; Z0's rows have the zero pattern the middle-out order implies;
 every solve matches LU with partial pivoting; the reduced system's solution
-is the LU solution at the blocks' outer rows.
+is the LU solution at the blocks' outer rows; the normal equations give the
+same solution (to their squared conditioning); the stepwise projection equals
+the projection after the solve when the outer unknowns are nonnegative, and
+otherwise depends on r.
 """
 import numpy as np
 
@@ -79,14 +86,20 @@ def aqif_solve(W, Z, f):
     return u
 
 
-def paqif_partitioned(A, f, beta, r, mode=0, return_reduced=False):
+def paqif_partitioned(A, f, beta, r, mode=0, return_reduced=False, reduced="lu", projection="after"):
     """The partitioned PAQIF of Sec. 2.2.4 on a dense banded ``A`` (half-band ``beta``).
 
     ``r`` blocks of equal even order ``n / r >= 2 beta + 2``.  mode 0 returns
-    U, mode 1 ``max(0, U)`` (the projection after the full solve).  With
-    ``return_reduced`` also the reduced system's solution, ordered
-    ``[U_F^(1), U_L^(1), U_F^(2), ...]``.
+    U, mode 1 ``max(0, U)``.  ``reduced``: "lu" solves the reduced system
+    R_d U_d = F_d directly, "normal" through its normal equations by Cholesky
+    (Step 4 as printed).  ``projection`` (mode 1): "after" projects the full
+    solution once, "steps" projects U_F, U_L (Step 5), solves the interiors
+    from the projected values (Step 6) and projects them (Step 7).  With
+    ``return_reduced`` also the reduced system's solution before any
+    projection, ordered ``[U_F^(1), U_L^(1), U_F^(2), ...]``.
     """
+    if reduced not in ("lu", "normal") or projection not in ("after", "steps"):
+        raise ValueError("reduced is 'lu' or 'normal', projection 'after' or 'steps'")
     A = np.asarray(A, dtype=np.float64)
     f = np.asarray(f, dtype=np.float64)
     n = A.shape[0]
@@ -131,15 +144,21 @@ def paqif_partitioned(A, f, beta, r, mode=0, return_reduced=False):
             C = np.zeros((2 * b, b))
             C[b:, :] = Lp
             R[rows, 2 * b * (m + 1):2 * b * (m + 1) + b] += bm["Wout"] @ C
-    uO = np.linalg.solve(R, g)
+    if reduced == "lu":
+        uO = np.linalg.solve(R, g)
+    else:  # R_d^T R_d U_d = R_d^T F_d, symmetric positive definite: Cholesky without pivoting
+        C = np.linalg.cholesky(R.T @ R)
+        uO = np.linalg.solve(C.T, np.linalg.solve(C, R.T @ g))
+    stepwise = mode == 1 and projection == "steps"
+    uO_used = np.maximum(uO, 0.0) if stepwise else uO  # Step 5
     # Step 6: the interiors, Z0[M, M] u_M = y_M - Z0[M, O] u_O
     u = np.zeros(n)
     for m in range(r):
         bm = blocks[m]
-        uo = uO[2 * b * m:2 * b * (m + 1)]
+        uo = uO_used[2 * b * m:2 * b * (m + 1)]
         um = np.linalg.solve(bm["Z"][np.ix_(M, M)], bm["y"][M] - bm["Z"][np.ix_(M, O)] @ uo)
         u[m * nb + np.array(O)] = uo
         u[m * nb + np.array(M)] = um
-    if mode == 1:  # Steps 5 and 7, after the full solve
+    if mode == 1:  # Step 7 (with Step 5 above), or the projection of the full solution
         u = np.maximum(u, 0.0)
     return (u, uO) if return_reduced else u

@@ -74,3 +74,60 @@ def test_partitioned_needs_the_coupling_blocks():
     ub = aq.paqif_partitioned(Ab, f, beta, r)
     assert np.max(np.abs(ub - np.linalg.solve(A, f))) > 1e-6
     assert np.max(np.abs(ub - np.linalg.solve(Ab, f))) <= 1e-12 * np.max(np.abs(ub))
+
+
+@pytest.mark.parametrize("beta", [1, 2, 4])
+@pytest.mark.parametrize("r", [2, 4])
+def test_normal_equations_of_step_4_give_the_same_solution(beta, r):
+    """Step 4 as printed (R_d^T R_d U_d = R_d^T F_d by Cholesky) and the direct solve the GPU
+    path takes (reading A18) agree on well-conditioned systems."""
+    n = 48 if beta < 4 else 80
+    A, f = dense(n, beta, 300 * r + beta)
+    ref = np.linalg.solve(A, f)
+    u_n, uO_n = aq.paqif_partitioned(A, f, beta, r, return_reduced=True, reduced="normal")
+    u_d, uO_d = aq.paqif_partitioned(A, f, beta, r, return_reduced=True)
+    assert np.max(np.abs(u_n - ref)) <= 1e-11 * np.max(np.abs(ref))
+    assert np.max(np.abs(uO_n - uO_d)) <= 1e-11 * np.max(np.abs(uO_d))
+
+
+def test_normal_equations_square_the_conditioning():
+    """On the 1-D Laplacian shifted to within 0.1 % of its smallest eigenvalue (condition number
+    about 1e6) the direct solve keeps about 11 digits and the normal equations about 8: they
+    square the reduced system's conditioning (why the GPU path eliminates it instead, reading
+    A18)."""
+    beta, r, n = 1, 4, 48
+    lmin = 2.0 - 2.0 * np.cos(np.pi / (n + 1))
+    A = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1) - lmin * (1.0 - 1e-3) * np.eye(n)
+    f = np.random.default_rng(3).uniform(-1.0, 1.0, n)
+    ref = np.linalg.solve(A, f)
+    err_d = np.max(np.abs(aq.paqif_partitioned(A, f, beta, r) - ref)) / np.max(np.abs(ref))
+    err_n = np.max(np.abs(aq.paqif_partitioned(A, f, beta, r, reduced="normal") - ref)) / np.max(np.abs(ref))
+    assert err_d <= 1e-9
+    assert err_n > 100 * err_d
+
+
+def test_stepwise_projection_equals_projection_after_for_a_positive_solution():
+    """Steps 5-7 (project U_F, U_L, solve the interiors from them, project) and the projection
+    after the full solve (reading A17) coincide when the outer unknowns are nonnegative."""
+    beta, n = 2, 48
+    A, _ = dense(n, beta, 21)
+    xt = np.random.default_rng(21).uniform(0.5, 1.5, n)
+    f = A @ xt
+    for r in (1, 2, 4):
+        us = aq.paqif_partitioned(A, f, beta, r, mode=1, projection="steps")
+        ua = aq.paqif_partitioned(A, f, beta, r, mode=1)
+        assert np.max(np.abs(us - xt)) <= 1e-12 and np.max(np.abs(ua - xt)) <= 1e-12
+
+
+def test_stepwise_projection_depends_on_the_partition_count():
+    """With negative outer unknowns the stepwise projection feeds clipped values into the
+    interior solves, so its result changes with r; the projection after the solve does not."""
+    beta, n = 2, 48
+    A, f = dense(n, beta, 23)
+    u = np.linalg.solve(A, f)
+    assert np.min(u) < 0 and np.max(u) > 0
+    after = [aq.paqif_partitioned(A, f, beta, r, mode=1) for r in (2, 4)]
+    steps = [aq.paqif_partitioned(A, f, beta, r, mode=1, projection="steps") for r in (2, 4)]
+    assert np.max(np.abs(after[0] - after[1])) <= 1e-12 * np.max(np.abs(u))
+    assert np.array_equal(after[0], np.maximum(aq.paqif_partitioned(A, f, beta, 2), 0.0))
+    assert np.max(np.abs(steps[0] - steps[1])) > 1e-6
