@@ -349,7 +349,7 @@ def run_ours(args):
         "wall_s": round(wall, 3),
     }
     if world == 1 and not args.no_configs:
-        line["configs"] = config_legs(ops, inputs, torch, dev)
+        line["configs"] = config_legs(ops, inputs, torch, dev, paqif=(band, rhs))
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(band_h, rhs_h, budget_s=args.cpu_seconds)
     return line
@@ -378,10 +378,19 @@ def _timed(torch, fn, reps=1, warm=1):
     return best, out
 
 
-def config_legs(ops, inputs, torch, dev):
+def _band_matvec(torch, band, x, beta):
+    """y_i = sum_q band[i, q] x[i - beta + q] (zero outside the system), for checking results."""
+    xp = torch.nn.functional.pad(x, (beta, beta))
+    return (band * xp.unfold(1, 2 * beta + 1, 1)).sum(dim=2)
+
+
+def config_legs(ops, inputs, torch, dev, paqif=None):
     """One measurement per remaining configuration, outside the K timed steps:
-    C1 (the paper's load, both methods), C3 (ragged batch of 512), C4 (point
-    contact 257^2) and C5 (adjoint gradients of H_min, batch of 64)."""
+    C1 (the paper's load, both methods), C2a (the high load's largest line grid),
+    C2b in mode 2 (the standalone PAQIF batch as an LCP; ``paqif`` = its band and
+    rhs on the device), C3 (ragged batch of 512), C4 (point contact 257^2) and C5
+    (adjoint gradients of H_min, batch of 64).  C2a and C2b record an error string
+    instead of raising."""
     res = {}
 
     def summary(it, rs, code, tol):
@@ -401,6 +410,38 @@ def config_legs(ops, inputs, torch, dev):
                  solves_per_s=round(1e3 / ms, 2))
         d.update(summary(out[2], out[3], out[4], 1e-8))
         res[f"C1_method{method}"] = d
+    # C2a: N = 4097, M = 200, L = 10, van Leer, beta 8, one instance
+    try:
+        p = ops.default_params(1, nx=4097, M=200.0, L=10.0, limiter=1, halfband=8, method=1, tol=1e-8, max_iter=80)
+        ctx = ops.Context(p)
+        ms, out = _timed(torch, lambda: ctx.solve(check=False), reps=2)
+        d = dict(workload="line N=4097, M=200, L=10, van Leer, beta=8, 1 instance, tol 1e-8", ms=round(ms, 2),
+                 solves_per_s=round(1e3 / ms, 2))
+        d.update(summary(out[2], out[3], out[4], 1e-8))
+        d["newton_iters_per_s"] = round(d["newton_iters_min_max"][1] * 1e3 / ms, 1)
+        res["C2a_4097"] = d
+        del ctx
+    except Exception as e:  # a failed leg leaves the others and the main line intact
+        res["C2a_4097"] = {"error": f"{type(e).__name__}: {e}"}
+    # C2b in mode 2: the standalone batch as an LCP (x >= 0, A x - b >= 0, complementary)
+    if paqif is not None:
+        try:
+            band, rhs = paqif
+            n_sys, n = rhs.shape
+            ws2 = torch.empty(ops.paqif_workspace_size(n_sys, n, PAQIF_BETA, 2), dtype=torch.uint8, device=dev)
+            x2 = torch.empty_like(rhs)
+            ms, (xs, its, info) = _timed(torch, lambda: ops.paqif_solve(band, rhs, PAQIF_BETA, 2, x=x2, workspace=ws2),
+                                         reps=3)
+            w = _band_matvec(torch, band, xs, PAQIF_BETA) - rhs
+            viol = max(float((-xs).clamp(min=0).max()), float((-w).clamp(min=0).max()), float((xs * w).abs().max()))
+            res["C2b_mode2"] = dict(
+                workload=f"standalone PAQIF batch as an LCP ({n_sys} x n={n}, beta={PAQIF_BETA}, mode 2)",
+                ms=round(ms, 4), gbs=round(paqif_bytes(n_sys, n, PAQIF_BETA) / (ms * 1e-3) / 1e9, 2),
+                paqif_solves_per_system_min_max=[int(its.min()), int(its.max())],
+                info_all_zero=bool((info == 0).all().item()),
+                lcp_violation_rel=viol / float(rhs.abs().max()))
+        except Exception as e:
+            res["C2b_mode2"] = {"error": f"{type(e).__name__}: {e}"}
     # C3: 512 instances, M log-uniform [10, 1000], L uniform [5, 20], N from {257, ..., 2049}
     per = inputs.batched_line_params(512, seed=1)
     Href = None
