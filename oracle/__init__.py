@@ -9,6 +9,8 @@ Modules
 -------
 paqif_ref     banded (projected) solves: dense LU, projected Gauss-Seidel,
               brute-force active-set enumeration (Sec. 2.1-2.2, Sec. 3.2).
+aqif_ref      the AQIF factorization L0 = W0 Z0, its two sweeps and the
+              partitioned method's Steps 1-7 on dense matrices (Sec. 2.2.1-2.2.4).
 kernels_ref   closed-form deformation kernels for piecewise-constant pressure
               (Sec. 3.3.1, line and point contact).
 material_ref  Moes parameter conversion, Roelands viscosity, Dowson-Higginson
