@@ -31,7 +31,7 @@ extern "C" {
 typedef enum {
   EHL_OK = 0,
   EHL_EINVAL = 1,      /* an argument is out of range or a required pointer is NULL */
-  EHL_ENOMEM = 2,      /* device memory could not be allocated                       */
+  EHL_ENOMEM = 2,      /* device or host memory (or a host thread) not available      */
   EHL_ECUDA = 3,       /* a CUDA runtime call failed (launch, copy, ...)             */
   EHL_ENOCONV = 4,     /* an iteration did not converge within its limit             */
   EHL_ENONFINITE = 5,  /* a NaN or Inf appeared                                      */

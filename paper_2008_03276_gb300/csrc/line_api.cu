@@ -410,7 +410,7 @@ static ehl_status create_point(const ehl_params* p, int n_inst, const ehl_params
   return EHL_OK;
 }
 
-extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_params* per_inst, void* stream,
+static ehl_status ehl_create_impl(const ehl_params* p, int n_inst, const ehl_params* per_inst, void* stream,
                                  ehl_ctx** out) {
   if (!p || !out || n_inst < 1 || n_inst > 65535 || !params_ok(*p)) return EHL_EINVAL;
   if (p->dim == 2) {
@@ -647,7 +647,7 @@ static ehl_status pt_solve_api(ehl_ctx* ctx, double* P, double* H0, const double
   return nonfinite ? EHL_ENONFINITE : (noconv ? EHL_ENOCONV : EHL_OK);
 }
 
-extern "C" ehl_status ehl_residual(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, double* R,
+static ehl_status ehl_residual_impl(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, double* R,
                                    double* H, double* comp_res) {
   if (!ctx || !P || !H0 || !R) return EHL_EINVAL;
   if (ctx->pt) return pt_residual_api(ctx, P, H0, rough, R, H, comp_res);
@@ -663,7 +663,7 @@ extern "C" ehl_status ehl_residual(ehl_ctx* ctx, const double* P, const double* 
   return cuda_status(e);
 }
 
-extern "C" ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
+static ehl_status ehl_jacobian_band_impl(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
                                         int kind, double* band, uint8_t* active) {
   if (!ctx || !P || !H0 || !band || !active || (kind != 0 && kind != 1)) return EHL_EINVAL;
   if (ctx->pt) {
@@ -692,7 +692,7 @@ extern "C" ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const dou
   return cuda_status(e);
 }
 
-extern "C" ehl_status ehl_jacobian_apply(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
+static ehl_status ehl_jacobian_apply_impl(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
                                          const double* v, const double* v_h0, double* out) {
   if (!ctx || !P || !H0 || !v || !v_h0 || !out) return EHL_EINVAL;
   if (ctx->pt) return cuda_status(pt_jacobian_apply(ctx->pt, P, H0, rough, v, v_h0, out));
@@ -841,7 +841,7 @@ static cudaError_t solve_bucket(ehl_ctx* ctx, Bucket* b, const double* P, const 
   return e;
 }
 
-extern "C" ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const double* rough, int init, int* iters,
+static ehl_status ehl_solve_impl(ehl_ctx* ctx, double* P, double* H0, const double* rough, int init, int* iters,
                                 double* final_res) {
   if (!ctx || !P || !H0 || (init != 0 && init != 1)) return EHL_EINVAL;
   if (ctx->pt) return pt_solve_api(ctx, P, H0, rough, init, iters, final_res);
@@ -856,12 +856,27 @@ extern "C" ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const doubl
     int dev = 0;
     cudaGetDevice(&dev);
     std::vector<std::thread> th;
-    for (size_t q = 0; q < nb; ++q)
-      th.emplace_back([&, q, dev]() {
-        cudaSetDevice(dev);
-        errs[q] = solve_bucket(ctx, ctx->buckets[q], P, H0, rough, init, dones[q]);
-      });
+    th.reserve(nb);
+    bool spawned = true;
+    for (size_t q = 0; q < nb && spawned; ++q) {
+      try {
+        th.emplace_back([&, q, dev]() {
+          cudaSetDevice(dev);
+          try {
+            errs[q] = solve_bucket(ctx, ctx->buckets[q], P, H0, rough, init, dones[q]);
+          } catch (...) {  // a host allocation failed inside the bucket's solve
+            errs[q] = cudaErrorMemoryAllocation;
+          }
+        });
+      } catch (...) {  // no thread for this bucket: the started ones finish, then the call fails
+        spawned = false;
+      }
+    }
     for (auto& t : th) t.join();
+    if (!spawned) {
+      join(ctx);
+      return EHL_ENOMEM;
+    }
   }
   for (size_t q = 0; q < nb; ++q) {
     Bucket* b = ctx->buckets[q];
@@ -885,7 +900,7 @@ extern "C" ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const doubl
   return nonfinite ? EHL_ENONFINITE : (noconv ? EHL_ENOCONV : EHL_OK);
 }
 
-extern "C" ehl_status ehl_adjoint(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
+static ehl_status ehl_adjoint_impl(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
                                   const double* gP, const double* gH, const double* gH0, double* grad_rough,
                                   double* grad_ML, double* relres, double tol, int max_cycles) {
   if (!ctx || !P || !H0 || !(tol > 0.0) || max_cycles < 1 || max_cycles > 1000) return EHL_EINVAL;
@@ -944,3 +959,46 @@ extern "C" ehl_status ehl_adjoint(ehl_ctx* ctx, const double* P, const double* H
   }
   return nonfinite ? EHL_ENONFINITE : (noconv ? EHL_ENOCONV : EHL_OK);
 }
+
+// ---------------------------------------------------------------- C ABI
+// No C++ exception leaves an entry point: a failed host allocation (or host
+// thread) is reported as EHL_ENOMEM.
+#define EHL_NOTHROW(call)           \
+  try {                             \
+    return call;                    \
+  } catch (...) {                   \
+    return EHL_ENOMEM;              \
+  }
+
+extern "C" ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_params* per_inst, void* stream,
+                                 ehl_ctx** out) {
+  EHL_NOTHROW(ehl_create_impl(p, n_inst, per_inst, stream, out))
+}
+
+extern "C" ehl_status ehl_residual(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, double* R,
+                                   double* H, double* comp_res) {
+  EHL_NOTHROW(ehl_residual_impl(ctx, P, H0, rough, R, H, comp_res))
+}
+
+extern "C" ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
+                                        int kind, double* band, uint8_t* active) {
+  EHL_NOTHROW(ehl_jacobian_band_impl(ctx, P, H0, rough, kind, band, active))
+}
+
+extern "C" ehl_status ehl_jacobian_apply(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
+                                         const double* v, const double* v_h0, double* out) {
+  EHL_NOTHROW(ehl_jacobian_apply_impl(ctx, P, H0, rough, v, v_h0, out))
+}
+
+extern "C" ehl_status ehl_solve(ehl_ctx* ctx, double* P, double* H0, const double* rough, int init, int* iters,
+                                double* final_res) {
+  EHL_NOTHROW(ehl_solve_impl(ctx, P, H0, rough, init, iters, final_res))
+}
+
+extern "C" ehl_status ehl_adjoint(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
+                                  const double* gP, const double* gH, const double* gH0, double* grad_rough,
+                                  double* grad_ML, double* relres, double tol, int max_cycles) {
+  EHL_NOTHROW(ehl_adjoint_impl(ctx, P, H0, rough, gP, gH, gH0, grad_rough, grad_ML, relres, tol, max_cycles))
+}
+
+#undef EHL_NOTHROW

@@ -87,3 +87,16 @@ def test_create_rejects_bad_params_on_host(field, value):
     h = ctypes.c_void_p(0)
     assert lib.ehl_create(ctypes.byref(p), 1, None, None, ctypes.byref(h)) == _ffi.EHL_EINVAL
     assert lib.ehl_create(None, 1, None, None, ctypes.byref(h)) == _ffi.EHL_EINVAL
+
+
+def test_context_entry_points_reject_a_null_context():
+    """Every context call checks its handle on the host and returns a status (no exception,
+    no CUDA call)."""
+    lib = _ffi.load()
+    z = ctypes.c_void_p(0)
+    assert lib.ehl_residual(z, z, z, z, z, z, z) == _ffi.EHL_EINVAL
+    assert lib.ehl_jacobian_band(z, z, z, z, 1, z, z) == _ffi.EHL_EINVAL
+    assert lib.ehl_jacobian_apply(z, z, z, z, z, z, z) == _ffi.EHL_EINVAL
+    assert lib.ehl_solve(z, z, z, z, 0, z, z) == _ffi.EHL_EINVAL
+    assert lib.ehl_adjoint(*([z] * 10), 1e-10, 10) == _ffi.EHL_EINVAL
+    assert lib.ehl_destroy(z) == _ffi.EHL_EINVAL
