@@ -199,7 +199,8 @@ typedef struct {
                         /*   (the residual stays float64, so the converged answer does     */
                         /*   not depend on it): 0 double-float Toeplitz kernel; with one   */
                         /*   grid spacing per grid size, a float32-output GEMM of all     */
-                        /*   instances: 1 float32, 2 float32 emulated on BF16 tensor cores,*/
+                        /*   instances: 1 float32, 2 float32 with cuBLAS's BF16x9        */
+                        /*   emulation requested (cuBLAS may still choose a SIMT SGEMM),   */
                         /*   3 TF32 tensor cores, 4 BF16 tensor cores; point contact: one */
                         /*   GEMM [nx x nx ny] . [nx ny x ny] per instance from the        */
                         /*   block-Toeplitz structure of the 2-D kernel                    */
