@@ -1,0 +1,53 @@
+"""Host-side pieces of bench.py that need no GPU: the algorithmic byte count behind the
+roofline, the peak lookup with its fallback, and the parsing of the nvidia-smi clock samples
+that decide whether a measurement is kept."""
+import json
+
+import pytest
+
+import bench
+
+
+def test_paqif_algorithmic_bytes():
+    # band (2 beta + 1 doubles per row) and rhs read, x written: 369.1 MB for the standalone batch
+    assert bench.paqif_bytes(4096, 1024, 4) == 4096 * (1024 * 9 * 8 + 2 * 1024 * 8) == 369_098_752
+    assert bench.paqif_bytes(1, 7, 1) == 7 * 3 * 8 + 2 * 7 * 8
+
+
+def test_peaks_measured_then_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peaks() == (bench.FALLBACK_HBM_GBS, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6651.4}))
+    assert bench.peaks() == (6651.4, "measured")
+
+
+def _summary(lines):
+    s = bench.ClockSampler(0)  # not entered: no nvidia-smi process
+    s.out.write("".join(line + "\n" for line in lines))
+    return s.summary()
+
+
+def test_clock_summary_median_max_and_reasons():
+    lines = [
+        "0, 2070, 2070, 950.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1301.7, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    got = _summary(lines)
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"]}
+
+
+def test_clock_summary_flags_thermal_slowdown():
+    got = _summary(["0, 1500, 2070, 1400, 0x20, Not Active, Active, Not Active, Not Active"])
+    assert got["reasons"] == ["hw_thermal_slowdown"] and got["sm_mhz"] == 1500.0
+
+
+def test_clock_summary_without_samples():
+    assert _summary([])["reasons"] == ["unsampled"]
+
+
+@pytest.mark.parametrize("world,units,ms,rate", [(1, 512, 122.4, 512 / 0.1224), (4, 512, 130.0, 2048 / 0.13)])
+def test_job_rate(world, units, ms, rate):
+    assert bench.job_rate(world, units, ms) == pytest.approx(rate)
