@@ -51,3 +51,16 @@ def test_clock_summary_without_samples():
 @pytest.mark.parametrize("world,units,ms,rate", [(1, 512, 122.4, 512 / 0.1224), (4, 512, 130.0, 2048 / 0.13)])
 def test_job_rate(world, units, ms, rate):
     assert bench.job_rate(world, units, ms) == pytest.approx(rate)
+
+
+def test_cpu_baseline_runs_on_a_spawned_pool():
+    """The oracle leg of the bench: one single-threaded worker per core, whole instances each;
+    a short budget still runs one round of each leg and reports the workers as its cores."""
+    import os
+
+    from paper_2008_03276_gb300 import inputs
+
+    band, rhs = inputs.dd_band_systems(2 * (os.cpu_count() or 1), 1024, 4, seed=0)
+    out = bench.cpu_baseline(band, rhs, budget_s=0.5)
+    assert out["kind"] == "oracle" and out["cores"] == (os.cpu_count() or 1)
+    assert out["value"] > 0 and "single-threaded worker processes" in out["sample"]
