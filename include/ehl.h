@@ -136,6 +136,17 @@ ehl_status ehl_paqif_solve_partitioned(int n_sys, int n, int beta, int partition
                                        int* iters, int* info, void* workspace, size_t workspace_bytes,
                                        void* stream);
 
+/* The partition count a batch is solved with (host only, no CUDA call).
+ *   partitions  0: the automatic choice of ehl_paqif_solve (among the
+ *               admissible r whose n_sys r lane groups fit in two rounds of
+ *               the resident groups of the GPU, the one with the shortest
+ *               chain per group: its sweep levels n_p/2 - beta plus 2 beta r
+ *               for the reduced system; on a tie the larger r if it fits in
+ *               one round); r >= 1: r itself if admissible
+ *   *r          output
+ * Returns EHL_EINVAL for bad sizes, a NULL r or an inadmissible r. */
+ehl_status ehl_paqif_partitions(int n_sys, int n, int beta, int partitions, int* r);
+
 /* ------------------------------------------------------------------------
  * EHL problem: context, residual, band Jacobian, solve
  * ------------------------------------------------------------------------

@@ -54,6 +54,14 @@ extern "C" ehl_status ehl_paqif_workspace_size_partitioned(int n_sys, int n, int
   return EHL_OK;
 }
 
+extern "C" ehl_status ehl_paqif_partitions(int n_sys, int n, int beta, int partitions, int* r) {
+  if (!r || !paqif_args_ok(n_sys, n, beta, 0) || partitions < 0) return EHL_EINVAL;
+  const int got = paqif_parts(n_sys, n, beta, partitions);
+  if (got < 1) return EHL_EINVAL;
+  *r = got;
+  return EHL_OK;
+}
+
 extern "C" ehl_status ehl_paqif_workspace_size(int n_sys, int n, int beta, int mode, size_t* bytes) {
   return ehl_paqif_workspace_size_partitioned(n_sys, n, beta, 0, mode, bytes);
 }

@@ -33,6 +33,14 @@ def kernel_launches():
     return int(_ffi.load().ehl_kernel_launches())
 
 
+def paqif_partitions(n_sys, n, beta, partitions=0):
+    """The blocks per system a batch is solved with: the library's choice for ``partitions`` = 0."""
+    lib = _ffi.load()
+    out = ctypes.c_int(0)
+    _ffi.check(lib.ehl_paqif_partitions(n_sys, n, beta, partitions, ctypes.byref(out)), "ehl_paqif_partitions")
+    return out.value
+
+
 def paqif_workspace_size(n_sys, n, beta, mode, partitions=0):
     lib = _ffi.load()
     out = ctypes.c_size_t(0)

@@ -100,3 +100,29 @@ def test_context_entry_points_reject_a_null_context():
     assert lib.ehl_solve(z, z, z, z, 0, z, z) == _ffi.EHL_EINVAL
     assert lib.ehl_adjoint(*([z] * 10), 1e-10, 10) == _ffi.EHL_EINVAL
     assert lib.ehl_destroy(z) == _ffi.EHL_EINVAL
+
+
+@pytest.mark.parametrize("shape,r", [
+    ((4096, 1024, 4), 4),   # the standalone batch: chains 252+16, 167+24, 124+32 levels for r = 2, 3, 4
+    ((512, 1025, 8), 4),    # the line preconditioner: r = 4 and 8 tie at 185, and 8 x 512 groups exceed one round
+    ((1, 4097, 8), 8),      # one long system: 249 + 128 levels at r = 8 against 505 + 64 at r = 4
+    ((127, 127, 2), 4),     # x-lines of 129^2: 14 + 16 at r = 4, 11 + 20 at r = 5, 30 + 8 at r = 2
+    ((1, 8, 2), 1),         # too short to cut: a block needs 2 beta + 2 rows
+])
+def test_partition_rule_of_the_library(shape, r):
+    """The automatic partition count, by hand from the rule in include/ehl.h (lane groups per
+    CTA 12 at beta = 4, 8 at beta = 8, 20 at beta = 2; resident groups 152 SMs x CTAs per SM
+    x groups per CTA)."""
+    from paper_2008_03276_gb300 import ops
+
+    assert ops.paqif_partitions(*shape) == r
+    assert ops.paqif_partitions(*shape, partitions=r) == r
+
+
+def test_partition_rule_rejects_bad_requests():
+    lib = _ffi.load()
+    out = ctypes.c_int(0)
+    assert lib.ehl_paqif_partitions(4, 1024, 8, 3, ctypes.byref(out)) == _ffi.EHL_EINVAL  # 3 does not divide 8
+    assert lib.ehl_paqif_partitions(4, 16, 8, 2, ctypes.byref(out)) == _ffi.EHL_EINVAL   # blocks too short
+    assert lib.ehl_paqif_partitions(4, 16, 2, -1, ctypes.byref(out)) == _ffi.EHL_EINVAL
+    assert lib.ehl_paqif_partitions(4, 16, 2, 0, None) == _ffi.EHL_EINVAL
