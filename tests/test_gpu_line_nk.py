@@ -67,25 +67,6 @@ def test_high_load_newton_krylov():
     check(P[0], H0[0], pb, Pr, H0r)
 
 
-@pytest.mark.slow
-def test_high_load_batch_of_512_in_the_bench_configuration():
-    """The bench's line batch (512 instances of N = 1025, M = 200, L = 10, van Leer, band 8,
-    Krylov basis 40, the library's nested iteration and partition count for 512 systems),
-    solved to 3e-10: sampled instances match the oracle, and the 512 identical problems,
-    solved side by side, return the same solution."""
-    N, M = 1025, 200.0
-    pb = lr.LineProblem(N, M, 10.0, limiter="vanleer")
-    Pr, H0r, info = lr.solve(pb)
-    assert info["converged"]
-    P, H0, iters, res, code, dt = gpu_solve(N, M, 10.0, 1, 8, tol=3e-10, n_inst=512)
-    print(f"batch of 512: iters {iters.min()}-{iters.max()}, {dt * 1e3:.1f} ms")
-    assert code == 0
-    for k in (0, 255, 511):
-        check(P[k], H0[k], pb, Pr, H0r)
-    assert np.max(np.abs(P - P[0])) <= 1e-12 * np.max(np.abs(P[0]))
-    assert np.max(np.abs(H0 - H0[0])) <= 1e-12 * abs(H0[0])
-
-
 def test_batch_of_loads_newton_krylov():
     per = [dict(M=10.0, L=5.0), dict(M=50.0, L=10.0), dict(M=150.0, L=15.0), dict(M=400.0, L=8.0)]
     P, H0, iters, res, code, dt = gpu_solve(257, 20.0, 10.0, 0, 4, tol=1e-10, n_inst=4, per=per)

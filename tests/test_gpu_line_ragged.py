@@ -141,31 +141,3 @@ def test_ragged_paper_method_runs_per_group():
         assert it1.cpu().numpy()[0] == iters[k]
         assert np.array_equal(P[k, :n], P1.cpu().numpy()[0])
         assert H0[k] == H01.cpu().numpy()[0]
-
-
-@pytest.mark.slow
-def test_c3_full_batch_solutions_satisfy_the_oracles_problem():
-    """C3 as the bench runs it (512 instances, N from {257, 513, 1025, 2049}, M log-uniform on
-    [10, 1000], L on [5, 20], minmod, band 2, tol 1e-8): for the first and last instance of every
-    grid size the oracle's residual at the GPU's solution meets the convergence test the bench
-    counts (complementarity and force residual within 10 tol, or the rounding floor)."""
-    per = inputs.batched_line_params(512, seed=1)
-    kw = dict(limiter=0, halfband=2, method=1, tol=1e-8, max_iter=60, precision=0)
-    pp = [ops.default_params(1, nx=q["N"], M=q["M"], L=q["L"], **kw) for q in per]
-    ctx = ops.Context(pp[0], n_inst=len(pp), per_inst=pp)
-    P, H0, iters, res, code = ctx.solve(check=False)
-    assert code == 0, code
-    P, H0 = P.cpu().numpy(), H0.cpu().numpy()
-    picks = []
-    for N in (257, 513, 1025, 2049):
-        ks = [k for k, q in enumerate(per) if q["N"] == N]
-        picks += [ks[0], ks[-1]]
-    for k in picks:
-        q = per[k]
-        n = q["N"]
-        pb = lr.LineProblem(n, q["M"], q["L"], limiter="minmod")
-        assert P[k, 0] == 0.0 and P[k, n - 1] == 0.0 and np.all(P[k, n:] == 0.0)
-        rc, g = lr.comp_residual(pb, P[k, 1:n - 1], H0[k])
-        floor = lr.rounding_floor(pb, P[k, 1:n - 1], H0[k])
-        assert rc <= max(1e-7, floor) and abs(g) <= 1e-7, (k, q, rc, g, floor)
-

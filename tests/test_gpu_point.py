@@ -141,27 +141,6 @@ def test_point_solve_129_properties():
     assert np.max(np.abs(Pn - Pn[::-1, :])) <= 1e-6 * np.max(Pn)       # Y -> -Y
 
 
-@pytest.mark.slow
-def test_point_solve_257_in_the_bench_configuration():
-    """C4 as the bench runs it (257^2, M = 100, L = 10, minmod, band 2, nested from 33^2,
-    tol 1e-8, the library's Krylov basis): the oracle's residual at the GPU's solution, the
-    force balance and the Y-mirror symmetry (the dense oracle does not reach this size)."""
-    n = 257
-    p = ops.default_params(2, nx=n, ny=n, M=100.0, L=10.0, limiter=0, halfband=2, method=1, tol=1e-8,
-                           max_iter=60, coarse_min_nodes=33)
-    ctx = ops.Context(p)
-    P, H0, iters, res, code = ctx.solve(check=False)
-    print(f"257^2: code {code} iters {iters.tolist()} res {res.tolist()}")
-    assert code == 0
-    Pn, H0n = P.cpu().numpy()[0], float(H0.cpu()[0])
-    pb = pr.PointProblem(n, n, 100.0, 10.0, limiter="minmod")
-    Pint = Pn.T[1:-1, 1:-1].ravel()
-    R = pr.residual(pb, Pint, H0n)       # the oracle's residual at the GPU's solution
-    assert np.max(np.abs(np.minimum(Pint, R))) <= 2e-8
-    assert abs(pb.h**2 * Pint.sum() - 2 * np.pi / 3) <= 1e-8
-    assert np.max(np.abs(Pn - Pn[::-1, :])) <= 1e-6 * np.max(Pn)       # Y -> -Y
-
-
 # ---------------------------------------------------------------- point-contact adjoint
 @pytest.mark.parametrize("which", ["H_c", "P2"])
 def test_point_adjoint_matches_dense_oracle(which):
