@@ -51,9 +51,12 @@ FALLBACK_HBM_GBS = 6800.0
 # capture summarised in profiles/, valid only for the kernel sources with these
 # sha256 prefixes; any other source reports traffic = null.
 PAQIF_TRAFFIC = {("7ec492ea359502ff", "6a71297bc569ed85"): 564364800 + 309009152}
+# smsp__inst_executed.sum of the same launch and capture: the kernel is bound by instruction issue
+PAQIF_WARP_INSTRUCTIONS = {("7ec492ea359502ff", "6a71297bc569ed85"): 852480330}
+SCHEDULERS = 152 * 4  # SMs x warp schedulers per SM, one warp instruction issued per scheduler and cycle
 
 
-def paqif_traffic():
+def _paqif_source_key():
     import hashlib
 
     def h(p):
@@ -61,14 +64,33 @@ def paqif_traffic():
             return hashlib.sha256(f.read()).hexdigest()[:16]
 
     try:
-        return PAQIF_TRAFFIC.get((h("paqif4.cu"), h("df64.cuh")))
+        return h("paqif4.cu"), h("df64.cuh")
     except OSError:
         return None
+
+
+def paqif_traffic():
+    return PAQIF_TRAFFIC.get(_paqif_source_key())
+
+
+def issue_fraction(warp_instructions, ms, sm_mhz):
+    """Warp instructions over the issue slots of all schedulers during ms at sm_mhz."""
+    if not warp_instructions or not ms or not sm_mhz:
+        return None
+    return warp_instructions / (SCHEDULERS * sm_mhz * 1e6 * ms * 1e-3)
 
 
 def paqif_bytes(n_sys, n, beta):
     """Algorithmic bytes of one batched solve: band + rhs read, x written."""
     return n_sys * (n * (2 * beta + 1) * 8 + 2 * n * 8)
+
+
+def peaks_sm_mhz():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f).get("sm_max_mhz", 0.0)) or None
+    return None
 
 
 def peaks():
@@ -310,6 +332,14 @@ def run_ours(args):
         mixed["value"] = round(job_rate(world, B, ms_m), 3)
         mixed["ms"] = round(ms_m, 3)
     solves = job_rate(world, B, ms_b) if B > 0 else None
+    clocks = clk.summary()
+    winst = PAQIF_WARP_INSTRUCTIONS.get(_paqif_source_key()) if n_sys == PAQIF_NSYS else None
+    frac_issue = issue_fraction(winst, ms_a, clocks.get("sm_mhz") or peaks_sm_mhz())
+    issue = None if frac_issue is None else {
+        "warp_instructions": winst, "slots": SCHEDULERS, "sm_mhz": clocks.get("sm_mhz") or peaks_sm_mhz(),
+        "frac": round(frac_issue, 4),
+        "note": "warp instructions of the launch (ncu, keyed to the kernel source) over the issue slots of "
+                "152 SMs x 4 schedulers at the sampled SM clock during its CUDA-event time"}
     line = {
         "metric": METRIC,
         "value": round(solves, 3) if solves is not None else None,
@@ -342,13 +372,13 @@ def run_ours(args):
         "mixed_precision": mixed,
         "roofline": {"bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "traffic": paqif_traffic(),
-                     "kernel": "paqif4_kernel<4> (leg A)", "peak_source": src},
+                     "kernel": "paqif4_kernel<4> (leg A)", "peak_source": src, "issue": issue},
         "e2e": {"value": round(job_rate(world, B, e2e_b), 3) if e2e_b else None, "unit": "converged solves/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": B * (EHL["N"] + 1 + 2) * 8 + B * 4,
                 "paqif_gbs": round(job_rate(world, nbytes, e2e_a) / 1e9, 2),
                 "paqif_h2d_bytes_per_step": band_h.nbytes + rhs_h.nbytes, "paqif_d2h_bytes_per_step": rhs_h.nbytes},
         "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "wall_s": round(wall, 3),
     }
     if world == 1 and not args.no_configs:

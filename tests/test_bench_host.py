@@ -64,3 +64,11 @@ def test_cpu_baseline_runs_on_a_spawned_pool():
     out = bench.cpu_baseline(band, rhs, budget_s=0.5)
     assert out["kind"] == "oracle" and out["cores"] == (os.cpu_count() or 1)
     assert out["value"] > 0 and "single-threaded worker processes" in out["sample"]
+
+
+def test_issue_fraction_of_the_paqif_launch():
+    # the capture's 852.5 M warp instructions in 0.964 ms at 2070 MHz fill 70 % of 608 schedulers' slots
+    assert bench.issue_fraction(852_480_330, 0.964224, 2070.0) == pytest.approx(0.7025, abs=1e-4)
+    assert bench.issue_fraction(None, 1.0, 2070.0) is None
+    assert bench.issue_fraction(1, 1.0, None) is None
+    assert bench.SCHEDULERS == 608
