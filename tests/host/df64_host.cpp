@@ -115,7 +115,8 @@ int main(int argc, char** argv) {
       pdf(ehl::df_sub_two_prods(z, a, b, c, d));
       std::printf("\n");
     } else if (!std::strcmp(op, "mul_floats")) {  // lo = 0 on both sides, away from underflow: exact
-      const df x = ehl::make_df((float)random_double(-40, 40), 0.f), y = ehl::make_df((float)random_double(-40, 40), 0.f);
+      const df x = ehl::make_df((float)random_double(-40, 40), 0.f);
+      const df y = ehl::make_df((float)random_double(-40, 40), 0.f);
       pdf(x);
       pdf(y);
       pdf(ehl::df_mul(x, y));
