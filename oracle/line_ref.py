@@ -325,6 +325,51 @@ def solve(pb, P_init=None, H0_init=None, h_init=0.05, tol=1e-12, max_iter=200, v
                        force=abs(pb.h * np.sum(P) - pb.load))
 
 
+def solve_paper(pb, beta=2, omega=1.0, c=0.05, tol=1e-8, max_iter=4000, h_init=0.05):
+    """The paper's hybrid limiter-based Newton iteration for line contact, step by step.
+
+    From the Hertzian start with ``min H = h_init`` (Sec. 4), each iteration
+    (Sec. 3.3.3-3.3.4):
+    1. the residual R at the current iterate (Eqs. eqn62-eqn65);
+    2. the banded approximate Jacobian ``band_beta(J_frozen D)`` with eps, rho
+       and the limiter factor frozen and the change distributed by D in the
+       weighted-change subregion (Eqs. eqn66-eqn69; ``jacobian_band``), the
+       cavitated rows as identity rows (reading of Sec. 2.2.2);
+    3. the band system for the change sigma with right-hand side -R (0 on the
+       cavitated rows), solved here by dense LU in place of PAQIF;
+    4. the projected distributed update ``P <- max(0, P + omega D sigma)``;
+    5. the H0 relaxation ``H0 <- H0 - c (pi/2 - h sum P)`` (Eq. eqn75 with the
+       line-contact load).
+    Stops when ``||min(P, R)||_inf <= tol`` and ``|h sum P - pi/2| <= tol``
+    (checked before each update), or at ``max_iter`` updates, or when the
+    iterate stops being finite.  Returns ``(P, H0, info)`` with ``info["hist"]``
+    the residual before every update.
+    """
+    P = pb.hertz()
+    H0 = pb.h0_for_min_film(P, h_init)
+    hist = []
+    with np.errstate(over="ignore", invalid="ignore"):
+        for it in range(max_iter):
+            r_c, g = comp_residual(pb, P, H0)
+            hist.append(r_c)
+            if not (np.isfinite(r_c) and np.isfinite(g)):
+                return P, H0, dict(iters=it, converged=False, diverged=True, hist=hist)
+            if r_c <= tol and abs(g) <= tol:
+                return P, H0, dict(iters=it, converged=True, diverged=False, hist=hist)
+            R = residual(pb, P, H0)
+            band, act = jacobian_band(pb, P, H0, beta)
+            A = np.zeros((pb.n, pb.n))
+            for i in range(pb.n):
+                for j in range(2 * beta + 1):
+                    col = i - beta + j
+                    if 0 <= col < pb.n:
+                        A[i, col] = band[i, j]
+            sigma = np.linalg.solve(A, np.where(act, 0.0, -R))
+            P = np.maximum(P + omega * (distribution_matrix(pb, P, H0) @ sigma), 0.0)
+            H0 = H0 - c * (pb.load - pb.h * np.sum(P))
+    return P, H0, dict(iters=max_iter, converged=False, diverged=False, hist=hist)
+
+
 def solve_continuation(pb_factory, M_target, L_target, steps, **kw):
     """Solve at ``M_target, L_target`` by a sequence of loads (plain continuation).
 

@@ -299,3 +299,25 @@ def test_nested_solve_where_the_hertzian_start_fails():
     assert np.min(P) >= -1e-10 and np.min(R) >= -1e-10 * max(1.0, np.max(np.abs(R)))
     assert np.max(np.abs(np.minimum(P, R))) <= 1e-10
     assert abs(pbn.h * np.sum(P) - np.pi / 2) <= 1e-10
+
+
+def test_paper_iteration_reaches_the_newton_fixed_point():
+    """The paper's own iteration (frozen band Jacobian, distributed change, H0 relaxation) at
+    the paper's load converges to the solution of the dense semismooth Newton, a different
+    iteration: the fixed point is the discrete problem's, not the method's."""
+    pb = lr.LineProblem(129, 20.0, 10.0, limiter="minmod", dist_weight=0.5)
+    P, H0, info = lr.solve_paper(pb, tol=1e-10)
+    assert info["converged"], info["iters"]
+    Pr, H0r, inf2 = lr.solve(lr.LineProblem(129, 20.0, 10.0, limiter="minmod"))
+    assert inf2["converged"]
+    assert np.max(np.abs(P - Pr)) <= 1e-8 * np.max(Pr)
+    assert abs(H0 - H0r) <= 1e-8 * abs(H0r)
+
+
+def test_literal_distribution_weight_does_not_converge():
+    """Reading A12: with the printed weight 1/4 per neighbour the same iteration wanders with a
+    residual of order 10 instead of converging; 1/2 (no net change of the load) converges."""
+    pb = lr.LineProblem(129, 20.0, 10.0, limiter="minmod", dist_weight=0.25)
+    P, H0, info = lr.solve_paper(pb, max_iter=600)
+    assert not info["converged"]
+    assert min(info["hist"][-300:]) > 1.0
