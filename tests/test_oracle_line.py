@@ -321,3 +321,14 @@ def test_literal_distribution_weight_does_not_converge():
     P, H0, info = lr.solve_paper(pb, max_iter=600)
     assert not info["converged"]
     assert min(info["hist"][-300:]) > 1.0
+
+
+def test_paper_iteration_fails_at_high_load():
+    """At the high load (M = 200) the paper's iteration from the Hertzian start does not
+    converge: its residual grows by orders of magnitude and keeps jumping (why the library's
+    default is the Newton-Krylov method)."""
+    pb = lr.LineProblem(257, 200.0, 10.0, limiter="minmod", dist_weight=0.5)
+    P, H0, info = lr.solve_paper(pb, max_iter=200)
+    assert not info["converged"]
+    h = np.asarray(info["hist"])
+    assert np.nanmax(h) > 100 * h[0]
