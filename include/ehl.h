@@ -339,7 +339,12 @@ ehl_status ehl_adjoint(ehl_ctx* ctx, const double* P, const double* H0, const do
  *  - Set-up: the first call on each device looks up the array's device
  *    address (cudaGetSymbolAddress) with that device current and caches it;
  *    make that first call before any stream capture.  A failed lookup returns
- *    EHL_ECUDA.
+ *    EHL_ECUDA.  The address belongs to the device's primary context (the
+ *    CUDA runtime's): after a cudaDeviceReset the cached address is stale,
+ *    so do not call this entry point in a process that has reset the device.
+ *  - Partitions: the solve always uses the automatic partition count of
+ *    ehl_paqif_solve (partitions = 0); the size limit is checked against
+ *    ehl_paqif_workspace_size() for that count.
  *  - Sharing: all calls on a device use the same array and it keeps the last
  *    call's contents.  Each call overwrites every scratch word it reads, so no
  *    clearing is needed, but calls whose GPU work overlaps in time (different

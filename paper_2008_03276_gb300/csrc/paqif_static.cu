@@ -31,7 +31,10 @@ std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up on the
-// first call per device and cached.  Returns EHL_ECUDA if the lookup fails.
+// first call per device and cached.  The address belongs to the device's primary context (the
+// one the CUDA runtime uses): it stays valid until that context is destroyed, so a process that
+// calls cudaDeviceReset must not call this entry point afterwards.  Returns EHL_ECUDA if the
+// lookup fails.
 ehl_status scratch_address(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -62,6 +65,10 @@ extern "C" ehl_status ehl_paqif_solve_static(int n_sys, int n, int beta, const d
   size_t need = 0;
   if (ehl_paqif_workspace_size(n_sys, n, beta, mode, &need) != EHL_OK) return EHL_EINVAL;
   if (need > (size_t)EHL_PAQIF_STATIC_SCRATCH_BYTES) return EHL_EINVAL;  // batch too large for the fixed array
+  // the layout below is the one ehl_paqif_workspace_size() counts for partitions = 0: the stack,
+  // then the int32 flags at the next aligned offset; both must lie inside `need`
+  const size_t stack_end = align_up(paqif_stack_bytes(n_sys, n, beta, 0), kWorkspaceAlign);
+  if (stack_end + (size_t)n_sys * (size_t)n * sizeof(int) > need) return EHL_EINVAL;
   void* base = nullptr;
   ehl_status st = scratch_address(&base);
   if (st != EHL_OK) return st;

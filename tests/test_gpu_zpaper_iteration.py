@@ -16,19 +16,43 @@ from paper_2008_03276_gb300 import ops
 pytestmark = pytest.mark.gpu
 
 
-def test_paper_iteration_follows_the_oracle():
-    N, M, L = 129, 20.0, 10.0
-    pb = lr.LineProblem(N, M, L, limiter="minmod", dist_weight=0.5)
-    Pr, H0r, info = lr.solve_paper(pb, tol=1e-8)
-    assert info["converged"]
-    p = ops.default_params(1, nx=N, M=M, L=L, limiter=0, halfband=2, method=0, tol=1e-8, max_iter=4000,
+def _gpu_paper_iteration(N, M, L, tol):
+    p = ops.default_params(1, nx=N, M=M, L=L, limiter=0, halfband=2, method=0, tol=tol, max_iter=4000,
                            levels=0)
     assert (p.dist_weight, p.omega, p.c_h0, p.h_init) == (0.5, 1.0, 0.05, 0.05)
     ctx = ops.Context(p)
     P, H0, iters, res, code = ctx.solve(check=False)
-    print(f"GPU method 0: {int(iters.cpu()[0])} iterations; oracle: {info['iters']}")
     assert code == 0
-    assert abs(int(iters.cpu()[0]) - info["iters"]) <= 3
+    return ctx, P, H0, int(iters.cpu()[0])
+
+
+def test_paper_iteration_follows_the_oracle():
+    """Same iteration count at tol 1e-8 (up to PAQIF's rounding against dense LU)."""
+    N, M, L = 129, 20.0, 10.0
+    pb = lr.LineProblem(N, M, L, limiter="minmod", dist_weight=0.5)
+    Pr, H0r, info = lr.solve_paper(pb, tol=1e-8)
+    assert info["converged"]
+    _, P, H0, iters = _gpu_paper_iteration(N, M, L, 1e-8)
+    print(f"GPU method 0: {iters} iterations; oracle: {info['iters']}")
+    assert abs(iters - info["iters"]) <= 3
+
+
+def test_paper_iteration_reaches_the_oracle_solution():
+    """P, H0 and the film H within 1e-8 of the oracle's iteration.
+
+    The iteration converges linearly (a frozen Jacobian), so at tol 1e-8 the two sides may
+    stop one or two iterations apart with iterates that differ by about the tolerance; both
+    are run to 1e-11 here, where their distance to the common fixed point is far below 1e-8.
+    """
+    N, M, L = 129, 20.0, 10.0
+    pb = lr.LineProblem(N, M, L, limiter="minmod", dist_weight=0.5)
+    Pr, H0r, info = lr.solve_paper(pb, tol=1e-11)
+    assert info["converged"]
+    ctx, P, H0, _ = _gpu_paper_iteration(N, M, L, 1e-11)
     Pn = P.cpu().numpy()[0]
-    assert np.max(np.abs(Pn[1:-1] - Pr)) <= 1e-6 * np.max(Pr)
-    assert abs(float(H0.cpu()[0]) - H0r) <= 1e-6 * abs(H0r)
+    assert np.max(np.abs(Pn[1:-1] - Pr)) <= 1e-8 * np.max(Pr)
+    assert abs(float(H0.cpu()[0]) - H0r) <= 1e-8 * abs(H0r)
+    _, H, _ = ctx.residual(P, H0)
+    Hr = pb.film(Pr, H0r)
+    Hg = H.cpu().numpy()[0]
+    assert np.max(np.abs(Hg - Hr)) <= 1e-8 * np.max(np.abs(Hr))

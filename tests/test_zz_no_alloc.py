@@ -18,6 +18,7 @@ from paper_2008_03276_gb300 import _ffi, inputs
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12  # the tolerance of the other PAQIF parity tests
+SCRATCH_BYTES = 16 << 20  # EHL_PAQIF_STATIC_SCRATCH_BYTES of include/ehl.h
 
 
 def _p(t):
@@ -49,7 +50,7 @@ def _static(lib, band, rhs, beta, mode, active, stream):
     return x, it, info
 
 
-@pytest.mark.parametrize("beta,n,n_sys,mode,use_active", [(4, 1024, 200, 1, False), (2, 255, 257, 2, True),
+@pytest.mark.parametrize("beta,n,n_sys,mode,use_active", [(4, 1024, 128, 1, False), (2, 255, 257, 2, True),
                                                           (8, 301, 9, 0, False)])
 def test_static_matches_regular_twice(beta, n, n_sys, mode, use_active):
     lib = _ffi.load()
@@ -86,4 +87,46 @@ def test_static_rejects_batch_beyond_scratch():
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     code = lib.ehl_paqif_solve_static(4096, 1024, 4, _p(band), _p(rhs), _p(None), 1, _p(x), _p(None), _p(None),
                                       stream)
+    assert code == _ffi.EHL_EINVAL
+
+
+def _largest_fitting(lib, n, beta, mode):
+    """The largest n_sys whose workspace fits in the fixed array (bisection on the size query)."""
+    limit = SCRATCH_BYTES
+    nb = ctypes.c_size_t(0)
+
+    def need(k):
+        assert lib.ehl_paqif_workspace_size(k, n, beta, mode, ctypes.byref(nb)) == 0
+        return nb.value
+
+    lo, hi = 1, 1
+    while need(hi) <= limit:
+        lo, hi = hi, hi * 2
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if need(mid) <= limit:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def test_static_accepts_the_largest_batch_and_rejects_one_more():
+    lib = _ffi.load()
+    dev = torch.device("cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    n, beta, mode = 1024, 4, 1
+    k = _largest_fitting(lib, n, beta, mode)
+    band_h, rhs_h = inputs.dd_band_systems(k, n, beta, seed=77)
+    band = torch.from_numpy(band_h).to(dev)
+    rhs = torch.from_numpy(rhs_h).to(dev)
+    xr, _, _ = _regular(lib, band, rhs, beta, mode, None, stream)
+    xs, _, infs = _static(lib, band, rhs, beta, mode, None, stream)
+    torch.cuda.synchronize()
+    assert np.all(infs.cpu().numpy() == 0)
+    xr, xs = xr.cpu().numpy(), xs.cpu().numpy()
+    assert np.max(np.abs(xs - xr)) / np.max(np.abs(xr)) <= TOL
+    x = torch.empty(1, dtype=torch.float64, device=dev)
+    code = lib.ehl_paqif_solve_static(k + 1, n, beta, _p(band), _p(rhs), _p(None), mode, _p(x), _p(None),
+                                      _p(None), stream)
     assert code == _ffi.EHL_EINVAL
