@@ -170,6 +170,49 @@ def jacobian_exact(pb, P_int, H0, Kd=None, block=512):
     return J, JH
 
 
+def xline_band_exact(pb, P_int, H0, beta):
+    """The x-line bands of the exact Jacobian: ``[ny-2, nx-2, 2 beta + 1]``.
+
+    Entry ``[j-1, i-1, beta + k - i]`` is ``dR_ij / dP_kj`` (Sec. 3.3.3: the
+    x-line systems of the point-contact Newton matrix, one per grid row j,
+    here from the exact Jacobian).  Without the dense Jacobian: the residual
+    row ``(i, j)`` reads the film at x-nodes ``i-2 .. i+1`` (the limited faces)
+    and at ``(i, j +/- 1)`` (eps of the y-faces), so the band entries of column
+    ``(k, j)`` need the deformation column of a unit pressure at ``(k, j)``
+    only on the window ``x in [k - beta - 2, k + beta + 1]``, ``y in
+    [j - 1, j + 1]``.  Columns whose windows and stencils are disjoint
+    (x-indices ``2 beta + 4`` apart, y-indices 3 apart) share one forward-mode
+    tangent, each filled with the kernel table on its own window.
+    """
+    s = state(pb, P_int, H0)
+    nx, ny = pb.nx, pb.ny
+    px, py = 2 * beta + 4, 3
+    band = np.zeros((ny - 2, nx - 2, 2 * beta + 1))
+    for cx in range(px):
+        ks = np.arange(1 + cx, nx - 1, px)
+        for cy in range(py):
+            ls = np.arange(1 + cy, ny - 1, py)
+            if len(ks) == 0 or len(ls) == 0:
+                continue
+            dH = np.zeros((nx, ny, 1))
+            dP = np.zeros((nx, ny, 1))
+            K, L = np.meshgrid(ks, ls, indexing="ij")
+            K, L = K.ravel(), L.ravel()
+            dP[K, L, 0] = 1.0
+            if pb.elastic:
+                for ox in range(-beta - 2, beta + 2):
+                    for oy in (-1, 0, 1):
+                        mx, my = K + ox, L + oy
+                        ok = (mx >= 0) & (mx < nx) & (my >= 0) & (my < ny)
+                        dH[mx[ok], my[ok], 0] = pb.table[np.abs(ox), np.abs(oy)]
+            t = _tangent(pb, s, dH, dP)[:, 0].reshape(nx - 2, ny - 2)  # row (i, j) -> [i-1, j-1]
+            for d in range(-beta, beta + 1):
+                rows = K + d  # row i = k + d, entry beta + k - i = beta - d
+                ok = (rows >= 1) & (rows <= nx - 2)
+                band[L[ok] - 1, rows[ok] - 1, beta - d] = t[rows[ok] - 1, L[ok] - 1]
+    return band
+
+
 def rounding_floor(pb, P_int, H0):
     """``1e3`` roundoff units times the largest term entering any ``R_ij``."""
     s = state(pb, P_int, H0)

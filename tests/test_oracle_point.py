@@ -148,3 +148,20 @@ def test_point_adjoint_vs_resolved_differences(solved_33):
     assert abs(fd - g["M"]) <= 1e-5 * abs(fd)
     fd = (hc(L=pb.L * (1 + d)) - hc(L=pb.L * (1 - d))) / (2 * d * pb.L)
     assert abs(fd - g["L"]) <= 1e-5 * abs(fd)
+
+
+@pytest.mark.parametrize("n,beta,limiter", [(17, 2, "minmod"), (21, 3, "vanleer")])
+def test_xline_band_is_the_band_of_the_dense_exact_jacobian(n, beta, limiter):
+    pb = pr.PointProblem(n, n, 20.0, 10.0, limiter=limiter)
+    rng = np.random.default_rng(n)
+    P = pb.hertz() * (1 + 0.05 * rng.standard_normal(pb.n)).clip(0)
+    H0 = pb.h0_for_min_film(P, 0.1)
+    J, _ = pr.jacobian_exact(pb, P, H0)
+    band = pr.xline_band_exact(pb, P, H0, beta)
+    m = n - 2
+    for j in range(m):
+        for i in range(m):
+            for d in range(-beta, beta + 1):
+                k = i + d
+                want = J[i * m + j, k * m + j] if 0 <= k < m else 0.0
+                assert band[j, i, beta + d] == want
