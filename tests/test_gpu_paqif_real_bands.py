@@ -32,7 +32,7 @@ import torch
 from oracle import line_ref as lr
 from oracle import paqif_ref as pq
 from oracle import point_ref as ptr
-from paper_2008_03276_gb300 import ops
+from paper_2008_03276_gb300 import inputs, ops
 
 pytestmark = pytest.mark.gpu
 U_DF = 2.0**-48
@@ -202,9 +202,10 @@ def test_nondominant_seeded_bands(kind, beta, n):
 @pytest.mark.parametrize("rel_det", [0.0, 1e-15])
 def test_singular_middle_pivot_is_reported(beta, rel_det):
     """With one block per system the first 2x2 pivot is the middle pair of rows (s-1, s);
-    a pivot with |det| far below the rounding of |a d| + |b c| must set EHL_INFO_SINGULAR."""
+    a pivot with |det| far below the rounding of |a d| + |b c| must set EHL_INFO_SINGULAR.
+    The other systems of the batch (diagonally dominant) are solved as usual."""
     n = 128
-    band, rhs = nondominant("positive", 3, n, beta, seed=7 + beta)
+    band, rhs = inputs.dd_band_systems(3, n, beta, seed=7 + beta)
     s = n // 2
     # pivot block [[1, 2], [2, 4 (1 + rel_det)]] in rows / columns (s-1, s) of system 1
     band[1, s - 1, beta] = 1.0
