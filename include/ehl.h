@@ -319,6 +319,61 @@ ehl_status ehl_adjoint(ehl_ctx* ctx, const double* P, const double* H0, const do
                        double tol, int max_cycles);
 
 /* ------------------------------------------------------------------------
+ * Linear convection-diffusion workload of the line splittings
+ * ------------------------------------------------------------------------
+ * Defines: Sec. 3.1, Examples 1 and 2 (L u = (a u)_x + (b u)_y - eps Lap u = f,
+ * Dirichlet data), Eq. eqn41 (van Leer's kappa-scheme for the convective
+ * term), Eqs. eqn48-eqn49 (the x-line splittings Ls0 and Ls1), solved by AQIF
+ * line by line (Sec. 6 runs it with u = x^4 + y^4, eps = 1e-6).
+ *
+ * Grid: n x n nodes on [lo, hi]^2, h = (hi - lo) / (n - 1).  Arrays are
+ * [n_inst][n][n] float64 with x fastest (index [z][j][i] for node (x_i, y_j));
+ * every instance shares the parameters.  u carries the Dirichlet values on
+ * its boundary nodes (never written); f is read at the interior nodes.
+ * Convective face value F_{k+1/2} = u_k + (1-kappa)/4 (u_k - u_{k-1})
+ * + (1+kappa)/4 (u_{k+1} - u_k), the node before the inflow boundary being the
+ * linear extrapolation 2 u_0 - u_1; diffusion by the 5-point Laplacian.
+ */
+typedef struct {
+  int n;            /* nodes per direction incl. the boundary, 5..16385             */
+  double lo, hi;    /* the square [lo, hi]^2                                        */
+  double a, b;      /* constant convection coefficients, a > 0, b >= 0             */
+  double eps;       /* diffusion coefficient, >= 0                                  */
+  double kappa;     /* kappa of the scheme, -1..1                                   */
+  int splitting;    /* 0: Ls0 (line operator c = (2-kappa)/2 + (1-kappa)/4),       */
+                    /* 1: Ls1 (c = (2-kappa)/2); the line operator is the upwind   */
+                    /*    difference c a (u_i - u_{i-1}) / h plus the diffusion's    */
+                    /*    x part and diagonal: tridiagonal                          */
+  int order;        /* 0: x-lines one after another in increasing y, each from the */
+                    /*    iterate its predecessors left (the paper's order);        */
+                    /* 1: all x-lines of a sweep from the same iterate              */
+  double omega;     /* relaxation of the change, > 0 (1)                           */
+} ehl_cd_params;
+
+/* r = f - L u at the interior nodes (r nullable, [n_inst][n][n], 0 on the
+ * boundary) and rmax (nullable, [n_inst]) = max |r| per instance (NaN if any r
+ * is NaN).  Asynchronous.  EHL_EINVAL for bad parameters or NULL u / f. */
+ehl_status ehl_cd_residual(const ehl_cd_params* p, int n_inst, const double* u, const double* f, double* r,
+                           double* rmax, void* stream);
+
+/* Bytes of device workspace ehl_cd_relax needs (line matrices, right-hand
+ * sides, changes and the PAQIF factors of the line operator). */
+ehl_status ehl_cd_workspace_size(const ehl_cd_params* p, int n_inst, size_t* bytes);
+
+/* `sweeps` x-line relaxation sweeps in place on u: for each x-line, the change
+ * sigma solves L^0 sigma = f - L u (the current residual of the line) by
+ * PAQIF (the line operator is factored once per call and resolved for every
+ * line), then u += omega sigma.
+ *   rmax_hist (nullable) [sweeps][n_inst]: max |f - L u| after each sweep.
+ *   info (nullable) [n_inst] int32: EHL_INFO_* of the line solves.
+ *   workspace: at least ehl_cd_workspace_size() bytes, 256-byte aligned, or
+ *   NULL to allocate it stream-ordered (cudaMallocAsync / cudaFreeAsync).
+ * Asynchronous.  EHL_EINVAL for bad parameters, u == f or a short workspace,
+ * EHL_ENOMEM, EHL_ECUDA. */
+ehl_status ehl_cd_relax(const ehl_cd_params* p, int n_inst, double* u, const double* f, int sweeps,
+                        double* rmax_hist, int* info, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * PAQIF without any allocation
  * ------------------------------------------------------------------------
  * The paper has no counterpart to this entry point: it exists for callers

@@ -25,6 +25,14 @@ class EhlParams(ctypes.Structure):
                 ("precision", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
+class EhlCdParams(ctypes.Structure):
+    """Mirror of ``ehl_cd_params`` in include/ehl.h."""
+
+    _fields_ = [("n", ctypes.c_int), ("lo", ctypes.c_double), ("hi", ctypes.c_double), ("a", ctypes.c_double),
+                ("b", ctypes.c_double), ("eps", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("splitting", ctypes.c_int), ("order", ctypes.c_int), ("omega", ctypes.c_double)]
+
+
 EHL_OK, EHL_EINVAL, EHL_ENOMEM, EHL_ECUDA, EHL_ENOCONV, EHL_ENONFINITE, EHL_ESINGULAR, EHL_ETIMEOUT = range(8)
 
 # every symbol the header declares; the CPU tests check the library exports them
@@ -57,6 +65,13 @@ SYMBOLS = {
     "ehl_jacobian_apply": (ctypes.c_int, [ctypes.c_void_p] * 7),
     "ehl_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                  ctypes.c_void_p, ctypes.c_void_p]),
+    "ehl_cd_residual": (ctypes.c_int, [ctypes.POINTER(EhlCdParams), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ehl_cd_workspace_size": (ctypes.c_int, [ctypes.POINTER(EhlCdParams), ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_size_t)]),
+    "ehl_cd_relax": (ctypes.c_int, [ctypes.POINTER(EhlCdParams), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_void_p]),
     "ehl_paqif_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),

@@ -258,3 +258,47 @@ def solve_differentiable(ctx, rough, ML, P0=None, H00=None, tol=1e-10, max_cycle
     roughness ``rough`` ([n_inst][nx]) and ``ML`` ([n_inst][2], the (M, L) the context was
     created with); the backward pass is one ``ehl_adjoint`` call."""
     return _SolveFunction.apply(ctx, rough, ML, P0, H00, tol, max_cycles)
+
+
+# ---- linear convection-diffusion workload of the line splittings (Sec. 3.1) ----------------------
+
+def cd_params(n, a=1.0, b=0.0, eps=1e-6, kappa=0.0, splitting="Ls0", order="lexicographic", omega=1.0, lo=-1.0,
+              hi=1.0):
+    """``ehl_cd_params`` for an n x n grid (splitting "Ls0"/"Ls1", order "lexicographic"/"jacobi")."""
+    return _ffi.EhlCdParams(int(n), float(lo), float(hi), float(a), float(b), float(eps), float(kappa),
+                            {"Ls0": 0, "Ls1": 1}[splitting], {"lexicographic": 0, "jacobi": 1}[order], float(omega))
+
+
+def cd_residual(p, u, f, stream=None):
+    """``(r, rmax)`` of ``u, f`` ([n_inst][n][n] float64, x fastest)."""
+    lib = _ffi.load()
+    _check_dev(u, f)
+    n_inst = u.shape[0]
+    r = torch.empty_like(u)
+    rmax = torch.empty(n_inst, dtype=torch.float64, device=u.device)
+    code = lib.ehl_cd_residual(ctypes.byref(p), n_inst, _ptr(u), _ptr(f), _ptr(r), _ptr(rmax), _stream(stream))
+    _ffi.check(code, "ehl_cd_residual")
+    return r, rmax
+
+
+def cd_relax(p, u, f, sweeps, workspace=None, stream=None):
+    """``sweeps`` line-relaxation sweeps on ``u`` in place; returns ``(rmax_hist [sweeps][n_inst], info)``."""
+    lib = _ffi.load()
+    _check_dev(u, f, workspace)
+    n_inst = u.shape[0]
+    hist = torch.empty((max(sweeps, 1), n_inst), dtype=torch.float64, device=u.device)
+    info = torch.empty(n_inst, dtype=torch.int32, device=u.device)
+    wbytes = 0
+    if workspace is not None:
+        wbytes = workspace.numel()
+    code = lib.ehl_cd_relax(ctypes.byref(p), n_inst, _ptr(u), _ptr(f), int(sweeps), _ptr(hist), _ptr(info),
+                            _ptr(workspace), wbytes, _stream(stream))
+    _ffi.check(code, "ehl_cd_relax")
+    return hist[:sweeps], info
+
+
+def cd_workspace_size(p, n_inst):
+    nb = ctypes.c_size_t(0)
+    _ffi.check(_ffi.load().ehl_cd_workspace_size(ctypes.byref(p), int(n_inst), ctypes.byref(nb)),
+               "ehl_cd_workspace_size")
+    return nb.value
