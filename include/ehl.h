@@ -184,7 +184,9 @@ typedef struct {
   double p0, z;         /* Roelands constants (1.98e8, 0.68)                            */
   int compressible;     /* 1: Roelands + Dowson-Higginson; 0: rho = eta = 1             */
   int elastic;          /* 1: elastic deformation; 0: rigid surfaces                    */
-  int limiter;          /* 0: minmod, 1: van Leer                                       */
+  int limiter;          /* 0: minmod, 1: van Leer (limited, TVD); 2: the unlimited       */
+                        /*   kappa-scheme of van Leer (Sec. 3.1, Eq. eqn41; Sec. 3.3.2,  */
+                        /*   Eq. eqn56): psi = ((1 - kappa) a + (1 + kappa) b) / 2       */
   int halfband;         /* half-bandwidth beta of the band Jacobian, 1..8               */
   double switch_eps_h;  /* eps/h threshold of the hybrid splitting (0.6)                */
   double dist_weight;   /* weighted-change share per neighbour (line 0.5)               */
@@ -218,6 +220,15 @@ typedef struct {
   int graph;            /* line contact, method 1: 1 = each Newton step is one CUDA graph  */
                         /*   launch (captured once, replayed; one host check per step);    */
                         /*   0 = launched kernel by kernel with early exits (default)      */
+  double kappa;         /* kappa of limiter 2, -1..1 (0: Fromm, 1/3: third-order upwind    */
+                        /*   biased, -1: second-order upwind)                              */
+  int splitting;        /* Couette part of the kind-0 Newton matrix (method 0):             */
+                        /*   0: the limiter frozen at the current iterate (Sec. 3.3.3);    */
+                        /*   1: L_hs1, 2: L_hs2 (Sec. 3.3.2, Eqs. eqn57-eqn61): the upwind  */
+                        /*   difference c (rho_i dH_i - rho_{i-1} dH_{i-1}) / h with        */
+                        /*   c = (2 - kappa)/2 (L_hs1) or (2 - kappa)/2 + (1 - kappa)/4    */
+                        /*   (L_hs2); the weighted-change distribution where eps/h is at   */
+                        /*   most switch_eps_h in every case                               */
 } ehl_params;
 
 /* Fill *p with the defaults above for dimension `dim` (1). */

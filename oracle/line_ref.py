@@ -34,7 +34,7 @@ class LineProblem:
 
     def __init__(self, N, M, L, xa=-4.5, xb=1.5, alpha=1.7e-8, compressible=True,
                  elastic=True, limiter="minmod", rough=None, switch_eps_h=0.6,
-                 dist_weight=0.25):
+                 dist_weight=0.25, kappa=0.0, splitting="frozen"):
         self.N = int(N)
         self.n = self.N - 2
         self.M, self.L = float(M), float(L)
@@ -45,9 +45,13 @@ class LineProblem:
         self.lam, self.abar = material_ref.moes_line(self.M, self.L)
         self.compressible = bool(compressible)
         self.elastic = bool(elastic)
-        if limiter not in ("minmod", "vanleer"):
+        if limiter not in ("minmod", "vanleer", "kappa"):
             raise ValueError(limiter)
+        if splitting not in ("frozen", "hs1", "hs2"):
+            raise ValueError(splitting)
         self.limiter = limiter
+        self.kappa = float(kappa)
+        self.splitting = splitting
         self.rough = np.zeros(self.N) if rough is None else np.asarray(rough, dtype=np.float64)
         self.K = kernels_ref.k_line(self.N, self.h) if self.elastic else np.zeros((self.N, self.N))
         self.switch_eps_h = float(switch_eps_h)
@@ -75,10 +79,20 @@ class LineProblem:
         return h_init - np.min(H)
 
 
-def limiter(a, b, kind):
-    """``psi(a, b)`` and its partial derivatives (piecewise, exact on each branch)."""
+def limiter(a, b, kind, kappa=0.0):
+    """``psi(a, b)`` and its partial derivatives (piecewise, exact on each branch).
+
+    ``kind`` "minmod" or "vanleer" (limited, Sec. 3.3.3), or "kappa": van Leer's
+    unlimited kappa-scheme, whose face value ``u_i + (1 - kappa)/4 a + (1 + kappa)/4 b``
+    (Sec. 3.1, Eq. eqn41; Sec. 3.3.2, Eq. eqn56) is ``u_i + psi / 2`` with the linear
+    ``psi = ((1 - kappa) a + (1 + kappa) b) / 2``.
+    """
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
+    if kind == "kappa":
+        da = np.full(a.shape, 0.5 * (1.0 - kappa))
+        db = np.full(b.shape, 0.5 * (1.0 + kappa))
+        return da * a + db * b, da, db
     same = a * b > 0.0
     if kind == "minmod":
         use_a = np.abs(a) <= np.abs(b)
@@ -106,7 +120,7 @@ def state(pb, P_int, H0):
     b = np.zeros(N - 1)
     a[1:] = u[1:-1] - u[:-2]
     b[1:] = u[2:] - u[1:-1]
-    psi, pa, pbb = limiter(a, b, pb.limiter)
+    psi, pa, pbb = limiter(a, b, pb.limiter, pb.kappa)
     psi[0] = 0.0
     pa[0] = 0.0
     pbb[0] = 0.0
@@ -159,6 +173,24 @@ def jacobian_exact(pb, P_int, H0):
     return J[:, :n], J[:, n]
 
 
+def split_coefficient(pb):
+    """``c`` of the hybrid splittings' upwind Couette part, or None for the frozen limiter.
+
+    Sec. 3.3.2, Eqs. eqn57-eqn61: L_hs1 keeps the kappa-scheme's first-order part
+    ``(2 - kappa)/2 (H_i - H_{i-1})`` in the line operator (Ls1 / Ls4), L_hs2 also
+    the ``(1 - kappa)/4 (H_i - H_{i-1})`` that Eq. eqn58 splits off the upwind
+    difference (Ls0 / Ls5); the rest of the convective term stays on the right-hand
+    side.  Both use the weighted-change distribution where eps/h <= switch.
+    Parity unpinned: these matrices are the paper's iteration operators, which no
+    closed form or limit case fixes; only their fixed point (the residual) is pinned.
+    """
+    if pb.splitting == "hs1":
+        return (2.0 - pb.kappa) / 2.0
+    if pb.splitting == "hs2":
+        return (2.0 - pb.kappa) / 2.0 + (1.0 - pb.kappa) / 4.0
+    return None
+
+
 def jacobian_frozen(pb, P_int, H0):
     """``dR/dP`` with eps, rho and the limiter factor frozen (Sec. 3.3.3, Eqs. eqn62-eqn66).
 
@@ -172,12 +204,16 @@ def jacobian_frozen(pb, P_int, H0):
     N, n, h = pb.N, pb.n, pb.h
     rho = s["rho"]
     a = s["a"]
-    phi = np.where(a != 0.0, s["psi"] / np.where(a != 0.0, a, 1.0), 0.0)
-    phi[0] = 0.0
     du = -rho[:, None] * pb.K[:, 1:-1]  # [N, n]
-    dF = du[:-1].copy()
-    dF[1:] += 0.5 * phi[1:, None] * (du[1:-1] - du[:-2])
-    dC = (dF[1:] - dF[:-1]) / h
+    c = split_coefficient(pb)
+    if c is not None:
+        dC = c * (du[1:-1] - du[:-2]) / h
+    else:
+        phi = np.where(a != 0.0, s["psi"] / np.where(a != 0.0, a, 1.0), 0.0)
+        phi[0] = 0.0
+        dF = du[:-1].copy()
+        dF[1:] += 0.5 * phi[1:, None] * (du[1:-1] - du[:-2])
+        dC = (dF[1:] - dF[:-1]) / h
     epsf = s["epsf"]
     dQ = np.zeros((n, n))
     for r in range(n):  # row r <-> node r+1

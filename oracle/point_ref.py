@@ -30,7 +30,7 @@ class PointProblem:
     """Grid, kernel and lubricant constants of one point-contact instance."""
 
     def __init__(self, nx, ny, M, L, xa=-4.5, xb=1.5, ya=-3.0, alpha=1.7e-8, compressible=True,
-                 elastic=True, limiter="minmod", rough=None):
+                 elastic=True, limiter="minmod", rough=None, kappa=0.0):
         self.nx, self.ny = int(nx), int(ny)
         self.M, self.L = float(M), float(L)
         self.h = (xb - xa) / (self.nx - 1)
@@ -41,9 +41,10 @@ class PointProblem:
         self.lam, self.abar = material_ref.moes_point(self.M, self.L)
         self.compressible = bool(compressible)
         self.elastic = bool(elastic)
-        if limiter not in ("minmod", "vanleer"):
+        if limiter not in ("minmod", "vanleer", "kappa"):
             raise ValueError(limiter)
         self.limiter = limiter
+        self.kappa = float(kappa)
         self.rough = np.zeros((self.nx, self.ny)) if rough is None else np.asarray(rough, dtype=np.float64)
         self.table = kernels_ref.g_point_table(self.nx, self.ny, self.h)
         self.load = 2.0 * np.pi / 3.0
@@ -92,7 +93,7 @@ def state(pb, P_int, H0):
     b = np.zeros((nx - 1, pb.ny))
     a[1:] = u[1:-1] - u[:-2]
     b[1:] = u[2:] - u[1:-1]
-    psi, pa, pbb = line_ref.limiter(a, b, pb.limiter)
+    psi, pa, pbb = line_ref.limiter(a, b, pb.limiter, pb.kappa)
     psi[0] = pa[0] = pbb[0] = 0.0
     F = u[:-1] + 0.5 * psi
     ex = 0.5 * (eps[:-1] + eps[1:])        # [nx-1, ny]

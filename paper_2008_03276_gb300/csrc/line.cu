@@ -199,7 +199,7 @@ __global__ void k_line_faces(const LineInst* __restrict__ inst, const double* __
   if (j >= N - 1) return;
   const size_t o = (size_t)z * N + j;
   double ps = 0.0, pa = 0.0, pb = 0.0;
-  if (j >= 1) line_limiter(inst[z].limiter, u[o] - u[o - 1], u[o + 1] - u[o], ps, pa, pb);
+  if (j >= 1) line_limiter(inst[z].limiter, inst[z].kappa, u[o] - u[o - 1], u[o + 1] - u[o], ps, pa, pb);
   F[o] = u[o] + 0.5 * ps;
   psi[o] = ps;
   psia[o] = pa;
@@ -330,14 +330,16 @@ struct LineRowCtx {
     const double a = u[base + j] - u[base + j - 1];
     return a != 0.0 ? psi[base + j] / a : 0.0;
   }
-  // frozen face derivative dF_{j+1/2}/dP_m (rho, phi, eps frozen)
-  __device__ double dF_frozen(int j, int m) const {
+  // frozen face derivative dF_{j+1/2}/dP_m (rho, phi, eps frozen); with a hybrid splitting
+  // (cs > 0) the face carries cs rho_j dH_j, so that dC_i = cs (du_i - du_{i-1}) / h
+  __device__ double dF_frozen(int j, int m, double cs) const {
+    if (cs > 0.0) return -cs * rho[base + j] * K(j - m);
     if (j == 0) return -rho[base] * K(0 - m);
     const double ph = phi(j);
     return -rho[base + j] * (1.0 + 0.5 * ph) * K(j - m) + 0.5 * ph * rho[base + j - 1] * K(j - 1 - m);
   }
-  __device__ double J_frozen(int i, int m, double ef0, double ef1) const {
-    double dC = (dF_frozen(i, m) - dF_frozen(i - 1, m)) / h;
+  __device__ double J_frozen(int i, int m, double ef0, double ef1, double cs) const {
+    double dC = (dF_frozen(i, m, cs) - dF_frozen(i - 1, m, cs)) / h;
     double dQ = 0.0;
     if (m == i + 1) dQ = ef1 / (h * h);
     if (m == i) dQ = -(ef1 + ef0) / (h * h);
@@ -448,8 +450,9 @@ struct LineRowCtx {
                       0.5 * (dEh(i - 1) + dEh(i)) * (Pi - P[base + i - 1]);
     return dC - dq / (h * h);
   }
-  __device__ double JH_frozen(int i) const {
+  __device__ double JH_frozen(int i, double cs) const {
     auto dFh = [&](int j) {
+      if (cs > 0.0) return cs * rho[base + j];
       if (j == 0) return rho[base];
       const double ph = phi(j);
       return rho[base + j] * (1.0 + 0.5 * ph) - 0.5 * ph * rho[base + j - 1];
@@ -482,20 +485,21 @@ __global__ void k_line_jac_band(const LineInst* __restrict__ inst, LineRowCtx c,
   if (kind == 0) {
     a = (Pi <= 0.0) && (Ri > 0.0);
     const double w = inst[z].dist_w, sw = inst[z].switch_eps_h;
+    const double cs = line_split_coef(inst[z]);
     for (int j = 0; j < bw; ++j) {
       const int col = r - beta + j;  // interior column index, node col + 1
       double v = 0.0;
       if (col >= 0 && col < n) {
         const int m = col + 1;
-        v = q.J_frozen(i, m, ef0, ef1);
+        v = q.J_frozen(i, m, ef0, ef1, cs);
         if (c.eps[q.base + m] / q.h <= sw) {
-          if (m - 1 >= 1) v -= w * q.J_frozen(i, m - 1, ef0, ef1);
-          if (m + 1 <= N - 2) v -= w * q.J_frozen(i, m + 1, ef0, ef1);
+          if (m - 1 >= 1) v -= w * q.J_frozen(i, m - 1, ef0, ef1, cs);
+          if (m + 1 <= N - 2) v -= w * q.J_frozen(i, m + 1, ef0, ef1, cs);
         }
       }
       row[j] = a ? (j == beta ? 1.0 : 0.0) : v;
     }
-    if (jh) jh[(size_t)z * n + r] = a ? 0.0 : q.JH_frozen(i);
+    if (jh) jh[(size_t)z * n + r] = a ? 0.0 : q.JH_frozen(i, cs);
   } else {
     // row scale d = max(|J_ii|, |J_i|_max / 10) over the band: |J_ii| alone can pass
     // through zero in the Hertzian zone, where the row is carried by its neighbours

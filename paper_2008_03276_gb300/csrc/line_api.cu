@@ -102,6 +102,8 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   p->precond_blocks = 1;
   p->precision = 0;
   p->graph = 0;
+  p->kappa = 0.0;
+  p->splitting = 0;
 }
 
 static bool point_grid_ok(const ehl_params& p) {
@@ -112,7 +114,8 @@ static bool point_grid_ok(const ehl_params& p) {
 
 static bool params_ok(const ehl_params& p) {
   return (p.dim == 1 || p.dim == 2) && point_grid_ok(p) && p.nx >= 5 && p.nx <= 65536 && p.halfband >= 1 && p.halfband <= 8 && p.M > 0.0 &&
-         p.L >= 0.0 && p.xb > p.xa && p.alpha > 0.0 && p.p0 > 0.0 && p.z > 0.0 && (p.limiter == 0 || p.limiter == 1) &&
+         p.L >= 0.0 && p.xb > p.xa && p.alpha > 0.0 && p.p0 > 0.0 && p.z > 0.0 && (p.limiter >= 0 && p.limiter <= 2) &&
+         p.kappa >= -1.0 && p.kappa <= 1.0 && p.splitting >= 0 && p.splitting <= 2 &&
          (p.method == 0 || p.method == 1) && p.max_iter >= 1 && p.krylov_dim >= 1 && p.krylov_dim <= 200 &&
          p.tol > 0.0 && isfinite(p.h_init) && isfinite(p.c_h0) && isfinite(p.omega) && isfinite(p.dist_weight) &&
          isfinite(p.switch_eps_h) && p.levels >= -1 && p.coarse_min_nodes >= 5 && p.coarse_tol > 0.0 &&
@@ -126,6 +129,8 @@ static LineInst make_inst(const ehl_params& p) {
   q.N = p.nx;
   q.beta = p.halfband;
   q.limiter = p.limiter;
+  q.kappa = p.kappa;
+  q.splitting = p.splitting;
   q.compressible = p.compressible ? 1 : 0;
   q.elastic = p.elastic ? 1 : 0;
   q.xa = p.xa;

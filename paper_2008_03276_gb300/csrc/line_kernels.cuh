@@ -5,7 +5,8 @@
 //    K_d = G_d / pi with the closed-form cell integral G_d of log|x - x'|;
 //  * lubricant (Sec. 3.3, Example 6): Roelands eta, Dowson-Higginson rho, eps = rho H^3/(eta lambda);
 //  * TVD residual (Sec. 3.3.3, Eqs. eqn62-eqn65 in the standard upwind form):
-//    F_{j+1/2} = u_j + psi(u_j - u_{j-1}, u_{j+1} - u_j)/2 (F_{1/2} = u_0), u = rho H,
+//    F_{j+1/2} = u_j + psi(u_j - u_{j-1}, u_{j+1} - u_j)/2 (F_{1/2} = u_0), u = rho H, psi a
+//    limiter (minmod, van Leer) or the linear kappa-scheme (Sec. 3.1, Eq. eqn41),
 //    R_i = (F_{i+1/2} - F_{i-1/2})/h - [eps_{i+1/2}(P_{i+1}-P_i) - eps_{i-1/2}(P_i-P_{i-1})]/h^2.
 #pragma once
 #include <cuda_runtime.h>
@@ -17,15 +18,26 @@ namespace ehl {
 struct LineInst {
   int N;             // nodes including the two boundary nodes
   int beta;          // half-band of the Jacobian
-  int limiter;       // 0 minmod, 1 van Leer
+  int limiter;       // 0 minmod, 1 van Leer, 2 the unlimited kappa-scheme
   int compressible;  // 0: rho = eta = 1
   int elastic;       // 0: rigid surfaces
-  int pad0;
+  int splitting;     // kind-0 Couette part: 0 frozen limiter, 1 L_hs1, 2 L_hs2
   double xa, h;
   double lam, abar, alpha, p0, z, pH;
   double switch_eps_h, dist_w, c_h0, omega, tol, h_init;
   double M, L;       // Moes parameters (lam = 3 pi^2/(8 M^2), pH = L sqrt(M/(2 pi))/alpha)
+  double kappa;      // kappa of limiter 2
 };
+
+// Coefficient c of the upwind Couette difference in the kind-0 Newton matrix of the hybrid
+// splittings (Sec. 3.3.2, Eqs. eqn57, eqn59): L_hs1 keeps (2 - kappa)/2 of the kappa-scheme's
+// first-order part, L_hs2 adds the (1 - kappa)/4 it moves over from the upwind node; 0 selects
+// the frozen limiter factor of Sec. 3.3.3.
+__host__ __device__ __forceinline__ double line_split_coef(const LineInst& q) {
+  if (q.splitting == 1) return (2.0 - q.kappa) / 2.0;
+  if (q.splitting == 2) return (2.0 - q.kappa) / 2.0 + (1.0 - q.kappa) / 4.0;
+  return 0.0;
+}
 
 // rho, d rho/dP, ln eta and (d eta/dP)/eta at pressure P (float64).
 __device__ __forceinline__ void line_material(const LineInst& q, double P, double& rho, double& drho,
@@ -47,8 +59,16 @@ __device__ __forceinline__ void line_material(const LineInst& q, double P, doubl
   drho = a * (1.34 * q.pH - q.pH) / (den * den);
 }
 
-// Limiter function psi(a, b) and its partial derivatives on the current branch.
-__device__ __forceinline__ void line_limiter(int kind, double a, double b, double& psi, double& pa, double& pb) {
+// Limiter function psi(a, b) and its partial derivatives on the current branch; kind 2 is the
+// unlimited kappa-scheme (Eq. eqn41: F = u_i + (1-kappa)/4 a + (1+kappa)/4 b), linear in a, b.
+__device__ __forceinline__ void line_limiter(int kind, double kappa, double a, double b, double& psi, double& pa,
+                                             double& pb) {
+  if (kind == 2) {
+    pa = 0.5 * (1.0 - kappa);
+    pb = 0.5 * (1.0 + kappa);
+    psi = pa * a + pb * b;
+    return;
+  }
   if (!(a * b > 0.0)) {
     psi = pa = pb = 0.0;
     return;

@@ -242,7 +242,7 @@ __global__ void k_pt_faces(const PointInst* __restrict__ inst, const double* __r
     return;
   }
   double ps = 0.0, pa = 0.0, pb = 0.0;
-  if (f >= 1) line_limiter(q.m.limiter, u[o] - u[o - 1], u[o + 1] - u[o], ps, pa, pb);
+  if (f >= 1) line_limiter(q.m.limiter, q.m.kappa, u[o] - u[o - 1], u[o + 1] - u[o], ps, pa, pb);
   F[o] = u[o] + 0.5 * ps;
   psia[o] = pa;
   psib[o] = pb;

@@ -11,6 +11,8 @@ Independent checks:
 * the Hertzian dry-contact limit at high load;
 * force balance and complementarity at convergence; grid-convergence order.
 """
+import os
+
 import numpy as np
 import pytest
 from scipy import integrate, optimize
@@ -66,9 +68,9 @@ def test_material_limits_and_derivatives():
     assert np.all(one[0] == 1) and np.all(one[2] == 1)
 
 
-@pytest.mark.parametrize("limiter", ["minmod", "vanleer"])
+@pytest.mark.parametrize("limiter", ["minmod", "vanleer", "kappa"])
 def test_exact_jacobian_vs_fd(limiter):
-    pb = lr.LineProblem(65, 20, 10, limiter=limiter)
+    pb = lr.LineProblem(65, 20, 10, limiter=limiter, kappa=1.0 / 3.0)
     P = pb.hertz() * (1 + 0.1 * np.sin(np.arange(pb.n)))
     H0 = pb.h0_for_min_film(P, 0.1)
     J, JH = lr.jacobian_exact(pb, P, H0)
@@ -332,3 +334,47 @@ def test_paper_iteration_fails_at_high_load():
     assert not info["converged"]
     h = np.asarray(info["hist"])
     assert np.nanmax(h) > 100 * h[0]
+
+
+# ------------------------------------------------------ van Leer's kappa-schemes (Sec. 3.1, 3.3.2)
+GOLDEN_KAPPA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "kappa_stencils.txt")
+
+
+def test_kappa_scheme_couette_stencil():
+    """The Couette difference of the EHL residual with limiter "kappa" expands to the
+    stencils of Eq. eqn42 (kappa = 0) and the textbook upwind differences: rigid,
+    incompressible, P = 0, so R_i = (F_{i+1/2} - F_{i-1/2}) / h of u = H, and a unit
+    roughness pulse at node k gives the coefficient of offset k - i."""
+    for kappa, *coef in np.loadtxt(GOLDEN_KAPPA):
+        pb0 = lr.LineProblem(33, 20.0, 10.0, compressible=False, elastic=False, limiter="kappa", kappa=kappa)
+        base = lr.residual(pb0, np.zeros(pb0.n), 0.3)
+        i = 12  # node; residual row i - 1
+        for d, c in zip(range(-2, 3), coef):
+            rough = np.zeros(pb0.N)
+            rough[i + d] = 1.0
+            pb = lr.LineProblem(33, 20.0, 10.0, compressible=False, elastic=False, limiter="kappa", kappa=kappa,
+                                rough=rough)
+            got = (lr.residual(pb, np.zeros(pb.n), 0.3) - base)[i - 1] * pb.h
+            assert abs(got - c) <= 1e-12, (kappa, d, got, c)
+
+
+@pytest.mark.parametrize("kappa", [0.0, 1.0 / 3.0, -1.0])
+def test_kappa_scheme_grid_convergence(kappa):
+    """Observed orders of Eqs. eqn96-eqn97 (L1 and L2) at M = 20, L = 10 are positive; the
+    L1 order is near one (the pressure spike sharpens under refinement, which also keeps
+    the max-norm differences from decreasing)."""
+    sols = {}
+    for N in (257, 513, 1025):
+        fac = lambda n: lr.LineProblem(n, 20.0, 10.0, limiter="kappa", kappa=kappa)
+        pb, P, H0, info = lr.solve_nested(fac, N, tol=1e-12)
+        assert info["converged"]
+        sols[N] = pb.full(P)
+
+    def norms(coarse, fine):
+        d = sols[coarse] - sols[fine][::2]
+        Hc = 6.0 / (coarse - 1)
+        return Hc * np.sum(np.abs(d)), np.sqrt(Hc * np.sum(d**2))
+
+    (l1a, l2a), (l1b, l2b) = norms(257, 513), norms(513, 1025)
+    p1, p2 = np.log2(l1a / l1b), np.log2(l2a / l2b)
+    assert 0.6 < p1 < 1.6 and 0.2 < p2 < 1.5, (p1, p2)
