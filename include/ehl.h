@@ -229,6 +229,12 @@ typedef struct {
                         /*   c = (2 - kappa)/2 (L_hs1) or (2 - kappa)/2 + (1 - kappa)/4    */
                         /*   (L_hs2); the weighted-change distribution where eps/h is at   */
                         /*   most switch_eps_h in every case                               */
+  int deform;           /* point contact: evaluation of the deformation sum (Sec. 3.3.1   */
+                        /*   Case 2) in the film and the Krylov products:                   */
+                        /*   0: the direct sum over all cells (the paper's);               */
+                        /*   1: the same discrete convolution through a float64 FFT of     */
+                        /*   cyclic length 2^ceil(log2(2 n - 3)) per direction (nx, ny up  */
+                        /*   to 2049); the adjoint's products keep the direct sum          */
 } ehl_params;
 
 /* Fill *p with the defaults above for dimension `dim` (1). */

@@ -104,6 +104,7 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   p->graph = 0;
   p->kappa = 0.0;
   p->splitting = 0;
+  p->deform = 0;
 }
 
 static bool point_grid_ok(const ehl_params& p) {
@@ -116,6 +117,7 @@ static bool params_ok(const ehl_params& p) {
   return (p.dim == 1 || p.dim == 2) && point_grid_ok(p) && p.nx >= 5 && p.nx <= 65536 && p.halfband >= 1 && p.halfband <= 8 && p.M > 0.0 &&
          p.L >= 0.0 && p.xb > p.xa && p.alpha > 0.0 && p.p0 > 0.0 && p.z > 0.0 && (p.limiter >= 0 && p.limiter <= 2) &&
          p.kappa >= -1.0 && p.kappa <= 1.0 && p.splitting >= 0 && p.splitting <= 2 &&
+         (p.deform == 0 || (p.deform == 1 && p.dim == 2 && fft2_size_ok(p.nx, p.ny))) &&
          (p.method == 0 || p.method == 1) && p.max_iter >= 1 && p.krylov_dim >= 1 && p.krylov_dim <= 200 &&
          p.tol > 0.0 && isfinite(p.h_init) && isfinite(p.c_h0) && isfinite(p.omega) && isfinite(p.dist_weight) &&
          isfinite(p.switch_eps_h) && p.levels >= -1 && p.coarse_min_nodes >= 5 && p.coarse_tol > 0.0 &&
@@ -368,7 +370,7 @@ static ehl_status create_point(const ehl_params* p, int n_inst, const ehl_params
   ctx->pt = new PtCtx();
   ctx->pt->st = stream;
   if (const char* tr = getenv("EHL_TRACE")) ctx->pt->trace = atoi(tr) > 0 ? atoi(tr) : 0;
-  ehl_status st = pt_init(ctx->pt, insts, p->halfband, p->max_iter, p->krylov_dim, p->precision);
+  ehl_status st = pt_init(ctx->pt, insts, p->halfband, p->max_iter, p->krylov_dim, p->precision, p->deform);
   // coarse grids: halve the intervals in both directions while both stay even and
   // the coarse grid keeps coarse_min_nodes nodes per direction
   int gx = p->nx, gy = p->ny;
@@ -393,7 +395,7 @@ static ehl_status create_point(const ehl_params* p, int n_inst, const ehl_params
     l->st = stream;
     l->trace = ctx->pt->trace;
     ctx->ptlv.push_back(l);
-    st = pt_init(l, ci, p->halfband, std::min(p->max_iter, kCoarseMaxIter), p->krylov_dim, p->precision);
+    st = pt_init(l, ci, p->halfband, std::min(p->max_iter, kCoarseMaxIter), p->krylov_dim, p->precision, p->deform);
     double* r = nullptr;
     if (st == EHL_OK && pt_alloc(l, (void**)&r, sizeof(double) * n_inst * (size_t)l->NN) != cudaSuccess) {
       cudaGetLastError();

@@ -613,7 +613,7 @@ static PtRow pt_row(PtCtx* c, const double* P) {
 }
 
 ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int max_iter, int krylov_dim,
-                   int precision) {
+                   int precision, int deform) {
   const int ni = (int)insts.size();
   c->n_inst = ni;
   c->nx = insts[0].nx;
@@ -681,7 +681,16 @@ ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int 
     note_launch();
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess && precision > 0 && insts[0].m.elastic) {
+  if (e == cudaSuccess && deform == 1 && insts[0].m.elastic) {
+    void* mem = nullptr;
+    if (pt_alloc(c, &mem, fft2_bytes(c->nx, c->ny, ni)) != cudaSuccess) {
+      cudaGetLastError();
+      return EHL_ENOMEM;
+    }
+    e = fft2_init(c->fft, c->nx, c->ny, ni, mem, c->gtab64, c->st);
+    c->use_fft = e == cudaSuccess;
+  }
+  if (e == cudaSuccess && precision > 0 && insts[0].m.elastic && !c->use_fft) {
     const size_t ldt = pt_ld8(c->nx), ldq = pt_ld8((size_t)c->NN);
     const size_t tall = ldt * c->nx * c->ny, q = ldq * c->ny * ni, dn = ldt * c->ny * ni;
     if (pt_alloc(c, (void**)&c->Tall, sizeof(float) * tall) != cudaSuccess ||
@@ -706,7 +715,16 @@ ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int 
   return EHL_OK;
 }
 
-static cudaError_t pt_deform(PtCtx* c, const double* V, const int* skip, bool f64) {
+// D = K V into c->partial: `parts` partial sums, float64 (p64 = 1) or double-float (0)
+static cudaError_t pt_deform(PtCtx* c, const double* V, const int* skip, bool f64, int& parts, int& p64,
+                             bool direct = false) {
+  if (c->use_fft && !direct) {
+    parts = 1;
+    p64 = 1;
+    return fft2_conv(c->fft, V, skip, reinterpret_cast<double*>(c->partial), c->st);
+  }
+  parts = c->ksplit;
+  p64 = f64 ? 1 : 0;
   dim3 g((c->nx + kPtTI - 1) / kPtTI, (c->ny + kPtTJ - 1) / kPtTJ, c->n_inst * c->ksplit);
   if (f64)
     k_pt_deform<true><<<g, kPtTI * kPtTJ, 0, c->st>>>(c->inst, c->gtab, c->gtab64, V, skip, c->partial, c->n_inst,
@@ -719,10 +737,11 @@ static cudaError_t pt_deform(PtCtx* c, const double* V, const int* skip, bool f6
 }
 
 cudaError_t pt_state(PtCtx* c, const double* P, const double* H0, const double* rough, const int* skip) {
-  cudaError_t e = pt_deform(c, P, skip, true);
+  int parts = 1, p64 = 1;
+  cudaError_t e = pt_deform(c, P, skip, true, parts, p64);
   if (e != cudaSuccess) return e;
   const dim3 gn((c->NN + kPtNode - 1) / kPtNode, c->n_inst);
-  k_pt_film<<<gn, kPtNode, 0, c->st>>>(c->inst, c->partial, c->ksplit, 1, H0, rough, skip, c->H, c->n_inst, 0);
+  k_pt_film<<<gn, kPtNode, 0, c->st>>>(c->inst, c->partial, parts, p64, H0, rough, skip, c->H, c->n_inst, 0);
   note_launch();
   k_pt_nodes<<<gn, kPtNode, 0, c->st>>>(c->inst, P, c->H, skip, c->rho, c->drho, c->deta_rel, c->eps, c->u);
   note_launch();
@@ -789,20 +808,22 @@ static cudaError_t pt_deform_gemm(PtCtx* c, const double* zn, const int* skip, c
 }
 
 cudaError_t pt_deform_dir(PtCtx* c, const double* zn, const double* zh0, const int* skip) {
-  if (c->precision > 0) return pt_deform_gemm(c, zn, skip, zh0);
-  cudaError_t e = pt_deform(c, zn, skip, false);
+  if (c->precision > 0 && !c->use_fft) return pt_deform_gemm(c, zn, skip, zh0);
+  int parts = 1, p64 = 0;
+  cudaError_t e = pt_deform(c, zn, skip, false, parts, p64);
   if (e != cudaSuccess) return e;
   const dim3 gn((c->NN + kPtNode - 1) / kPtNode, c->n_inst);
-  k_pt_film<<<gn, kPtNode, 0, c->st>>>(c->inst, c->partial, c->ksplit, 0, zh0, nullptr, skip, c->dH, c->n_inst, 1);
+  k_pt_film<<<gn, kPtNode, 0, c->st>>>(c->inst, c->partial, parts, p64, zh0, nullptr, skip, c->dH, c->n_inst, 1);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t pt_deform_dir64(PtCtx* c, const double* v, const int* skip) {
-  cudaError_t e = pt_deform(c, v, skip, true);
+  int parts = 1, p64 = 1;
+  cudaError_t e = pt_deform(c, v, skip, true, parts, p64, /*direct=*/true);
   if (e != cudaSuccess) return e;
   const dim3 gn((c->NN + kPtNode - 1) / kPtNode, c->n_inst);
-  k_pt_film<<<gn, kPtNode, 0, c->st>>>(c->inst, c->partial, c->ksplit, 1, nullptr, nullptr, skip, c->dH, c->n_inst,
+  k_pt_film<<<gn, kPtNode, 0, c->st>>>(c->inst, c->partial, parts, p64, nullptr, nullptr, skip, c->dH, c->n_inst,
                                        1);
   note_launch();
   return cudaGetLastError();

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "ehl_internal.h"
+#include "fft.h"
 #include "line_kernels.cuh"
 
 namespace ehl {
@@ -51,12 +52,17 @@ struct PtCtx {
   cublasHandle_t blas = nullptr;
   float *Tall = nullptr, *Qf = nullptr, *Df = nullptr;
   int trace = 0;
+  // deformation by the float64 FFT convolution (fft.cu) instead of the direct sum: the film of the
+  // residual and the Krylov products (their inputs vanish on the boundary nodes); the adjoint's
+  // transposed products, whose weights do not, keep the direct sum
+  bool use_fft = false;
+  Fft2 fft;
   std::vector<void*> allocs;
 };
 
 cudaError_t pt_alloc(PtCtx* c, void** p, size_t bytes);
 ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int max_iter, int krylov_dim,
-                   int precision = 0);
+                   int precision = 0, int deform = 0);
 void pt_free(PtCtx* c);
 // state (film, lubricant, faces, residual, block partials) at (P, H0); all [n_inst][ny][nx]
 cudaError_t pt_state(PtCtx* c, const double* P, const double* H0, const double* rough, const int* skip);
