@@ -235,6 +235,12 @@ typedef struct {
                         /*   1: the same discrete convolution through a float64 FFT of     */
                         /*   cyclic length 2^ceil(log2(2 n - 3)) per direction (nx, ny up  */
                         /*   to 2049); the adjoint's products keep the direct sum          */
+  int yline;            /* point contact: 1 adds the y-line stage to the preconditioner:    */
+                        /*   z1 = M_x^-1 v, z = z1 + M_y^-1 (v - J z1), M_x and M_y the     */
+                        /*   bordered PAQIF solves on the x- and y-line bands of the exact  */
+                        /*   Jacobian (the alternating directions of Sec. 3.3.2-3.3.4); one */
+                        /*   more Jacobian product and y-line solve per Krylov vector; 0   */
+                        /*   x-lines only                                                  */
 } ehl_params;
 
 /* Fill *p with the defaults above for dimension `dim` (1). */
@@ -275,6 +281,13 @@ ehl_status ehl_residual(ehl_ctx* ctx, const double* P, const double* H0, const d
  *          are identity rows (active = 1), d_i = max(|dR_i/dP_i|, m_i / 10)
  *          with m_i the largest |entry| of the row's band (the Newton
  *          row scale; the diagonal alone can pass through zero).
+ *  kind 2 (point contact only): the y-line bands of the exact Jacobian,
+ *          band [n_inst][nx-2][ny-2][2 beta + 1] (one system per interior grid
+ *          column, rows along y; the alternating direction of Sec. 3.3.2-3.3.4),
+ *          with the identity rows and active flags of kind 1.
+ * Point contact (dim = 2): kind 1 gives the x-line bands
+ * [n_inst][ny-2][nx-2][2 beta + 1] (one system per interior grid row); kind 0
+ * is line contact only.
  * Asynchronous. */
 ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, int kind,
                              double* band, uint8_t* active);

@@ -214,6 +214,45 @@ def xline_band_exact(pb, P_int, H0, beta):
     return band
 
 
+def yline_band_exact(pb, P_int, H0, beta):
+    """The y-line bands of the exact Jacobian: ``[nx-2, ny-2, 2 beta + 1]``.
+
+    Entry ``[i-1, j-1, beta + l - j]`` is ``dR_ij / dP_il`` (Sec. 3.3.2-3.3.4: the
+    y-line systems of the alternating line splitting, one per grid column i; the
+    paper writes out only the x-line equations, the y-lines follow by symmetry).
+    As in ``xline_band_exact``: the rows ``(i, l + d)`` of column ``(i, l)`` read
+    the film at ``x in [i - 2, i + 1]``, ``y in [l - beta - 1, l + beta + 1]``, so
+    columns 4 apart in x and ``2 beta + 3`` apart in y share one tangent.
+    """
+    s = state(pb, P_int, H0)
+    nx, ny = pb.nx, pb.ny
+    px, py = 4, 2 * beta + 3
+    band = np.zeros((nx - 2, ny - 2, 2 * beta + 1))
+    for cx in range(px):
+        ks = np.arange(1 + cx, nx - 1, px)
+        for cy in range(py):
+            ls = np.arange(1 + cy, ny - 1, py)
+            if len(ks) == 0 or len(ls) == 0:
+                continue
+            dH = np.zeros((nx, ny, 1))
+            dP = np.zeros((nx, ny, 1))
+            K, L = np.meshgrid(ks, ls, indexing="ij")
+            K, L = K.ravel(), L.ravel()
+            dP[K, L, 0] = 1.0
+            if pb.elastic:
+                for ox in range(-2, 2):
+                    for oy in range(-beta - 1, beta + 2):
+                        mx, my = K + ox, L + oy
+                        ok = (mx >= 0) & (mx < nx) & (my >= 0) & (my < ny)
+                        dH[mx[ok], my[ok], 0] = pb.table[np.abs(ox), np.abs(oy)]
+            t = _tangent(pb, s, dH, dP)[:, 0].reshape(nx - 2, ny - 2)
+            for d in range(-beta, beta + 1):
+                rows = L + d  # row j = l + d, entry beta + l - j = beta - d
+                ok = (rows >= 1) & (rows <= ny - 2)
+                band[K[ok] - 1, rows[ok] - 1, beta - d] = t[K[ok] - 1, rows[ok] - 1]
+    return band
+
+
 def rounding_floor(pb, P_int, H0):
     """``1e3`` roundoff units times the largest term entering any ``R_ij``."""
     s = state(pb, P_int, H0)

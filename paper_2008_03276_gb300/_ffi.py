@@ -23,7 +23,7 @@ class EhlParams(ctypes.Structure):
                 ("h_init", ctypes.c_double), ("levels", ctypes.c_int), ("coarse_min_nodes", ctypes.c_int),
                 ("coarse_tol", ctypes.c_double), ("precond_blocks", ctypes.c_int),
                 ("precision", ctypes.c_int), ("graph", ctypes.c_int), ("kappa", ctypes.c_double),
-                ("splitting", ctypes.c_int), ("deform", ctypes.c_int)]
+                ("splitting", ctypes.c_int), ("deform", ctypes.c_int), ("yline", ctypes.c_int)]
 
 
 class EhlCdParams(ctypes.Structure):

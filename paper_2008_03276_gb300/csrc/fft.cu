@@ -174,12 +174,13 @@ int cols_per_cta(int My, int Mx) {
   return c;
 }
 
-cudaError_t fft_attrs(const Fft2& f) {
-  const int rs = (int)(f.v.Mx * sizeof(double2));
-  const int cs = (int)(f.cnt * f.v.My * sizeof(double2));
-  cudaError_t e = cudaFuncSetAttribute(k_fft_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, cs);
+// the kernels' dynamic shared-memory limit is a per-function setting shared by every plan of the
+// process, so it is always raised to the cap (each launch still asks for its own size only)
+cudaError_t fft_attrs() {
+  const int cap = (int)kFftSmemCap;
+  cudaError_t e = cudaFuncSetAttribute(k_fft_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   return e;
 }
 
@@ -221,7 +222,7 @@ cudaError_t fft2_init(Fft2& f, int nx, int ny, int n_inst, void* mem, const doub
   v.ghat = (double*)take((size_t)n_inst * v.My * v.Mx * sizeof(double));
   const int rows = v.My > ny ? v.My : ny;
   f.work = (double2*)take((size_t)n_inst * rows * v.Mx * sizeof(double2));
-  cudaError_t e = fft_attrs(f);
+  cudaError_t e = fft_attrs();
   if (e != cudaSuccess) return e;
   k_fft_twiddles<<<(v.Mx / 2 + 255) / 256, 256, 0, st>>>(v.twx, v.Mx);
   note_launch();

@@ -105,6 +105,7 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   p->kappa = 0.0;
   p->splitting = 0;
   p->deform = 0;
+  p->yline = 0;
 }
 
 static bool point_grid_ok(const ehl_params& p) {
@@ -118,6 +119,7 @@ static bool params_ok(const ehl_params& p) {
          p.L >= 0.0 && p.xb > p.xa && p.alpha > 0.0 && p.p0 > 0.0 && p.z > 0.0 && (p.limiter >= 0 && p.limiter <= 2) &&
          p.kappa >= -1.0 && p.kappa <= 1.0 && p.splitting >= 0 && p.splitting <= 2 &&
          (p.deform == 0 || (p.deform == 1 && p.dim == 2 && fft2_size_ok(p.nx, p.ny))) &&
+         (p.yline == 0 || (p.yline == 1 && p.dim == 2)) &&
          (p.method == 0 || p.method == 1) && p.max_iter >= 1 && p.krylov_dim >= 1 && p.krylov_dim <= 200 &&
          p.tol > 0.0 && isfinite(p.h_init) && isfinite(p.c_h0) && isfinite(p.omega) && isfinite(p.dist_weight) &&
          isfinite(p.switch_eps_h) && p.levels >= -1 && p.coarse_min_nodes >= 5 && p.coarse_tol > 0.0 &&
@@ -370,7 +372,7 @@ static ehl_status create_point(const ehl_params* p, int n_inst, const ehl_params
   ctx->pt = new PtCtx();
   ctx->pt->st = stream;
   if (const char* tr = getenv("EHL_TRACE")) ctx->pt->trace = atoi(tr) > 0 ? atoi(tr) : 0;
-  ehl_status st = pt_init(ctx->pt, insts, p->halfband, p->max_iter, p->krylov_dim, p->precision, p->deform);
+  ehl_status st = pt_init(ctx->pt, insts, p->halfband, p->max_iter, p->krylov_dim, p->precision, p->deform, p->yline);
   // coarse grids: halve the intervals in both directions while both stay even and
   // the coarse grid keeps coarse_min_nodes nodes per direction
   int gx = p->nx, gy = p->ny;
@@ -395,7 +397,7 @@ static ehl_status create_point(const ehl_params* p, int n_inst, const ehl_params
     l->st = stream;
     l->trace = ctx->pt->trace;
     ctx->ptlv.push_back(l);
-    st = pt_init(l, ci, p->halfband, std::min(p->max_iter, kCoarseMaxIter), p->krylov_dim, p->precision, p->deform);
+    st = pt_init(l, ci, p->halfband, std::min(p->max_iter, kCoarseMaxIter), p->krylov_dim, p->precision, p->deform, p->yline);
     double* r = nullptr;
     if (st == EHL_OK && pt_alloc(l, (void**)&r, sizeof(double) * n_inst * (size_t)l->NN) != cudaSuccess) {
       cudaGetLastError();
@@ -672,13 +674,22 @@ static ehl_status ehl_residual_impl(ehl_ctx* ctx, const double* P, const double*
 
 static ehl_status ehl_jacobian_band_impl(ehl_ctx* ctx, const double* P, const double* H0, const double* rough,
                                         int kind, double* band, uint8_t* active) {
-  if (!ctx || !P || !H0 || !band || !active || (kind != 0 && kind != 1)) return EHL_EINVAL;
+  if (!ctx || !P || !H0 || !band || !active || kind < 0 || kind > 2) return EHL_EINVAL;
   if (ctx->pt) {
-    if (kind != 1) return EHL_EINVAL;
-    cudaError_t e = pt_state(ctx->pt, P, H0, rough, nullptr);
-    if (e == cudaSuccess) e = pt_jac_band(ctx->pt, P, band, active, nullptr, nullptr, nullptr);
+    if (kind == 0) return EHL_EINVAL;
+    PtCtx* c = ctx->pt;
+    cudaError_t e = pt_state(c, P, H0, rough, nullptr);
+    if (kind == 1) {
+      if (e == cudaSuccess) e = pt_jac_band(c, P, band, active, nullptr, nullptr, nullptr);
+    } else {
+      // the y-line bands; the x-line bands (into the context's scratch) fix the row scale and the
+      // identity rows
+      if (e == cudaSuccess) e = pt_jac_band(c, P, c->band, active, nullptr, c->dg, nullptr);
+      if (e == cudaSuccess) e = pt_jac_yband(c, P, active, c->dg, band, 0, nullptr);
+    }
     return cuda_status(e);
   }
+  if (kind == 2) return EHL_EINVAL;
   const int bw = 2 * ctx->beta + 1, nmax = ctx->nx_max - 2;
   cudaError_t e = fork(ctx);
   for (Bucket* b : ctx->buckets) {

@@ -471,6 +471,49 @@ __global__ void k_pt_jac_band(const PointInst* __restrict__ inst, PtRow c, const
   act[(size_t)z * n + r] = a ? 1 : 0;
 }
 
+// exact y-line band: system (z, i) (grid column i), row j - 1, columns (i, jc) with |jc - j| <= beta;
+// rows the x-band kernel marked active become identity rows; scale != 0 divides the others by
+// the row scale d of the x-band (the scaled Newton system of the Krylov solve)
+__global__ void k_pt_jac_yband(const PointInst* __restrict__ inst, PtRow c, const double* __restrict__ gtab64,
+                               const double* __restrict__ dg, const uint8_t* __restrict__ act,
+                               const int* __restrict__ skip, int beta, int scale, double* __restrict__ band) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  const PointInst q = inst[z];
+  const int nx = q.nx, ny = q.ny, NN = nx * ny, ni = nx - 2, nj = ny - 2, n = ni * nj;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  PtRow row = c;
+  row.base = (size_t)z * NN;
+  row.h = q.h;
+  row.nx = nx;
+  const int i = r % ni + 1, j = r / ni + 1;
+  const double* T = gtab64 + (size_t)z * NN;
+  const bool el = q.m.elastic != 0;
+  const int bw = 2 * beta + 1;
+  double* out = band + (((size_t)z * ni + (i - 1)) * nj + (j - 1)) * bw;
+  const size_t o = (size_t)z * n + r;
+  if (act[o]) {
+    for (int t = 0; t < bw; ++t) out[t] = (t == beta ? 1.0 : 0.0);
+    return;
+  }
+  const double rd = scale ? 1.0 / dg[o] : 1.0;
+  for (int t = 0; t < bw; ++t) {
+    const int jc = j - beta + t;
+    double v = 0.0;
+    if (jc >= 1 && jc <= ny - 2) {
+      auto dH = [&](int p, int qq) {
+        if (!el) return 0.0;
+        const int a = p > i ? p - i : i - p, b = qq > jc ? qq - jc : jc - qq;
+        return T[(size_t)b * nx + a];
+      };
+      auto zn = [&](int p, int qq) { return (p == i && qq == jc) ? 1.0 : 0.0; };
+      v = row.jv(i, j, dH, zn) * rd;
+    }
+    out[t] = v;
+  }
+}
+
 // (dR/dP) v + (dR/dH0) v_h0 at interior nodes (dH = K v + v_h0 precomputed), 0 on the boundary
 __global__ void k_pt_jv_raw(const PointInst* __restrict__ inst, PtRow c, const double* __restrict__ dH,
                             const double* __restrict__ v, double* __restrict__ out) {
@@ -613,7 +656,7 @@ static PtRow pt_row(PtCtx* c, const double* P) {
 }
 
 ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int max_iter, int krylov_dim,
-                   int precision, int deform) {
+                   int precision, int deform, int yline) {
   const int ni = (int)insts.size();
   c->n_inst = ni;
   c->nx = insts[0].nx;
@@ -669,6 +712,20 @@ ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int 
     ehl_paqif_workspace_size(c->lines, c->nx - 2, beta, 0, &wb);
     A(&c->pq_ws, wb);
     A(&c->fstore, paqif_factor_store_bytes(c->lines, c->nx - 2, beta));
+  }
+  if (ok && yline) {
+    c->yline = 1;
+    c->ylines = ni * (c->nx - 2);
+    size_t wb = 0;
+    ehl_paqif_workspace_size(c->ylines, c->ny - 2, beta, 0, &wb);
+    A(&c->pq_ws_y, wb);
+    A(&c->fstore_y, paqif_factor_store_bytes(c->ylines, c->ny - 2, beta));
+    A((void**)&c->band_y, sizeof(double) * nt * bw);
+    double** yv[] = {&c->rhs_y, &c->sig_y, &c->zHy};
+    for (double** q : yv) A((void**)q, sizeof(double) * nt);
+    double** yp[] = {&c->deny, &c->xiy};
+    for (double** q : yp) A((void**)q, sizeof(double) * ni);
+    A((void**)&c->pq_info_y, sizeof(int) * c->ylines);
   }
   if (!ok) {
     cudaGetLastError();
@@ -764,6 +821,14 @@ cudaError_t pt_jac_band(PtCtx* c, const double* P, double* band, uint8_t* act, d
                         const int* skip) {
   const dim3 g((c->n + 127) / 128, c->n_inst);
   k_pt_jac_band<<<g, 128, 0, c->st>>>(c->inst, pt_row(c, P), c->gtab64, c->R, skip, c->beta, band, act, jh, dg);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t pt_jac_yband(PtCtx* c, const double* P, const uint8_t* act, const double* dg, double* band, int scale,
+                         const int* skip) {
+  const dim3 g((c->n + 127) / 128, c->n_inst);
+  k_pt_jac_yband<<<g, 128, 0, c->st>>>(c->inst, pt_row(c, P), c->gtab64, dg, act, skip, c->beta, scale, band);
   note_launch();
   return cudaGetLastError();
 }

@@ -57,12 +57,19 @@ struct PtCtx {
   // transposed products, whose weights do not, keep the direct sum
   bool use_fft = false;
   Fft2 fft;
+  // y-line stage of the preconditioner (yline = 1): after the bordered x-line solve z1 = M_x^-1 v,
+  // z = z1 + M_y^-1 (v - J z1) with M_y the bordered solve on the y-line bands (grid columns)
+  int yline = 0, ylines = 0;
+  double *band_y = nullptr, *rhs_y = nullptr, *sig_y = nullptr, *zHy = nullptr, *deny = nullptr, *xiy = nullptr;
+  void* pq_ws_y = nullptr;
+  void* fstore_y = nullptr;
+  int* pq_info_y = nullptr;
   std::vector<void*> allocs;
 };
 
 cudaError_t pt_alloc(PtCtx* c, void** p, size_t bytes);
 ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int max_iter, int krylov_dim,
-                   int precision = 0, int deform = 0);
+                   int precision = 0, int deform = 0, int yline = 0);
 void pt_free(PtCtx* c);
 // state (film, lubricant, faces, residual, block partials) at (P, H0); all [n_inst][ny][nx]
 cudaError_t pt_state(PtCtx* c, const double* P, const double* H0, const double* rough, const int* skip);
@@ -70,6 +77,10 @@ cudaError_t pt_finalize(PtCtx* c, int* done, int* iters);
 // exact x-line band Jacobian: band [n_inst][ny-2][nx-2][2 beta + 1], act [n_inst][n]
 cudaError_t pt_jac_band(PtCtx* c, const double* P, double* band, uint8_t* act, double* jh, double* dg,
                         const int* skip);
+// exact y-line band Jacobian: band [n_inst][nx-2][ny-2][2 beta + 1] (one system per grid column),
+// rows active in `act` (from pt_jac_band) identity, the others divided by dg when scale != 0
+cudaError_t pt_jac_yband(PtCtx* c, const double* P, const uint8_t* act, const double* dg, double* band, int scale,
+                         const int* skip);
 cudaError_t pt_jacobian_apply(PtCtx* c, const double* P, const double* H0, const double* rough, const double* v,
                               const double* v_h0, double* out);
 cudaError_t pt_start(PtCtx* c, double* P, double* H0, const double* rough);

@@ -35,6 +35,9 @@ struct PtView {  // device pointers the vector kernels need
   double *phinorm, *den, *rtol, *beta0, *tstep, *zh0, *H0t, *Pt, *znode;
   const uint8_t* act;
   int *gm_k, *gm_conv, *lsdone, *lsphase, *acc;
+  // y-line stage (yline = 1): rhs and solution of the y-line systems (column-major interior
+  // order r_y = (i-1)(ny-2) + (j-1)), their bordered correction zHy (row-major) and den_y, xi_y
+  double *rhs_y, *sig_y, *zHy, *deny, *xiy;
 };
 
 __device__ __forceinline__ double nk_block_sum(double v, double* sh) {
@@ -190,6 +193,84 @@ __global__ void __launch_bounds__(kNB) k_pn_prec3(PtView v, int j) {
     const size_t o = (size_t)z * v.n + r;
     val = v.sigma[o] - v.zh0[z] * v.zH[o];
     v.Z[((size_t)z * v.m + j) * v.n1 + r] = val;
+  }
+  v.znode[(size_t)z * v.NN + t] = val;
+}
+
+// ---- y-line stage of the preconditioner (Sec. 3.3.2-3.3.4: the y-line systems of the alternating
+// splitting): z = z1 + M_y^-1 (v - J z1), M_y the bordered solve on the y-line bands
+__device__ __forceinline__ int pn_ty(int r, int nx, int ny) {  // row-major interior -> column-major
+  return (r % (nx - 2)) * (ny - 2) + r / (nx - 2);
+}
+
+// dst (column-major) = src (row-major) on the interior
+__global__ void __launch_bounds__(kNB) k_pn_ytrans(PtView v, const double* __restrict__ src,
+                                                   double* __restrict__ dst, const int* __restrict__ skip) {
+  const int z = blockIdx.y;
+  if (skip[z]) return;
+  NK_FOR(r, v.n) dst[(size_t)z * v.n + pn_ty(r, v.nx, v.ny)] = src[(size_t)z * v.n + r];
+}
+
+// zHy (row-major) = sig_y (column-major): the y-line solve of the border column
+__global__ void __launch_bounds__(kNB) k_pn_ytrans_back(PtView v, const int* __restrict__ skip) {
+  const int z = blockIdx.y;
+  if (skip[z]) return;
+  NK_FOR(r, v.n) v.zHy[(size_t)z * v.n + r] = v.sig_y[(size_t)z * v.n + pn_ty(r, v.nx, v.ny)];
+}
+
+// den_y = h^2 sum zHy (after k_pn_psum of zHy into slot 0)
+__global__ void __launch_bounds__(kNB) k_pn_yden(PtView v) {
+  const int z = blockIdx.x;
+  if (v.done[z]) return;
+  __shared__ double sh[kNB];
+  const double s = pn_total(v, z, 0, sh);
+  if (threadIdx.x == 0) {
+    const double h = v.inst[z].h;
+    v.deny[z] = fabs(h * h * s) > 1e-300 ? h * h * s : 1e-300;
+  }
+}
+
+// rhs_y = (V_j - J z1)[0:n] in column-major order (w holds J z1)
+__global__ void __launch_bounds__(kNB) k_pn_yrhs(PtView v, int j) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  const double* Vj = v.V + ((size_t)z * (v.m + 1) + j) * v.n1;
+  const double* wz = v.w + (size_t)z * v.n1;
+  NK_FOR(r, v.n) v.rhs_y[(size_t)z * v.n + pn_ty(r, v.nx, v.ny)] = Vj[r] - wz[r];
+}
+
+// xi_y = (h^2 sum sig_y - (V_j[n] - w[n])) / den_y (after k_pn_psum of sig_y into slot 0); the
+// border component of Z_j and of the deformation input grows by xi_y
+__global__ void __launch_bounds__(kNB) k_pn_yprec2(PtView v, int j) {
+  const int z = blockIdx.x;
+  if (v.skip[z]) return;
+  __shared__ double sh[kNB];
+  const double s = pn_total(v, z, 0, sh);
+  if (threadIdx.x == 0) {
+    const double h = v.inst[z].h;
+    const double* Vj = v.V + ((size_t)z * (v.m + 1) + j) * v.n1;
+    const double r1n = Vj[v.n] - v.w[(size_t)z * v.n1 + v.n];
+    const double xi = (h * h * s - r1n) / v.deny[z];
+    v.xiy[z] = xi;
+    v.zh0[z] += xi;
+    v.Z[((size_t)z * v.m + j) * v.n1 + v.n] += xi;
+  }
+}
+
+// Z_j += sig_y - xi_y zHy on the interior; the nodal copy for the deformation (0 on the boundary)
+__global__ void __launch_bounds__(kNB) k_pn_yprec3(PtView v, int j) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= v.NN) return;
+  const int jj = t / v.nx, ii = t % v.nx;
+  double val = 0.0;
+  if (ii >= 1 && ii <= v.nx - 2 && jj >= 1 && jj <= v.ny - 2) {
+    const int r = (jj - 1) * (v.nx - 2) + (ii - 1);
+    const size_t o = (size_t)z * v.n + r;
+    double* Zj = v.Z + ((size_t)z * v.m + j) * v.n1;
+    val = Zj[r] + v.sig_y[(size_t)z * v.n + pn_ty(r, v.nx, v.ny)] - v.xiy[z] * v.zHy[o];
+    Zj[r] = val;
   }
   v.znode[(size_t)z * v.NN + t] = val;
 }
@@ -511,6 +592,11 @@ static PtView pt_view(PtCtx* c, const int* skip) {
   v.lsdone = c->lsdone;
   v.lsphase = c->lsphase;
   v.acc = c->acc;
+  v.rhs_y = c->rhs_y;
+  v.sig_y = c->sig_y;
+  v.zHy = c->zHy;
+  v.deny = c->deny;
+  v.xiy = c->xiy;
   return v;
 }
 
@@ -530,6 +616,22 @@ static cudaError_t pn_paqif(PtCtx* c, const double* rhs, double* x, bool factor)
   // double-float sweeps at every precision: with float32 x-line solves the 2-D Newton
   // iteration stalls (C4: 60 steps without convergence, against 14 in double-float)
   return factor ? launch_paqif_factor(L, c->fstore, c->st) : launch_paqif_resolve(L, c->fstore, c->st);
+}
+
+static cudaError_t pn_paqif_y(PtCtx* c, bool factor) {
+  PaqifLaunch L;
+  L.n_sys = c->ylines;
+  L.n = c->ny - 2;
+  L.beta = c->beta;
+  L.mode = 0;
+  L.band = c->band_y;
+  L.rhs = c->rhs_y;
+  L.act = nullptr;
+  L.stack = c->pq_ws_y;
+  L.x = c->sig_y;
+  L.iters = nullptr;
+  L.info = c->pq_info_y;
+  return factor ? launch_paqif_factor(L, c->fstore_y, c->st) : launch_paqif_resolve(L, c->fstore_y, c->st);
 }
 
 static bool pn_all(PtCtx* c, const int* a, const int* b, cudaError_t& e) {
@@ -556,6 +658,21 @@ cudaError_t pt_nk_step(PtCtx* c, double* P, double* H0, const double* rough) {
   note_launch();
   k_pn_scale<<<gv, kNB, 0, c->st>>>(vd, c->V, (size_t)(c->m + 1) * (c->n + 1), 0, c->done);
   note_launch();
+  if (c->yline) {
+    // y-line bands of the scaled system, their factorization solving for the border column
+    e = pt_jac_yband(c, P, c->act, c->dg, c->band_y, 1, c->done);
+    if (e != cudaSuccess) return e;
+    k_pn_ytrans<<<gv, kNB, 0, c->st>>>(vd, c->rhs, c->rhs_y, c->done);
+    note_launch();
+    e = pn_paqif_y(c, true);  // sig_y = B_y^-1 (dR/dH0)/d
+    if (e != cudaSuccess) return e;
+    k_pn_ytrans_back<<<gv, kNB, 0, c->st>>>(vd, c->done);
+    note_launch();
+    k_pn_psum<<<gv, kNB, 0, c->st>>>(vd, c->zHy, (size_t)c->n, 0, c->done);
+    note_launch();
+    k_pn_yden<<<ni, kNB, 0, c->st>>>(vd);
+    note_launch();
+  }
   e = pn_paqif(c, c->rhs, c->sigma, true);  // factor; sigma = B^-1 (dR/dH0)/d
   if (e != cudaSuccess) return e;
   k_pn_psum<<<gv, kNB, 0, c->st>>>(vd, c->sigma, (size_t)c->n, 0, c->done);
@@ -575,7 +692,28 @@ cudaError_t pt_nk_step(PtCtx* c, double* P, double* H0, const double* rough) {
     note_launch();
     k_pn_prec3<<<gn, 256, 0, c->st>>>(vs, j);
     note_launch();
-    // dH = K z + xi: the double-float deformation of the Krylov vector
+    if (c->yline) {
+      // w = J z1, then Z_j = z1 + M_y^-1 (V_j - w)
+      e = pt_deform_dir(c, c->znode, c->zh0, c->skip);
+      if (e != cudaSuccess) return e;
+      k_pn_jv<<<gv, kNB, 0, c->st>>>(vs, q, j);
+      note_launch();
+      k_pn_psum<<<gv, kNB, 0, c->st>>>(vs, c->Z + (size_t)j * (c->n + 1), (size_t)c->m * (c->n + 1), 0, c->skip);
+      note_launch();
+      k_pn_force<<<ni, kNB, 0, c->st>>>(vs);
+      note_launch();
+      k_pn_yrhs<<<gv, kNB, 0, c->st>>>(vs, j);
+      note_launch();
+      e = pn_paqif_y(c, false);
+      if (e != cudaSuccess) return e;
+      k_pn_psum<<<gv, kNB, 0, c->st>>>(vs, c->sig_y, (size_t)c->n, 0, c->skip);
+      note_launch();
+      k_pn_yprec2<<<ni, kNB, 0, c->st>>>(vs, j);
+      note_launch();
+      k_pn_yprec3<<<gn, 256, 0, c->st>>>(vs, j);
+      note_launch();
+    }
+    // dH = K z + xi: the deformation of the Krylov vector
     e = pt_deform_dir(c, c->znode, c->zh0, c->skip);
     if (e != cudaSuccess) return e;
     k_pn_jv<<<gv, kNB, 0, c->st>>>(vs, q, j);

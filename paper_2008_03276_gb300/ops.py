@@ -170,9 +170,18 @@ class Context:
 
     def jacobian_band(self, P, H0, kind=0, rough=None):
         """Band Jacobian: [n_inst][nx-2][2 beta + 1] (line) or the x-line bands
-        [n_inst][ny-2][nx-2][2 beta + 1] of the exact Jacobian (point, kind 1)."""
+        [n_inst][ny-2][nx-2][2 beta + 1] of the exact Jacobian (point, kind 1), or its
+        y-line bands [n_inst][nx-2][ny-2][2 beta + 1] (point, kind 2; act stays [ny-2][nx-2])."""
         self._check(P, H0, rough)
         rows = (self.nx - 2,) if self.dim == 1 else (self.ny - 2, self.nx - 2)
+        if self.dim == 2 and kind == 2:
+            alloc = torch.empty
+            band = alloc((self.n_inst, self.nx - 2, self.ny - 2, 2 * self.beta + 1), dtype=torch.float64,
+                         device=P.device)
+            act = alloc((self.n_inst,) + rows, dtype=torch.uint8, device=P.device)
+            code = self._lib.ehl_jacobian_band(self._h, _ptr(P), _ptr(H0), _ptr(rough), kind, _ptr(band), _ptr(act))
+            _ffi.check(code, "ehl_jacobian_band")
+            return band, act
         alloc = torch.zeros if self.ragged else torch.empty
         band = alloc((self.n_inst,) + rows + (2 * self.beta + 1,), dtype=torch.float64, device=P.device)
         act = alloc((self.n_inst,) + rows, dtype=torch.uint8, device=P.device)

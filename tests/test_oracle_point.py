@@ -165,3 +165,20 @@ def test_xline_band_is_the_band_of_the_dense_exact_jacobian(n, beta, limiter):
                 k = i + d
                 want = J[i * m + j, k * m + j] if 0 <= k < m else 0.0
                 assert band[j, i, beta + d] == want
+
+
+@pytest.mark.parametrize("n,beta,limiter", [(17, 2, "minmod"), (21, 3, "vanleer")])
+def test_yline_band_is_the_band_of_the_dense_exact_jacobian(n, beta, limiter):
+    pb = pr.PointProblem(n, n, 20.0, 10.0, limiter=limiter)
+    rng = np.random.default_rng(n + 1)
+    P = pb.hertz() * (1 + 0.05 * rng.standard_normal(pb.n)).clip(0)
+    H0 = pb.h0_for_min_film(P, 0.1)
+    J, _ = pr.jacobian_exact(pb, P, H0)
+    band = pr.yline_band_exact(pb, P, H0, beta)
+    m = n - 2
+    for i in range(m):
+        for j in range(m):
+            for d in range(-beta, beta + 1):
+                l = j + d
+                want = J[i * m + j, i * m + l] if 0 <= l < m else 0.0
+                assert band[i, j, beta + d] == want
