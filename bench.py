@@ -287,6 +287,8 @@ def run_ours(args):
     # end to end through the public API with pinned host buffers, copies inside the timed region
     e2e_b = None
     if ctx is not None:
+        rough_p = torch.zeros((B, EHL["N"]), dtype=torch.float64).pin_memory()  # smooth surfaces, from the host
+        rough_d = torch.empty((B, EHL["N"]), dtype=torch.float64, device=dev)
         P_p = torch.empty((B, EHL["N"]), dtype=torch.float64).pin_memory()
         H0_p = torch.empty(B, dtype=torch.float64).pin_memory()
         it_p = torch.empty(B, dtype=torch.int32).pin_memory()
@@ -296,7 +298,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
-            P, H0, iters, res, _ = ctx.solve(check=False)
+            rough_d.copy_(rough_p, non_blocking=True)
+            P, H0, iters, res, _ = ctx.solve(rough=rough_d, check=False)
             P_p.copy_(P, non_blocking=True)
             H0_p.copy_(H0, non_blocking=True)
             it_p.copy_(iters, non_blocking=True)
@@ -374,7 +377,9 @@ def run_ours(args):
                      "frac": round(gbs / hbm, 4), "traffic": paqif_traffic(),
                      "kernel": "paqif4_kernel<4> (leg A)", "peak_source": src, "issue": issue},
         "e2e": {"value": round(job_rate(world, B, e2e_b), 3) if e2e_b else None, "unit": "converged solves/s",
-                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": B * (EHL["N"] + 1 + 2) * 8 + B * 4,
+                "h2d_bytes_per_step": B * EHL["N"] * 8, "d2h_bytes_per_step": B * (EHL["N"] + 1 + 2) * 8 + B * 4,
+                "inputs": "the surface roughness of every instance (zeros: smooth surfaces) copied from pinned "
+                          "host memory each step; the Hertzian start is built on the device from the parameters",
                 "paqif_gbs": round(job_rate(world, nbytes, e2e_a) / 1e9, 2),
                 "paqif_h2d_bytes_per_step": band_h.nbytes + rhs_h.nbytes, "paqif_d2h_bytes_per_step": rhs_h.nbytes},
         "gpu_launches": launches,
@@ -383,6 +388,8 @@ def run_ours(args):
     }
     if world == 1 and not args.no_configs:
         line["configs"] = config_legs(ops, inputs, torch, dev, paqif=(band, rhs))
+        c3 = line["configs"].get("C3", {})
+        line["config"]["c3_ragged_batch_solves_per_s"] = c3.get("solves_per_s")
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(band_h, rhs_h, budget_s=args.cpu_seconds)
     return line
@@ -494,24 +501,43 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
             d["H_rel_err_vs_plain"] = float((H - Href).abs().max() / Href.abs().max())
         res["C3" if prec == 0 else "C3_mixed"] = d
         del ctx
-    # C4: point contact 257 x 257, M = 100, L = 10, minmod, beta 2
+    # C4: point contact 257 x 257, M = 100, L = 10, minmod, beta 2: the direct-sum deformation in
+    # float64 / double-float (the paper's), with the Krylov products as float32 GEMMs, and the same
+    # convolution through the float64 FFT
     Href = None
-    for prec in (0, 2):
+    for key, prec, deform in (("C4", 0, 0), ("C4_mixed", 2, 0), ("C4_fft", 0, 1)):
         p = ops.default_params(2, nx=257, ny=257, M=100.0, L=10.0, limiter=0, halfband=2, method=1, tol=1e-8,
-                               max_iter=60, coarse_min_nodes=33, precision=prec)
+                               max_iter=60, coarse_min_nodes=33, precision=prec, deform=deform)
         ctx = ops.Context(p)
-        ms, out = _timed(torch, lambda: ctx.solve(check=False), warm=0)
+        ms, out = _timed(torch, lambda: ctx.solve(check=False), warm=0 if deform == 0 else 1)
         d = dict(workload="point contact 257x257, M=100, L=10, minmod, beta=2 (x-line PAQIF preconditioner), "
-                          "tol 1e-8, nested 33-65-129-257", precision=PRECISION[prec], ms=round(ms, 1),
-                 solves_per_s=round(1e3 / ms, 4))
+                          "tol 1e-8, nested 33-65-129-257",
+                 precision=PRECISION[prec], deformation=("float64 FFT convolution (512 x 512 cyclic)" if deform
+                                                         else "direct sum"),
+                 ms=round(ms, 1), solves_per_s=round(1e3 / ms, 4))
         d.update(summary(out[2], out[3], out[4], 1e-8))
         _, H, _ = ctx.residual(out[0], out[1])
         if Href is None:
             Href = H
         else:
             d["H_rel_err_vs_plain"] = float((H - Href).abs().max() / Href.abs().max())
-        res["C4" if prec == 0 else "C4_mixed"] = d
+        res[key] = d
         del ctx
+    # C1 with van Leer's kappa = 1/3 scheme (limiter 2), Newton-Krylov
+    p = ops.default_params(1, nx=129, M=20.0, L=10.0, limiter=2, kappa=1.0 / 3.0, halfband=2, method=1, tol=1e-8,
+                           max_iter=60)
+    ctx = ops.Context(p)
+    ms, out = _timed(torch, lambda: ctx.solve(check=False), reps=5)
+    d = dict(workload="line N=129, M=20, L=10, kappa-scheme kappa=1/3, beta=2, 1 instance, tol 1e-8",
+             method="Newton-Krylov", ms=round(ms, 3), solves_per_s=round(1e3 / ms, 2))
+    d.update(summary(out[2], out[3], out[4], 1e-8))
+    res["C1_kappa_1/3"] = d
+    del ctx
+    # the convection-diffusion workload of the line splittings (Sec. 3.1, Sec. 6)
+    try:
+        res.update(cd_legs(ops, torch, dev))
+    except Exception as e:
+        res["CD"] = {"error": f"{type(e).__name__}: {e}"}
     # C5: adjoint, N = 1025, M = 50, L = 10, batch 64, roughness 0.1 sin(2 pi X/0.25) + field (0.05, 0.1)
     N, n = 1025, 64
     X = np.linspace(-4.5, 1.5, N)
@@ -531,9 +557,62 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
     rel = out[2].cpu().numpy()
     res["C5"] = dict(workload="adjoint of H_min w.r.t. roughness and (M, L): line N=1025, M=50, L=10, van Leer, "
                               "beta=8, batch 64, roughness 0.1 sin(2 pi X/0.25) + GRF(0.05, 0.1), seeds 2..65",
-                     ms=round(ms, 2), gradients_per_s=round(n * 1e3 / ms, 2), forward_converged=int(conv.sum()),
+                     ms=round(ms, 2), gradients_per_s=round(int(conv.sum()) * 1e3 / ms, 2),
+                     gradients_per_s_note="gradients of the instances whose forward solve converged (to 1e-8), "
+                                          "over the time of the batch's adjoint call",
+                     forward_converged=int(conv.sum()),
                      contact_instances=int(np.sum(H.min(dim=1).values.cpu().numpy() <= 0.0)),
                      adjoint_relres_le_1e_8=int(np.sum(rel[conv] <= 1e-8)))
+    return res
+
+
+def cd_bytes(n, sweeps):
+    """Algorithmic bytes of `sweeps` all-lines sweeps on an n x n grid: per sweep u and f read for
+    the residual, the right-hand sides written and read by the line solves, the changes written
+    and read, u read and written by the update (float64 each)."""
+    return sweeps * 8 * 8 * n * n
+
+
+def cd_legs(ops, torch, dev):
+    """Convection-diffusion workload: u = x^4 + y^4 on [-1, 1]^2, eps = 1e-6, a = 1, b = 0,
+    kappa = 0, Ls0: all x-lines per sweep at n = 1025 (the data-parallel order), and the paper's
+    line-by-line order at n = 129."""
+    res = {}
+    for key, n, order, sweeps in (("CD_all_lines_1025", 1025, "jacobi", 20), ("CD_lexicographic_129", 129,
+                                                                             "lexicographic", 10)):
+        x = torch.linspace(-1.0, 1.0, n, dtype=torch.float64, device=dev)
+        Y, X = torch.meshgrid(x, x, indexing="ij")  # [y][x]
+        exact = X**4 + Y**4
+        f = (4 * X**3 - 1e-6 * 12 * (X**2 + Y**2)).contiguous()[None]
+        u0 = exact.clone()
+        u0[1:-1, 1:-1] = 0.0
+        p = ops.cd_params(n, a=1.0, b=0.0, eps=1e-6, kappa=0.0, splitting="Ls0", order=order)
+        ws = torch.empty(ops.cd_workspace_size(p, 1), dtype=torch.uint8, device=dev)
+        u = u0[None].clone()
+        holder = {}
+
+        def run():
+            u.copy_(u0[None])
+            holder["h"], holder["i"] = ops.cd_relax(p, u, f, sweeps, workspace=ws)
+
+        n0 = ops.kernel_launches()
+        ms, _ = _timed(torch, run, reps=3)
+        launches = (ops.kernel_launches() - n0) // 4
+        r0 = float(ops.cd_residual(p, u0[None].contiguous(), f)[1][0])
+        hist = holder["h"][:, 0].cpu().numpy()
+        d = dict(workload=f"convection-diffusion n={n}x{n}, u=x^4+y^4, eps=1e-6, a=1, b=0, kappa=0, Ls0, "
+                          f"{'all x-lines per sweep' if order == 'jacobi' else 'x-lines one after another'}, "
+                          f"{sweeps} sweeps",
+                 ms=round(ms, 3), sweeps_per_s=round(sweeps * 1e3 / ms, 1), launches_per_call=int(launches),
+                 residual_decay=[float(f"{v / r0:.3e}") for v in hist],
+                 info_all_zero=bool((holder["i"] == 0).all().item()),
+                 max_error_vs_exact=float((u[0] - exact).abs().max()))
+        if order == "jacobi":
+            gbs = cd_bytes(n, sweeps) / (ms * 1e-3) / 1e9
+            hbm, src = peaks()
+            d["gbs"] = round(gbs, 1)
+            d["frac_of_measured_hbm"] = round(gbs / hbm, 4)
+        res[key] = d
     return res
 
 
