@@ -219,6 +219,10 @@ typedef struct {
                         /*   block-Toeplitz structure of the 2-D kernel                    */
   int graph;            /* line contact, method 1: 1 = each Newton step is one CUDA graph  */
                         /*   launch (captured once, replayed; one host check per step);    */
+                        /*   2 = the whole iteration of each grid is one graph launch: the  */
+                        /*   Newton, GMRES and line-search loops run as device-side while   */
+                        /*   loops whose conditions the kernels set from the instances'     */
+                        /*   flags (no host round trip inside a grid; precision 0 only);   */
                         /*   0 = launched kernel by kernel with early exits (default)      */
   double kappa;         /* kappa of limiter 2, -1..1 (0: Fromm, 1/3: third-order upwind    */
                         /*   biased, -1: second-order upwind)                              */

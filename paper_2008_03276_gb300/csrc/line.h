@@ -11,6 +11,11 @@
 
 namespace ehl {
 
+// kernels a device-driven solve graph holds outside its loops and in each loop body
+struct SolveGraphCounts {
+  long long fixed = 0, newton = 0, krylov = 0, trial = 0;
+};
+
 struct LineCtx {
   int n_inst = 0, N = 0, n = 0, beta = 2, method = 0, max_iter = 0, krylov_dim = 30;
   cudaStream_t st = nullptr;
@@ -51,6 +56,9 @@ struct LineCtx {
   // line search of the last Newton step evaluated and accepted it there
   bool state_current = false;
   cudaGraphExec_t graph = nullptr;
+  int graph_mode = 0;                    // 0 host-driven, 1 one Newton step per graph, 2 the whole solve
+  cudaStream_t gs1 = nullptr, gs2 = nullptr;  // mode 2: streams the loop bodies are captured on
+  SolveGraphCounts gcounts;
   const double *g_P = nullptr, *g_H0 = nullptr, *g_rough = nullptr;  // pointers the graph was captured with
   long long graph_launches = 0;
 };
@@ -86,6 +94,14 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
 // line-search trials first_trial.. after a graph replay, for instances still searching
 cudaError_t line_nk_finish(LineCtx* c, double* P, double* H0, const double* rough, int first_trial);
 constexpr int kGraphTrials = 6;
+// Graph mode 2: the whole iteration of one grid (Newton steps, their GMRES and line-search loops)
+// captured as one graph with device-side while-loops.  Captured on c->st (which must be capturing
+// when called); s1, s2 are streams of the same device for the loop bodies.  Counts hold the kernels
+// captured outside the loops and in each loop body, to count the kernels a replay runs.
+cudaError_t line_nk_capture_solve(LineCtx* c, double* P, double* H0, const double* rough, cudaStream_t s1,
+                                  cudaStream_t s2, SolveGraphCounts& n);
+long long line_nk_graph_launches(const SolveGraphCounts& n, const int* loop_host);
+const int* line_nk_loop_counters(LineCtx* c);
 // Adjoint of a converged state (line_adjoint.cu): gradients of an objective J(P, H, H0) given
 // its partials gP, gH ([n_inst][N], nullable) and gH0 ([n_inst], nullable) with respect to the
 // roughness (grad_rough [n_inst][N], nullable) and the Moes parameters (grad_ML [n_inst][2],

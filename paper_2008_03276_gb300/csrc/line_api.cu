@@ -124,7 +124,7 @@ static bool params_ok(const ehl_params& p) {
          p.tol > 0.0 && isfinite(p.h_init) && isfinite(p.c_h0) && isfinite(p.omega) && isfinite(p.dist_weight) &&
          isfinite(p.switch_eps_h) && p.levels >= -1 && p.coarse_min_nodes >= 5 && p.coarse_tol > 0.0 &&
          p.precond_blocks >= 1 && p.precond_blocks <= 4096 && p.precision >= 0 && p.precision <= 4 &&
-         (p.graph == 0 || p.graph == 1);
+         (p.graph == 0 || p.graph == 1 || (p.graph == 2 && p.precision == 0));
 }
 
 static LineInst make_inst(const ehl_params& p) {
@@ -164,6 +164,9 @@ static void free_all(LineCtx* c) {
   line_mixed_free(c);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   c->graph = nullptr;
+  if (c->gs1) cudaStreamDestroy(c->gs1);
+  if (c->gs2) cudaStreamDestroy(c->gs2);
+  c->gs1 = c->gs2 = nullptr;
 }
 
 static void free_bucket(Bucket* b) {
@@ -253,6 +256,7 @@ static ehl_status init_line(LineCtx* c, const std::vector<LineInst>& insts, int 
   if (e == cudaSuccess && c->method == 1) e = line_mixed_init(c, p.precision);
   if (e == cudaSuccess) e = paqif_prepare(c->beta);  // no attribute calls inside a graph capture
   c->use_graph = c->method == 1 && p.graph == 1;
+  c->graph_mode = c->method == 1 ? p.graph : 0;
   if (e != cudaSuccess) {
     cudaGetLastError();
     return EHL_ECUDA;
@@ -458,7 +462,7 @@ static ehl_status ehl_create_impl(const ehl_params* p, int n_inst, const ehl_par
   ctx->st = (cudaStream_t)stream;
   ctx->direct = sizes.size() == 1;
   // a graph cannot be captured on the legacy default stream the caller may pass
-  ctx->own_streams = !ctx->direct || (p->graph == 1 && p->method == 1);
+  ctx->own_streams = !ctx->direct || (p->graph >= 1 && p->method == 1);
   for (size_t q = 0; q < sizes.size(); ++q) {
     Bucket* b = new Bucket();
     ctx->buckets.push_back(b);
@@ -788,6 +792,53 @@ static cudaError_t iterate_graph(LineCtx* c, const double* rough, std::vector<in
   return e;
 }
 
+// Graph mode 2: the whole iteration of this grid as one graph with device-side loops (Newton
+// steps, GMRES, line search), captured once per (P, H0, rough) and launched once per solve; the
+// host reads the done flags and the loop totals afterwards.
+static cudaError_t iterate_device_graph(LineCtx* c, const double* rough, std::vector<int>& hdone) {
+  cudaError_t e = cudaSuccess;
+  if (!c->gs1) {
+    e = cudaStreamCreateWithFlags(&c->gs1, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->gs2, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  if (!c->graph || c->g_P != c->Pw || c->g_H0 != c->H0w || c->g_rough != rough) {
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    const unsigned long long l0 = thread_launches();
+    e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    SolveGraphCounts n;
+    const cudaError_t es = line_nk_capture_solve(c, c->Pw, c->H0w, rough, c->gs1, c->gs2, n);
+    e = cudaStreamEndCapture(c->st, &g);
+    add_launches(-(long long)(thread_launches() - l0));  // captured, not run
+    if (es != cudaSuccess) e = es;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph = nullptr;
+      cudaGetLastError();
+      return e;
+    }
+    c->gcounts = n;
+    c->g_P = c->Pw;
+    c->g_H0 = c->H0w;
+    c->g_rough = rough;
+  }
+  int loops[8] = {0};
+  e = cudaGraphLaunch(c->graph, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(loops, line_nk_loop_counters(c), sizeof(loops), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hdone.data(), c->done, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e == cudaSuccess) add_launches(line_nk_graph_launches(c->gcounts, loops));
+  return e;
+}
+
 // Outer iterations of one LineCtx from (c->Pw, c->H0w) until every instance is
 // done or max_iter; ends with the residual at the returned iterate and the
 // done flags in hdone.
@@ -799,6 +850,7 @@ static cudaError_t iterate(LineCtx* c, const double* rough, std::vector<int>& hd
   if (e == cudaSuccess) e = cudaMemsetAsync(c->best, 0x7f, sizeof(double) * c->n_inst, c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stall, 0, sizeof(int) * c->n_inst, c->st);
   hdone.assign(c->n_inst, 0);
+  if (e == cudaSuccess && c->method == 1 && c->graph_mode == 2) return iterate_device_graph(c, rough, hdone);
   if (e == cudaSuccess && c->method == 1 && c->use_graph) return iterate_graph(c, rough, hdone);
   const int check_every = 8;
   for (int it = 0; it < c->max_iter && e == cudaSuccess; ++it) {

@@ -26,6 +26,7 @@
 namespace ehl {
 
 constexpr int kNkBlock = 256;
+constexpr int kLoopSlots = 8;  // NkBuf::loop: newton, krylov, trial, krylov total, trial total
 
 struct NkBuf {
   int m = 0, n1 = 0;
@@ -37,6 +38,9 @@ struct NkBuf {
   int *gm_k = nullptr, *gm_conv = nullptr, *lsdone = nullptr, *skip = nullptr;
   int* lsphase = nullptr;  // line search: 0 projected trials (P_t >= 0), 1 unprojected
   void* fstore = nullptr;  // PAQIF factor store of the current preconditioner
+  // device-driven solve: loop counters (Newton step, Krylov index, line-search trial) and the
+  // totals of Krylov iterations and trials over the solve
+  int* loop = nullptr;
 };
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -131,11 +135,13 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_border(const LineInst* __restri
 }
 
 // z_j = M^-1 v_j from z1 = Jb^-1 v_j[0:n]: xi = (h sum z1 - v_j[n]) / den, z = z1 - xi zH
+// (jd != null: the Krylov index is read from device memory, the loop counter of a device-driven solve)
 __global__ void __launch_bounds__(kNkBlock) k_nk_prec(const LineInst* __restrict__ inst, NkBuf b, int j,
                                                       const double* __restrict__ sigma, const int* __restrict__ skip,
-                                                      int N) {
+                                                      int N, const int* __restrict__ jd) {
   const int z = blockIdx.x;
   if (skip[z]) return;
+  if (jd) j = *jd;
   __shared__ double sh[kNkBlock];
   const int n = N - 2, n1 = n + 1;
   double s = 0.0;
@@ -254,9 +260,10 @@ __global__ void k_line_jv_raw(const LineInst* __restrict__ inst, JvArgs q, doubl
 // Arnoldi step j with modified Gram-Schmidt, Givens update, convergence test
 __global__ void __launch_bounds__(kNkBlock) k_nk_arnoldi(const LineInst* __restrict__ inst, NkBuf b, int j,
                                                          const int* __restrict__ skip, double* __restrict__ rhs,
-                                                         int N) {
+                                                         int N, const int* __restrict__ jd) {
   const int z = blockIdx.x;
   if (skip[z]) return;
+  if (jd) j = *jd;
   __shared__ double sh[kNkBlock];
   const int n = N - 2, n1 = n + 1, m = b.m;
   double* w = b.w + (size_t)z * n1;
@@ -464,6 +471,7 @@ cudaError_t line_nk_alloc(LineCtx* c) {
             {(void**)&b->lsdone, sizeof(int) * ni},
             {(void**)&b->lsphase, sizeof(int) * ni},
             {(void**)&b->skip, sizeof(int) * ni},
+            {(void**)&b->loop, sizeof(int) * kLoopSlots},
             {(void**)&b->fstore, paqif_factor_store_bytes(ni * c->pq_parts, c->n / c->pq_parts, c->beta)}};
   for (auto& x : al) {
     cudaError_t e = ctx_alloc(c, x.p, x.bytes);
@@ -573,14 +581,14 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
     note_launch();
     e = paqif_on(c, c->rhs, c->sigma, false);
     if (e != cudaSuccess) return e;
-    k_nk_prec<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, b.skip, N);
+    k_nk_prec<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, b.skip, N, nullptr);
     note_launch();
     e = line_krylov_deform(c, b.znode, b.zh0, b.skip);
     if (e != cudaSuccess) return e;
     JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, b.znode};
     k_nk_jv<<<gn, 256, 0, c->st>>>(c->inst, b, q, c->act, b.skip, N);
     note_launch();
-    k_nk_arnoldi<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, b.skip, c->rhs, N);
+    k_nk_arnoldi<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, b.skip, c->rhs, N, nullptr);
     note_launch();
     if (!c->capturing && (j + 1) % 8 == 0 && j + 1 < b.m) {
       if (all_set(c, c->done, b.gm_conv, e)) break;
@@ -625,5 +633,181 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
   }
   return cudaGetLastError();
 }
+
+// ===================================================== device-driven solve (graph mode 2)
+// The outer Newton iteration, the GMRES iteration and the line search run as while-loops of one
+// CUDA graph: each loop's condition is set on the device (cudaGraphSetConditional) by k_nk_loop
+// from the instances' done / converged / accepted flags and an iteration cap, so a whole solve
+// of a grid is one graph launch with no host round trip.
+
+// any instance with done[z] == 0 and other[z] == 0 (block-wide)
+__device__ __forceinline__ bool nk_any_active(const int* done, const int* other, int ni) {
+  int a = 0;
+  for (int z = threadIdx.x; z < ni && !a; z += blockDim.x) a = !done[z] && !(other && other[z]);
+  return __syncthreads_or(a) != 0;
+}
+
+// next = 0: counter = 0 (before the loop); next = 1: counter += 1 (end of a pass), total += 1.
+// The loop continues while counter < cap and some instance is active.
+__global__ void k_nk_loop(cudaGraphConditionalHandle h, int* __restrict__ counter, int* __restrict__ total, int cap,
+                          int next, const int* __restrict__ done, const int* __restrict__ other, int ni) {
+  const int c = next ? *counter + 1 : 0;
+  const bool act = nk_any_active(done, other, ni);  // a block barrier: every thread has read *counter
+  if (threadIdx.x == 0) {
+    *counter = c;
+    if (next && total) *total += 1;
+    cudaGraphSetConditional(h, (c < cap && act) ? 1u : 0u);
+  }
+}
+
+namespace {
+
+cudaError_t nk_loop(LineCtx* c, cudaGraphConditionalHandle h, int slot, int total_slot, int cap, int next,
+                    const int* other) {
+  NkBuf& b = *(NkBuf*)c->nk;
+  k_nk_loop<<<1, 256, 0, c->st>>>(h, b.loop + slot, total_slot >= 0 ? b.loop + total_slot : nullptr, cap, next,
+                                  c->done, other, c->n_inst);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// A while-node appended to the graph captured on `outer`: `start` (launched on outer) sets the
+// first condition, the body is captured from what `body` launches on `inner`; c->st follows.
+template <class Start, class Body>
+cudaError_t capture_while(LineCtx* c, cudaStream_t outer, cudaStream_t inner, Start start, Body body,
+                          long long* body_launches) {
+  cudaStreamCaptureStatus stt;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(outer, &stt, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  if (stt != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphConditionalHandle h = 0;
+  e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+  if (e != cudaSuccess) return e;
+  c->st = outer;
+  e = start(h);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamGetCaptureInfo(outer, &stt, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t bg = p.conditional.phGraph_out[0];
+  e = cudaStreamUpdateCaptureDependencies(outer, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(inner, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  c->st = inner;
+  const unsigned long long l0 = thread_launches();
+  const cudaError_t eb = body(h);
+  if (body_launches) *body_launches = (long long)(thread_launches() - l0);
+  cudaGraph_t out = nullptr;
+  e = cudaStreamEndCapture(inner, &out);
+  c->st = outer;
+  return eb != cudaSuccess ? eb : e;
+}
+
+}  // namespace
+
+cudaError_t line_nk_capture_solve(LineCtx* c, double* P, double* H0, const double* rough, cudaStream_t s1,
+                                  cudaStream_t s2, SolveGraphCounts& n) {
+  NkBuf& b = *(NkBuf*)c->nk;
+  const int ni = c->n_inst, N = c->N;
+  const cudaStream_t s0 = c->st;
+  const dim3 gn((N + 255) / 256, ni);
+  c->capturing = true;
+  cudaError_t e = cudaSuccess;
+  unsigned long long l0 = thread_launches();
+  // as iterate(): fresh flags, no residual seen yet (bytes 0x7f: 1.4e306), no stall
+  e = cudaMemsetAsync(c->done, 0, sizeof(int) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->iters, 0, sizeof(int) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->best, 0x7f, sizeof(double) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->stall, 0, sizeof(int) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.loop, 0, sizeof(int) * kLoopSlots, s0);
+  auto krylov_body = [&](cudaGraphConditionalHandle hk) -> cudaError_t {
+    k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.gm_conv, b.skip, ni);
+    note_launch();
+    cudaError_t ee = paqif_on(c, c->rhs, c->sigma, false);
+    if (ee != cudaSuccess) return ee;
+    k_nk_prec<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, 0, c->sigma, b.skip, N, b.loop + 1);
+    note_launch();
+    ee = line_krylov_deform(c, b.znode, b.zh0, b.skip);
+    if (ee != cudaSuccess) return ee;
+    JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, b.znode};
+    k_nk_jv<<<gn, 256, 0, c->st>>>(c->inst, b, q, c->act, b.skip, N);
+    note_launch();
+    k_nk_arnoldi<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, 0, b.skip, c->rhs, N, b.loop + 1);
+    note_launch();
+    return nk_loop(c, hk, 1, 3, b.m, 1, b.gm_conv);
+  };
+  auto trial_body = [&](cudaGraphConditionalHandle ht) -> cudaError_t {
+    k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.lsdone, b.skip, ni);
+    note_launch();
+    k_nk_trial<<<gn, 256, 0, c->st>>>(b, P, H0, b.skip, N);
+    note_launch();
+    cudaError_t ee = line_state(c, b.Pt, b.H0t, rough, b.skip, nullptr);
+    if (ee == cudaSuccess) ee = line_finalize(c, nullptr, nullptr);
+    if (ee != cudaSuccess) return ee;
+    k_nk_merit<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->R, c->red, c->dg, b.skip, P, H0, N);
+    note_launch();
+    return nk_loop(c, ht, 2, 4, 64, 1, b.lsdone);
+  };
+  auto newton_body = [&](cudaGraphConditionalHandle hn) -> cudaError_t {
+    const unsigned long long m0 = thread_launches();
+    cudaError_t ee = line_state(c, P, H0, rough, c->done, nullptr);
+    if (ee == cudaSuccess) ee = line_finalize(c, c->done, c->iters);
+    if (ee == cudaSuccess) ee = line_jac_band(c, P, 1, c->band, c->act, c->jh, c->dg, c->done);
+    if (ee != cudaSuccess) return ee;
+    k_nk_setup<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, P, c->R, c->red, c->act, c->dg, c->jh, c->done, c->band,
+                                           c->rhs, N, c->beta);
+    note_launch();
+    k_nk_jvcoef<<<dim3((N + 255) / 256, ni), 256, 0, c->st>>>(c->rho, c->drho, c->deta_rel, c->eps, c->H, c->dg,
+                                                              c->done, b.jc, N);
+    note_launch();
+    ee = paqif_on(c, c->rhs, c->sigma, true);
+    if (ee != cudaSuccess) return ee;
+    k_nk_border<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->sigma, c->done, c->rhs, N);
+    note_launch();
+    const cudaStream_t here = c->st;
+    ee = capture_while(
+        c, here, s2, [&](cudaGraphConditionalHandle hk) { return nk_loop(c, hk, 1, -1, b.m, 0, b.gm_conv); },
+        krylov_body, &n.krylov);
+    if (ee != cudaSuccess) return ee;
+    k_nk_update<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->done, N);
+    note_launch();
+    ee = capture_while(
+        c, here, s2, [&](cudaGraphConditionalHandle ht) { return nk_loop(c, ht, 2, -1, 64, 0, b.lsdone); },
+        trial_body, &n.trial);
+    if (ee != cudaSuccess) return ee;
+    ee = nk_loop(c, hn, 0, -1, c->max_iter, 1, nullptr);
+    n.newton = (long long)(thread_launches() - m0) - n.krylov - n.trial;
+    return ee;
+  };
+  if (e == cudaSuccess)
+    e = capture_while(
+        c, s0, s1, [&](cudaGraphConditionalHandle hn) { return nk_loop(c, hn, 0, -1, c->max_iter, 0, nullptr); },
+        newton_body, nullptr);
+  c->st = s0;
+  if (e == cudaSuccess) e = line_state(c, P, H0, rough, nullptr, nullptr);
+  if (e == cudaSuccess) e = line_finalize(c, nullptr, nullptr);
+  c->capturing = false;
+  n.fixed = (long long)(thread_launches() - l0) - n.newton - n.krylov - n.trial;
+  return e;
+}
+
+// kernels the last replay ran, from the loop totals (read after the replay)
+long long line_nk_graph_launches(const SolveGraphCounts& n, const int* loop_host) {
+  return n.fixed + (long long)loop_host[0] * n.newton + (long long)loop_host[3] * n.krylov +
+         (long long)loop_host[4] * n.trial;
+}
+
+const int* line_nk_loop_counters(LineCtx* c) { return ((NkBuf*)c->nk)->loop; }
 
 }  // namespace ehl
