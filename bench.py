@@ -182,9 +182,11 @@ def job_rate(world, units_per_rank, ms):
     return world * units_per_rank / (ms * 1e-3)
 
 
-def ehl_params(ops):
+def ehl_params(ops, graph=2):
+    """Leg B's parameters; graph 2: each grid's Newton, GMRES and line-search loops run as one CUDA
+    graph with device-side while-loops (the mixed-precision leg uses cuBLAS and stays host-driven)."""
     return ops.default_params(1, nx=EHL["N"], M=EHL["M"], L=EHL["L"], limiter=EHL["limiter"], halfband=EHL["beta"],
-                              method=1, tol=EHL["tol"], max_iter=60, krylov_dim=40)
+                              method=1, tol=EHL["tol"], max_iter=60, krylov_dim=40, graph=graph)
 
 
 # --------------------------------------------------------------------------- ours
@@ -266,7 +268,7 @@ def run_ours(args):
     # stays float64): solves/s and its difference from the plain path
     mixed = None
     if ctx is not None:
-        pm = ehl_params(ops)
+        pm = ehl_params(ops, graph=0)
         pm.precision = 2
         ctx_m = ops.Context(pm, n_inst=B)
         barrier()
@@ -359,6 +361,8 @@ def run_ours(args):
         "config": {
             "workload": "high-load line contact: batch of converged solves N=1025, M=200, L=10, van Leer, "
                         "beta=8, tol 1e-8, plus the standalone PAQIF batch (4096 x n=1024, beta=4, mode 1)",
+            "ehl_loop": "device-driven: each grid's Newton, GMRES and line-search loops are one CUDA graph launch "
+                        "with conditional while-nodes (graph = 2)",
             "ehl_batch": B, "ehl_N": EHL["N"], "ehl_M": EHL["M"], "ehl_L": EHL["L"], "ehl_beta": EHL["beta"],
             "ehl_ms": round(ms_b, 3), "ehl_newton_iters_min_max": ehl_iters,
             "ehl_newton_iters_per_s": round(job_rate(world, ehl_iter_sum, ms_b), 1) if ehl_iter_sum else None,
@@ -440,16 +444,19 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
                     converged=int(np.sum((r[:, 0] <= 10 * tol) & (r[:, 1] <= 10 * tol))), status=int(code))
 
     # C1: N = 129, M = 20, L = 10, minmod, beta 2, one instance
-    for method in (0, 1):
+    for key, method, graph in (("C1_method0", 0, 0), ("C1_method1", 1, 0), ("C1_method1_graph", 1, 2)):
         p = ops.default_params(1, nx=129, M=20.0, L=10.0, limiter=0, halfband=2, method=method, tol=1e-8,
-                               max_iter=4000 if method == 0 else 60)
+                               max_iter=4000 if method == 0 else 60, graph=graph)
         ctx = ops.Context(p)
+        n0 = ops.kernel_launches()
         ms, out = _timed(torch, lambda: ctx.solve(check=False), reps=5)
         d = dict(workload="line N=129, M=20, L=10, minmod, beta=2, 1 instance, tol 1e-8",
-                 method=("paper relaxation" if method == 0 else "Newton-Krylov"), ms=round(ms, 3),
-                 solves_per_s=round(1e3 / ms, 2))
+                 method=("paper relaxation" if method == 0 else "Newton-Krylov"),
+                 loop=("device-driven graph (Newton, GMRES, line search as graph while-loops)" if graph == 2
+                       else "host-driven"), ms=round(ms, 3), solves_per_s=round(1e3 / ms, 2),
+                 kernels_per_solve=int((ops.kernel_launches() - n0) // 6))
         d.update(summary(out[2], out[3], out[4], 1e-8))
-        res[f"C1_method{method}"] = d
+        res[key] = d
     # C2a: N = 4097, M = 200, L = 10, van Leer, beta 8, one instance
     try:
         p = ops.default_params(1, nx=4097, M=200.0, L=10.0, limiter=1, halfband=8, method=1, tol=1e-8, max_iter=80)
@@ -486,12 +493,13 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
     per = inputs.batched_line_params(512, seed=1)
     Href = None
     for prec in (0, 2):
-        kw = dict(limiter=0, halfband=2, method=1, tol=1e-8, max_iter=60, precision=prec)
+        kw = dict(limiter=0, halfband=2, method=1, tol=1e-8, max_iter=60, precision=prec, graph=2 if prec == 0 else 0)
         pp = [ops.default_params(1, nx=q["N"], M=q["M"], L=q["L"], **kw) for q in per]
         ctx = ops.Context(pp[0], n_inst=len(pp), per_inst=pp)
         ms, out = _timed(torch, lambda: ctx.solve(check=False))
         d = dict(workload="ragged batch: 512 line instances, N from {257, 513, 1025, 2049}, M 10^U(1,3), L U(5,20), "
-                          "minmod, beta=2, tol 1e-8 (seed 1)", precision=PRECISION[prec], ms=round(ms, 2),
+                          "minmod, beta=2, tol 1e-8 (seed 1)", precision=PRECISION[prec],
+                 loop="device-driven graph per grid-size bucket" if prec == 0 else "host-driven", ms=round(ms, 2),
                  solves_per_s=round(512e3 / ms, 2))
         d.update(summary(out[2], out[3], out[4], 1e-8))
         _, H, _ = ctx.residual(out[0], out[1])
