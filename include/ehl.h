@@ -216,13 +216,16 @@ typedef struct {
                         /*   emulation requested (cuBLAS may still choose a SIMT SGEMM),   */
                         /*   3 TF32 tensor cores, 4 BF16 tensor cores; point contact: one */
                         /*   GEMM [nx x nx ny] . [nx ny x ny] per instance from the        */
-                        /*   block-Toeplitz structure of the 2-D kernel                    */
+                        /*   block-Toeplitz structure of the 2-D kernel; 5 (line contact)   */
+                        /*   the library's own tensor-core product: K and the vectors split */
+                        /*   into TF32 hi + lo parts, three tcgen05 TF32 products with     */
+                        /*   float32 accumulation (about 2^-21 relative)                   */
   int graph;            /* line contact, method 1: 1 = each Newton step is one CUDA graph  */
                         /*   launch (captured once, replayed; one host check per step);    */
                         /*   2 = the whole iteration of each grid is one graph launch: the  */
                         /*   Newton, GMRES and line-search loops run as device-side while   */
                         /*   loops whose conditions the kernels set from the instances'     */
-                        /*   flags (no host round trip inside a grid; precision 0 only);   */
+                        /*   flags (no host round trip inside a grid; precision 0 or 5);  */
                         /*   0 = launched kernel by kernel with early exits (default)      */
   double kappa;         /* kappa of limiter 2, -1..1 (0: Fromm, 1/3: third-order upwind    */
                         /*   biased, -1: second-order upwind)                              */
@@ -302,7 +305,8 @@ ehl_status ehl_jacobian_band(ehl_ctx* ctx, const double* P, const double* H0, co
  * eps, the limiter on its current branch).  v [n_inst][nx_max] nodal with
  * zeros at the boundary nodes, v_h0 [n_inst], out [n_inst][nx_max] (0 at the
  * boundary).
- * This is the operator the Newton-Krylov method (method 1) iterates on.
+ * This is the operator the Newton-Krylov method (method 1) iterates on; the
+ * deformation of v uses the arithmetic the context's `precision` selects.
  * Asynchronous. */
 ehl_status ehl_jacobian_apply(ehl_ctx* ctx, const double* P, const double* H0, const double* rough, const double* v,
                               const double* v_h0, double* out);

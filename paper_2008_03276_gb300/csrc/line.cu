@@ -12,6 +12,7 @@
 #include "ehl_internal.h"
 #include "line_kernels.cuh"
 #include "line.h"
+#include "tc_gemm.h"
 
 namespace ehl {
 
@@ -146,6 +147,10 @@ __global__ void k_line_film(const LineInst* __restrict__ inst, const float2* __r
   double Dd;
   if (p64 == 2) {  // one float32 product [n_inst][N] (the GEMM of the mixed-precision Krylov products)
     Dd = (double)reinterpret_cast<const float*>(partial)[(size_t)z * N + i];
+  } else if (p64 == 3) {  // float32 partial products of the K-splits [ksplit][n_inst][N] (tensor cores)
+    const float* pf = reinterpret_cast<const float*>(partial);
+    Dd = 0.0;
+    for (int y = 0; y < ksplit; ++y) Dd += (double)pf[((size_t)y * n_inst + z) * N + i];
   } else if (p64) {
     const double* pd = reinterpret_cast<const double*>(partial);
     Dd = 0.0;
@@ -788,6 +793,7 @@ cudaError_t line_mixed_init(LineCtx* c, int precision) {
   for (const LineInst& q : c->h_inst)
     if (q.h != c->h_inst[0].h || q.elastic != c->h_inst[0].elastic) return cudaSuccess;
   if (!c->h_inst[0].elastic) return cudaSuccess;
+  if (precision == 5) return line_tc_init(c);
   const size_t NN = (size_t)c->N * c->N, NI = (size_t)c->N * c->n_inst;
   cudaError_t e = ctx_alloc(c, (void**)&c->Kf, sizeof(float) * NN);
   if (e == cudaSuccess) e = ctx_alloc(c, (void**)&c->Vf, sizeof(float) * NI);
@@ -814,6 +820,39 @@ cudaError_t line_mixed_init(LineCtx* c, int precision) {
 void line_mixed_free(LineCtx* c) {
   if (c->blas) cublasDestroy(c->blas);
   c->blas = nullptr;
+  delete reinterpret_cast<TcGemm*>(c->tc);
+  c->tc = nullptr;
+}
+
+// precision 5: K [N][ld] and the vectors [n_inst][ld] as tf32 hi / lo parts, the tcgen05 plan and
+// K-splits enough to give the 152 SMs about one tile each
+cudaError_t line_tc_init(LineCtx* c) {
+  const int N = c->N, ni = c->n_inst, ld = tc_ld(N);
+  const int tiles = ((N + 127) / 128) * ((ni + 127) / 128);
+  const int ktiles = (N + 31) / 32;
+  int splits = kSmCount / (tiles > 0 ? tiles : 1);
+  splits = splits < 1 ? 1 : (splits > ktiles ? ktiles : splits);
+  cudaError_t e = ctx_alloc(c, (void**)&c->Khi, sizeof(float) * (size_t)N * ld);
+  if (e == cudaSuccess) e = ctx_alloc(c, (void**)&c->Klo, sizeof(float) * (size_t)N * ld);
+  if (e == cudaSuccess) e = ctx_alloc(c, (void**)&c->Vhi, sizeof(float) * (size_t)ni * ld);
+  if (e == cudaSuccess) e = ctx_alloc(c, (void**)&c->Vlo, sizeof(float) * (size_t)ni * ld);
+  if (e == cudaSuccess) e = ctx_alloc(c, (void**)&c->Df, sizeof(float) * (size_t)splits * ni * N);
+  if (e == cudaSuccess) e = ctx_alloc(c, (void**)&c->tc_err, sizeof(int));
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->st);
+  // the padding columns N..ld-1 are never read (the tensor maps end at column N)
+  if (e == cudaSuccess) e = tc_toeplitz(c->gtab64, N, c->Khi, c->Klo, ld, c->st);
+  if (e != cudaSuccess) return e;
+  TcGemm* g = new TcGemm();
+  e = tc_gemm_init(*g, c->Khi, c->Klo, c->Vhi, c->Vlo, N, ni, N, ld, ld, c->Df, N, splits);
+  if (e != cudaSuccess) {
+    delete g;
+    return e;
+  }
+  c->tc = g;
+  c->tc_splits = g->splits;
+  c->precision = 5;
+  return cudaSuccess;
 }
 
 // dH = -K v + zh0 for the Krylov vectors: the double-float Toeplitz kernel, or
@@ -827,6 +866,18 @@ cudaError_t line_krylov_deform(LineCtx* c, const double* V, const double* zh0, c
     return e;
   }
   const int N = c->N, ni = c->n_inst;
+  if (c->precision == 5) {
+    // TF32x3 on the tensor cores: D[s][z][i] partial sums of K V over the K-splits
+    const TcGemm& tg = *reinterpret_cast<const TcGemm*>(c->tc);
+    cudaError_t e = tc_split(V, N, ni, N, c->Vhi, c->Vlo, tc_ld(N), c->st);
+    if (e == cudaSuccess) e = tc_gemm_run(tg, c->tc_err, c->st);
+    if (e != cudaSuccess) return e;
+    dim3 gn((N + kNodeBlock - 1) / kNodeBlock, ni);
+    k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, reinterpret_cast<const float2*>(c->Df), tg.splits, zh0, nullptr,
+                                               N, skip, c->dH, ni, N, 1, 3);
+    note_launch();
+    return cudaGetLastError();
+  }
   dim3 g((N + 255) / 256, ni);
   k_line_to_f32<<<g, 256, 0, c->st>>>(V, N, c->Vf, N);
   note_launch();

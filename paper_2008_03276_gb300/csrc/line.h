@@ -38,6 +38,12 @@ struct LineCtx {
   int precision = 0;
   cublasHandle_t blas = nullptr;
   float *Kf = nullptr, *Vf = nullptr, *Df = nullptr;
+  // precision 5: the hand-written TF32x3 tcgen05 product (tc_gemm.cu): tf32 hi / lo parts of K
+  // and of the vectors, the plan (a TcGemm), its K-splits and its bounded-wait error flag
+  float *Khi = nullptr, *Klo = nullptr, *Vhi = nullptr, *Vlo = nullptr;
+  void* tc = nullptr;
+  int tc_splits = 1;
+  int* tc_err = nullptr;
   double *Pw = nullptr, *H0w = nullptr, *dH = nullptr;
   int *done = nullptr, *iters = nullptr;
   double* best = nullptr;  // smallest ||min(P,R)||_inf seen (stall test of the rounding-floor stop)
@@ -112,6 +118,7 @@ cudaError_t line_adjoint(LineCtx* c, const double* P, const double* H0, const do
 void line_adj_free(LineCtx* c);
 // Krylov products dH = -K v + zh0 (double-float, or a float32-output GEMM with precision > 0)
 cudaError_t line_mixed_init(LineCtx* c, int precision);
+cudaError_t line_tc_init(LineCtx* c);
 void line_mixed_free(LineCtx* c);
 cudaError_t line_krylov_deform(LineCtx* c, const double* V, const double* zh0, const int* skip);
 

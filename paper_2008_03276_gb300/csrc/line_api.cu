@@ -123,8 +123,9 @@ static bool params_ok(const ehl_params& p) {
          (p.method == 0 || p.method == 1) && p.max_iter >= 1 && p.krylov_dim >= 1 && p.krylov_dim <= 200 &&
          p.tol > 0.0 && isfinite(p.h_init) && isfinite(p.c_h0) && isfinite(p.omega) && isfinite(p.dist_weight) &&
          isfinite(p.switch_eps_h) && p.levels >= -1 && p.coarse_min_nodes >= 5 && p.coarse_tol > 0.0 &&
-         p.precond_blocks >= 1 && p.precond_blocks <= 4096 && p.precision >= 0 && p.precision <= 4 &&
-         (p.graph == 0 || p.graph == 1 || (p.graph == 2 && p.precision == 0));
+         p.precond_blocks >= 1 && p.precond_blocks <= 4096 && p.precision >= 0 && p.precision <= 5 &&
+         (p.graph == 0 || p.graph == 1 || (p.graph == 2 && (p.precision == 0 || p.precision == 5))) &&
+         (p.precision != 5 || p.dim == 1);
 }
 
 static LineInst make_inst(const ehl_params& p) {

@@ -421,8 +421,8 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_merit(const LineInst* __restric
 cudaError_t line_jacobian_apply(LineCtx* c, const double* P, const double* H0, const double* rough, const double* v,
                                 const double* v_h0, double* out) {
   cudaError_t e = line_state(c, P, H0, rough, nullptr, nullptr);
-  if (e == cudaSuccess) e = line_deform(c, v, c->N, nullptr);
-  if (e == cudaSuccess) e = line_film_dir(c, v_h0, nullptr);
+  // the film's change through the Krylov products' deformation (the arithmetic `precision` selects)
+  if (e == cudaSuccess) e = line_krylov_deform(c, v, v_h0, nullptr);
   if (e != cudaSuccess) return e;
   JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, v};
   const dim3 gn((c->N + 255) / 256, c->n_inst);
