@@ -268,18 +268,18 @@ def run_ours(args):
     # stays float64): solves/s and its difference from the plain path
     mixed = None
     if ctx is not None:
-        pm = ehl_params(ops, graph=0)
-        pm.precision = 2
+        pm = ehl_params(ops, graph=2)
+        pm.precision = 5
         ctx_m = ops.Context(pm, n_inst=B)
         barrier()
         ms_m, out_m = _timed(torch, lambda: ctx_m.solve(check=False), reps=2)
         _, Hm, _ = ctx_m.residual(out_m[0], out_m[1])
         _, Hp, _ = ctx.residual(sol["P"], sol["H0"])
         rs_m = out_m[3].abs().cpu().numpy()
-        mixed = {"precision": "Krylov products K v as one float32 cuBLAS GEMM per Krylov step (BF16x9 "
-                              "emulation requested; cuBLAS runs SIMT SGEMM kernels for these shapes, "
-                              "tensor pipe idle) and float32 PAQIF preconditioner sweeps; residual, line "
-                              "search and update in float64",
+        mixed = {"precision": "Krylov products K v as one TF32x3 GEMM per Krylov step on the tensor cores "
+                              "(the library's tcgen05 kernel: K and the vectors split into tf32 hi + lo, three "
+                              "products, float32 accumulation) and float32 PAQIF preconditioner sweeps; "
+                              "residual, line search and update in float64; device-driven loop (graph 2)",
                  "value": None, "unit": "converged solves/s", "ms": None,
                  "all_converged": int(out_m[4]) == 0, "max_final_residual": float(rs_m.max()),
                  "H_rel_err_vs_plain": float((Hm - Hp).abs().max() / Hp.abs().max())}
@@ -402,7 +402,9 @@ def run_ours(args):
 # ------------------------------------------------------------- the other configs
 PRECISION = {0: "Krylov products in double-float (plain path)",
              2: "Krylov products as float32 cuBLAS GEMMs (BF16x9 emulation requested, SIMT SGEMM kernels "
-                "run), float32 PAQIF preconditioner sweeps in line contact; residual float64"}
+                "run), float32 PAQIF preconditioner sweeps in line contact; residual float64",
+             5: "Krylov products as the library's TF32x3 tcgen05 GEMM (tensor cores), float32 PAQIF "
+                "preconditioner sweeps; residual float64"}
 
 def _timed(torch, fn, reps=1, warm=1):
     """CUDA-event time (ms, best of reps) of fn() after warm calls, and fn's last result."""
@@ -492,14 +494,14 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
     # C3: 512 instances, M log-uniform [10, 1000], L uniform [5, 20], N from {257, ..., 2049}
     per = inputs.batched_line_params(512, seed=1)
     Href = None
-    for prec in (0, 2):
-        kw = dict(limiter=0, halfband=2, method=1, tol=1e-8, max_iter=60, precision=prec, graph=2 if prec == 0 else 0)
+    for prec in (0, 5):
+        kw = dict(limiter=0, halfband=2, method=1, tol=1e-8, max_iter=60, precision=prec, graph=2)
         pp = [ops.default_params(1, nx=q["N"], M=q["M"], L=q["L"], **kw) for q in per]
         ctx = ops.Context(pp[0], n_inst=len(pp), per_inst=pp)
         ms, out = _timed(torch, lambda: ctx.solve(check=False))
         d = dict(workload="ragged batch: 512 line instances, N from {257, 513, 1025, 2049}, M 10^U(1,3), L U(5,20), "
                           "minmod, beta=2, tol 1e-8 (seed 1)", precision=PRECISION[prec],
-                 loop="device-driven graph per grid-size bucket" if prec == 0 else "host-driven", ms=round(ms, 2),
+                 loop="device-driven graph per grid-size bucket", ms=round(ms, 2),
                  solves_per_s=round(512e3 / ms, 2))
         d.update(summary(out[2], out[3], out[4], 1e-8))
         _, H, _ = ctx.residual(out[0], out[1])
@@ -737,6 +739,32 @@ def run_reference(args):
     }
 
 
+def profile_case(name):
+    """Small fixed cases for ncu captures of one kernel (no timing, no JSON line).
+
+    tc_gemm: three ehl_jacobian_apply calls on the 512-instance N = 1025, M = 200 context with the
+    tensor-core Krylov products (precision 5), each one launch of the TF32x3 tcgen05 kernel."""
+    import torch
+
+    from paper_2008_03276_gb300 import ops
+
+    if name == "tc_gemm":
+        B, N = 512, 1025
+        p = ops.default_params(1, nx=N, M=200.0, L=10.0, limiter=1, halfband=8, method=1, precision=5)
+        ctx = ops.Context(p, n_inst=B)
+        x = torch.linspace(-4.5, 1.5, N, dtype=torch.float64, device="cuda")
+        P = torch.sqrt(torch.clamp(1 - x * x, min=0)).repeat(B, 1).contiguous()
+        H0 = torch.full((B,), 0.1, dtype=torch.float64, device="cuda")
+        g = torch.Generator(device="cuda").manual_seed(0)
+        v = torch.randn((B, N), dtype=torch.float64, device="cuda", generator=g)
+        v[:, 0] = 0.0
+        v[:, -1] = 0.0
+        vh = torch.zeros(B, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            ctx.jacobian_apply(P, H0, v, vh)
+        torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -750,7 +778,11 @@ def main():
     ap.add_argument("--ehl-batch", type=int, default=512, help="line-contact instances solved per step")
     ap.add_argument("--paqif-nsys", type=int, default=PAQIF_NSYS,
                     help="systems in the PAQIF batch (smaller only for profiling captures)")
+    ap.add_argument("--profile", choices=["tc_gemm"], help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
+    if args.profile:
+        profile_case(args.profile)
+        return
     if args.warmup < 3:
         args.warmup = 3
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
