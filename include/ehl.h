@@ -147,6 +147,19 @@ ehl_status ehl_paqif_solve_partitioned(int n_sys, int n, int beta, int partition
  * Returns EHL_EINVAL for bad sizes, a NULL r or an inadmissible r. */
 ehl_status ehl_paqif_partitions(int n_sys, int n, int beta, int partitions, int* r);
 
+/* Autotuning of the partition count for a batch shape (Sec. 2.2.4 leaves r
+ * free; the best r depends on the batch size, the order and the GPU).  Times
+ * every admissible r (1..32) on the caller's band / rhs (device arrays as for
+ * ehl_paqif_solve; x receives a solution) with CUDA events: one untimed call,
+ * then the best of `reps` (1..100).  best_r receives the fastest r, to pass to
+ * ehl_paqif_solve_partitioned with a workspace of
+ * ehl_paqif_workspace_size_partitioned(..., r, ...); ms_per_r (nullable, 32
+ * floats) the best time of each r, -1 where r is not admissible.  Allocates
+ * its workspace stream-ordered and synchronises the stream.  Returns
+ * EHL_EINVAL, EHL_ENOMEM, EHL_ECUDA or a status of the timed solves. */
+ehl_status ehl_paqif_autotune(int n_sys, int n, int beta, int mode, const double* band, const double* rhs,
+                              double* x, int reps, void* stream, int* best_r, float* ms_per_r);
+
 /* ------------------------------------------------------------------------
  * EHL problem: context, residual, band Jacobian, solve
  * ------------------------------------------------------------------------
@@ -242,6 +255,11 @@ typedef struct {
                         /*   1: the same discrete convolution through a float64 FFT of     */
                         /*   cyclic length 2^ceil(log2(2 n - 3)) per direction (nx, ny up  */
                         /*   to 2049); the adjoint's products keep the direct sum          */
+  int autotune;         /* line contact, method 1: 1 = at ehl_create, time every admissible  */
+                        /*   PAQIF partition count on the shape of each grid's Krylov       */
+                        /*   preconditioner (ehl_paqif_autotune on a band of that shape)   */
+                        /*   and keep the fastest for the context's life; 0 = the          */
+                        /*   library's rule (ehl_paqif_partitions with 0)                  */
   int yline;            /* point contact: 1 adds the y-line stage to the preconditioner:    */
                         /*   z1 = M_x^-1 v, z = z1 + M_y^-1 (v - J z1), M_x and M_y the     */
                         /*   bordered PAQIF solves on the x- and y-line bands of the exact  */

@@ -23,7 +23,7 @@ class EhlParams(ctypes.Structure):
                 ("h_init", ctypes.c_double), ("levels", ctypes.c_int), ("coarse_min_nodes", ctypes.c_int),
                 ("coarse_tol", ctypes.c_double), ("precond_blocks", ctypes.c_int),
                 ("precision", ctypes.c_int), ("graph", ctypes.c_int), ("kappa", ctypes.c_double),
-                ("splitting", ctypes.c_int), ("deform", ctypes.c_int), ("yline", ctypes.c_int)]
+                ("splitting", ctypes.c_int), ("deform", ctypes.c_int), ("autotune", ctypes.c_int), ("yline", ctypes.c_int)]
 
 
 class EhlCdParams(ctypes.Structure):
@@ -73,6 +73,9 @@ SYMBOLS = {
     "ehl_cd_relax": (ctypes.c_int, [ctypes.POINTER(EhlCdParams), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_size_t, ctypes.c_void_p]),
+    "ehl_paqif_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "ehl_paqif_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),

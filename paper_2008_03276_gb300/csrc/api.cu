@@ -119,3 +119,68 @@ extern "C" ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* 
   return ehl_paqif_solve_partitioned(n_sys, n, beta, 0, band, rhs, active, mode, x, iters, info, workspace,
                                      workspace_bytes, stream);
 }
+
+// Autotuning of the partition count (Sec. 2.2.4: the partitioned method leaves r free): every
+// admissible r is timed on the caller's batch with CUDA events (one untimed launch, then the best
+// of `reps`), the fastest returned.  The workspace is allocated stream-ordered for the largest r
+// and released; the stream is synchronised.
+extern "C" ehl_status ehl_paqif_autotune(int n_sys, int n, int beta, int mode, const double* band, const double* rhs,
+                                         double* x, int reps, void* stream, int* best_r, float* ms_per_r) {
+  if (!band || !rhs || !x || !best_r || !paqif_args_ok(n_sys, n, beta, mode) || reps < 1 || reps > 100)
+    return EHL_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int gpc = 32;  // partition counts tried: the admissible ones up to the lane groups of a CTA
+  size_t need = 0;
+  for (int r = 1; r <= gpc; ++r) {
+    size_t b = 0;
+    if (paqif_parts(n_sys, n, beta, r) == r &&
+        ehl_paqif_workspace_size_partitioned(n_sys, n, beta, r, mode, &b) == EHL_OK && b > need)
+      need = b;
+  }
+  if (need == 0) return EHL_EINVAL;
+  void* ws = nullptr;
+  if (cudaMallocAsync(&ws, need, st) != cudaSuccess) {
+    cudaGetLastError();
+    return EHL_ENOMEM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best_ms = 0.f;
+  int best = -1;
+  ehl_status status = EHL_OK;
+  for (int r = 1; r <= gpc && e == cudaSuccess && status == EHL_OK; ++r) {
+    if (ms_per_r) ms_per_r[r - 1] = -1.f;
+    if (paqif_parts(n_sys, n, beta, r) != r) continue;
+    status = ehl_paqif_solve_partitioned(n_sys, n, beta, r, band, rhs, nullptr, mode, x, nullptr, nullptr, ws, need,
+                                         stream);
+    float t_best = -1.f;
+    for (int k = 0; k < reps && status == EHL_OK && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(e0, st);
+      if (e != cudaSuccess) break;
+      status = ehl_paqif_solve_partitioned(n_sys, n, beta, r, band, rhs, nullptr, mode, x, nullptr, nullptr, ws,
+                                           need, stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (e == cudaSuccess && (t_best < 0.f || t < t_best)) t_best = t;
+    }
+    if (ms_per_r) ms_per_r[r - 1] = t_best;
+    if (t_best >= 0.f && (best < 0 || t_best < best_ms)) {
+      best = r;
+      best_ms = t_best;
+    }
+  }
+  cudaFreeAsync(ws, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return EHL_ECUDA;
+  }
+  if (status != EHL_OK) return status;
+  *best_r = best;
+  return best > 0 ? EHL_OK : EHL_EINVAL;
+}

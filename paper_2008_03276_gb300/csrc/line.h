@@ -34,6 +34,7 @@ struct LineCtx {
   size_t pq_ws_bytes = 0;
   int* pq_info = nullptr;
   int pq_parts = 1;  // Krylov preconditioner: PAQIF blocks per band (block Jacobi)
+  int pq_r = 0;      // its partitions per system (Sec. 2.2.4): 0 the library's rule, else autotuned
   // mixed-precision Krylov products (precision > 0): dense float32 K, vectors, products
   int precision = 0;
   cublasHandle_t blas = nullptr;

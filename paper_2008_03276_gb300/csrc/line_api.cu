@@ -105,7 +105,14 @@ extern "C" void ehl_params_default(ehl_params* p, int dim) {
   p->kappa = 0.0;
   p->splitting = 0;
   p->deform = 0;
+  p->autotune = 0;
   p->yline = 0;
+}
+
+// band rows of the identity matrix (the other entries already zero): the autotuner's input
+__global__ void k_unit_diagonal(double* __restrict__ band, size_t rows, int bw, int beta) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < rows) band[t * bw + beta] = 1.0;
 }
 
 static bool point_grid_ok(const ehl_params& p) {
@@ -119,7 +126,7 @@ static bool params_ok(const ehl_params& p) {
          p.L >= 0.0 && p.xb > p.xa && p.alpha > 0.0 && p.p0 > 0.0 && p.z > 0.0 && (p.limiter >= 0 && p.limiter <= 2) &&
          p.kappa >= -1.0 && p.kappa <= 1.0 && p.splitting >= 0 && p.splitting <= 2 &&
          (p.deform == 0 || (p.deform == 1 && p.dim == 2 && fft2_size_ok(p.nx, p.ny))) &&
-         (p.yline == 0 || (p.yline == 1 && p.dim == 2)) &&
+         (p.yline == 0 || (p.yline == 1 && p.dim == 2)) && (p.autotune == 0 || p.autotune == 1) &&
          (p.method == 0 || p.method == 1) && p.max_iter >= 1 && p.krylov_dim >= 1 && p.krylov_dim <= 200 &&
          p.tol > 0.0 && isfinite(p.h_init) && isfinite(p.c_h0) && isfinite(p.omega) && isfinite(p.dist_weight) &&
          isfinite(p.switch_eps_h) && p.levels >= -1 && p.coarse_min_nodes >= 5 && p.coarse_tol > 0.0 &&
@@ -239,10 +246,35 @@ static ehl_status init_line(LineCtx* c, const std::vector<LineInst>& insts, int 
         break;
       }
   A((void**)&c->pq_info, sizeof(int) * n_inst * c->pq_parts);
+  c->pq_r = 0;
+  if (ok && p.method == 1 && p.autotune == 1) {
+    // the fastest partition count for the preconditioner's shape, timed on identity bands
+    const int ns = n_inst * c->pq_parts, nb = c->n / c->pq_parts, bw = 2 * c->beta + 1;
+    double *tb = nullptr, *tr = nullptr, *tx = nullptr;
+    cudaError_t e = cudaMalloc(&tb, sizeof(double) * (size_t)ns * nb * bw);
+    if (e == cudaSuccess) e = cudaMalloc(&tr, sizeof(double) * (size_t)ns * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&tx, sizeof(double) * (size_t)ns * nb);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tb, 0, sizeof(double) * (size_t)ns * nb * bw, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tr, 0, sizeof(double) * (size_t)ns * nb, c->st);
+    if (e == cudaSuccess) {
+      k_unit_diagonal<<<(unsigned)(((size_t)ns * nb + 255) / 256), 256, 0, c->st>>>(tb, (size_t)ns * nb, bw,
+                                                                                     c->beta);
+      note_launch();
+      e = cudaGetLastError();
+    }
+    int r = 0;
+    if (e == cudaSuccess &&
+        ehl_paqif_autotune(ns, nb, c->beta, 0, tb, tr, tx, 3, c->st, &r, nullptr) == EHL_OK && r > 0)
+      c->pq_r = r;
+    if (tb) cudaFree(tb);
+    if (tr) cudaFree(tr);
+    if (tx) cudaFree(tx);
+    cudaGetLastError();
+  }
   if (ok) {
     size_t wb = 0, wb2 = 0;
     ehl_paqif_workspace_size(n_inst, c->n, c->beta, 0, &wb);
-    ehl_paqif_workspace_size(n_inst * c->pq_parts, c->n / c->pq_parts, c->beta, 0, &wb2);
+    ehl_paqif_workspace_size_partitioned(n_inst * c->pq_parts, c->n / c->pq_parts, c->beta, c->pq_r, 0, &wb2);
     c->pq_ws_bytes = wb > wb2 ? wb : wb2;
     A(&c->pq_ws, c->pq_ws_bytes);
   }

@@ -472,7 +472,7 @@ cudaError_t line_nk_alloc(LineCtx* c) {
             {(void**)&b->lsphase, sizeof(int) * ni},
             {(void**)&b->skip, sizeof(int) * ni},
             {(void**)&b->loop, sizeof(int) * kLoopSlots},
-            {(void**)&b->fstore, paqif_factor_store_bytes(ni * c->pq_parts, c->n / c->pq_parts, c->beta)}};
+            {(void**)&b->fstore, paqif_factor_store_bytes(ni * c->pq_parts, c->n / c->pq_parts, c->beta, c->pq_r)}};
   for (auto& x : al) {
     cudaError_t e = ctx_alloc(c, x.p, x.bytes);
     if (e != cudaSuccess) return e;
@@ -493,6 +493,7 @@ static cudaError_t paqif_on(LineCtx* c, const double* rhs, double* x, bool facto
   // block's matrix, so PAQIF ignores them (block Jacobi)
   L.n_sys = c->n_inst * c->pq_parts;
   L.n = c->n / c->pq_parts;
+  L.parts = c->pq_r;
   L.beta = c->beta;
   L.mode = 0;
   L.band = c->band;

@@ -311,3 +311,18 @@ def cd_workspace_size(p, n_inst):
     _ffi.check(_ffi.load().ehl_cd_workspace_size(ctypes.byref(p), int(n_inst), ctypes.byref(nb)),
                "ehl_cd_workspace_size")
     return nb.value
+
+
+def paqif_autotune(band, rhs, beta, mode=0, reps=3, stream=None):
+    """Fastest partition count for this batch shape (``ehl_paqif_autotune``): ``(r, ms_per_r)``
+    with ``ms_per_r[r - 1]`` the best time of each admissible r (-1 where not admissible)."""
+    lib = _ffi.load()
+    _check_dev(band, rhs)
+    n_sys, n, _ = band.shape
+    x = torch.empty_like(rhs)
+    r = ctypes.c_int(0)
+    ms = (ctypes.c_float * 32)()
+    code = lib.ehl_paqif_autotune(n_sys, n, beta, mode, _ptr(band), _ptr(rhs), _ptr(x), int(reps), _stream(stream),
+                                  ctypes.byref(r), ms)
+    _ffi.check(code, "ehl_paqif_autotune")
+    return r.value, list(ms)

@@ -74,12 +74,12 @@ def test_params_struct_layout_matches_defaults():
     assert (p.method, p.tol, p.max_iter, p.krylov_dim, p.h_init) == (1, 1e-8, 200, 40, 0.05)
     assert (p.levels, p.coarse_min_nodes, p.coarse_tol) == (-1, 65, 1e-4)
     assert (p.precond_blocks, p.precision, p.graph) == (1, 0, 0)
-    assert (p.kappa, p.splitting, p.deform, p.yline) == (0.0, 0, 0, 0)
+    assert (p.kappa, p.splitting, p.deform, p.autotune, p.yline) == (0.0, 0, 0, 0, 0)
     assert ctypes.sizeof(p) == (_ffi.EhlParams.yline.offset + 4 + 7) // 8 * 8  # tail padding to 8 bytes
 
 
 @pytest.mark.parametrize("field,value", [("nx", 4), ("halfband", 9), ("M", -1.0), ("xb", -5.0), ("method", 7),
-                                         ("limiter", 3), ("kappa", 1.5), ("kappa", -1.01), ("splitting", 3), ("deform", 1), ("deform", 2), ("yline", 1),
+                                         ("limiter", 3), ("kappa", 1.5), ("kappa", -1.01), ("splitting", 3), ("deform", 1), ("deform", 2), ("yline", 1), ("autotune", 2),
                                          ("krylov_dim", 0), ("levels", -2),
                                          ("coarse_min_nodes", 4), ("coarse_tol", 0.0)])
 def test_create_rejects_bad_params_on_host(field, value):
