@@ -517,13 +517,13 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
     Href = None
     for key, prec, deform in (("C4", 0, 0), ("C4_mixed", 2, 0), ("C4_fft", 0, 1)):
         p = ops.default_params(2, nx=257, ny=257, M=100.0, L=10.0, limiter=0, halfband=2, method=1, tol=1e-8,
-                               max_iter=60, coarse_min_nodes=33, precision=prec, deform=deform)
+                               max_iter=60, coarse_min_nodes=33, precision=prec, deform=deform, autotune=deform)
         ctx = ops.Context(p)
         ms, out = _timed(torch, lambda: ctx.solve(check=False), warm=0 if deform == 0 else 1)
         d = dict(workload="point contact 257x257, M=100, L=10, minmod, beta=2 (x-line PAQIF preconditioner), "
                           "tol 1e-8, nested 33-65-129-257",
-                 precision=PRECISION[prec], deformation=("float64 FFT convolution (512 x 512 cyclic)" if deform
-                                                         else "direct sum"),
+                 precision=PRECISION[prec], deformation=("float64 FFT convolution (512 x 512 cyclic); x-line "
+                                                         "partition count autotuned" if deform else "direct sum"),
                  ms=round(ms, 1), solves_per_s=round(1e3 / ms, 4))
         d.update(summary(out[2], out[3], out[4], 1e-8))
         _, H, _ = ctx.residual(out[0], out[1])

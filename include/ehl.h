@@ -255,9 +255,10 @@ typedef struct {
                         /*   1: the same discrete convolution through a float64 FFT of     */
                         /*   cyclic length 2^ceil(log2(2 n - 3)) per direction (nx, ny up  */
                         /*   to 2049); the adjoint's products keep the direct sum          */
-  int autotune;         /* line contact, method 1: 1 = at ehl_create, time every admissible  */
-                        /*   PAQIF partition count on the shape of each grid's Krylov       */
-                        /*   preconditioner (ehl_paqif_autotune on a band of that shape)   */
+  int autotune;         /* method 1: 1 = at ehl_create, time every admissible PAQIF      */
+                        /*   partition count on the shape of each grid's Krylov             */
+                        /*   preconditioner (line: the bands; point: the x-line systems)   */
+                        /*   with ehl_paqif_autotune on identity bands of that shape       */
                         /*   and keep the fastest for the context's life; 0 = the          */
                         /*   library's rule (ehl_paqif_partitions with 0)                  */
   int yline;            /* point contact: 1 adds the y-line stage to the preconditioner:    */

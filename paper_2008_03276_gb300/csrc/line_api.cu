@@ -409,7 +409,7 @@ static ehl_status create_point(const ehl_params* p, int n_inst, const ehl_params
   ctx->pt = new PtCtx();
   ctx->pt->st = stream;
   if (const char* tr = getenv("EHL_TRACE")) ctx->pt->trace = atoi(tr) > 0 ? atoi(tr) : 0;
-  ehl_status st = pt_init(ctx->pt, insts, p->halfband, p->max_iter, p->krylov_dim, p->precision, p->deform, p->yline);
+  ehl_status st = pt_init(ctx->pt, insts, p->halfband, p->max_iter, p->krylov_dim, p->precision, p->deform, p->yline, p->autotune);
   // coarse grids: halve the intervals in both directions while both stay even and
   // the coarse grid keeps coarse_min_nodes nodes per direction
   int gx = p->nx, gy = p->ny;
@@ -434,7 +434,7 @@ static ehl_status create_point(const ehl_params* p, int n_inst, const ehl_params
     l->st = stream;
     l->trace = ctx->pt->trace;
     ctx->ptlv.push_back(l);
-    st = pt_init(l, ci, p->halfband, std::min(p->max_iter, kCoarseMaxIter), p->krylov_dim, p->precision, p->deform, p->yline);
+    st = pt_init(l, ci, p->halfband, std::min(p->max_iter, kCoarseMaxIter), p->krylov_dim, p->precision, p->deform, p->yline, p->autotune);
     double* r = nullptr;
     if (st == EHL_OK && pt_alloc(l, (void**)&r, sizeof(double) * n_inst * (size_t)l->NN) != cudaSuccess) {
       cudaGetLastError();

@@ -655,8 +655,13 @@ static PtRow pt_row(PtCtx* c, const double* P) {
   return r;
 }
 
+__global__ void k_pt_unit_diagonal(double* __restrict__ band, size_t rows, int bw, int beta) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < rows) band[t * bw + beta] = 1.0;
+}
+
 ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int max_iter, int krylov_dim,
-                   int precision, int deform, int yline) {
+                   int precision, int deform, int yline, int autotune) {
   const int ni = (int)insts.size();
   c->n_inst = ni;
   c->nx = insts[0].nx;
@@ -707,11 +712,31 @@ ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int 
   A((void**)&c->dots, sizeof(double) * ni * (size_t)c->nvb * (m + 2));
   A((void**)&c->hcol, sizeof(double) * ni * (size_t)(m + 2));
   A((void**)&c->pq_info, sizeof(int) * c->lines);
+  c->pq_r = 0;
+  if (ok && autotune) {
+    // the fastest partition count of the x-line systems (ny - 2 per instance, order nx - 2), timed
+    // on identity bands in the context's band / rhs / sigma arrays (rewritten by every Newton step)
+    const size_t rows = nt, bwz = (size_t)bw;
+    cudaError_t e = cudaMemsetAsync(c->band, 0, sizeof(double) * rows * bwz, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->rhs, 0, sizeof(double) * rows, c->st);
+    if (e == cudaSuccess) {
+      k_pt_unit_diagonal<<<(unsigned)((rows + 255) / 256), 256, 0, c->st>>>(c->band, rows, bw, beta);
+      note_launch();
+      e = cudaGetLastError();
+    }
+    int r = 0;
+    if (e == cudaSuccess &&
+        ehl_paqif_autotune(c->lines, c->nx - 2, beta, 0, c->band, c->rhs, c->sigma, 3, c->st, &r, nullptr) == EHL_OK &&
+        r > 0)
+      c->pq_r = r;
+    cudaGetLastError();
+  }
   if (ok) {
-    size_t wb = 0;
+    size_t wb = 0, wb2 = 0;
     ehl_paqif_workspace_size(c->lines, c->nx - 2, beta, 0, &wb);
-    A(&c->pq_ws, wb);
-    A(&c->fstore, paqif_factor_store_bytes(c->lines, c->nx - 2, beta));
+    ehl_paqif_workspace_size_partitioned(c->lines, c->nx - 2, beta, c->pq_r, 0, &wb2);
+    A(&c->pq_ws, wb > wb2 ? wb : wb2);
+    A(&c->fstore, paqif_factor_store_bytes(c->lines, c->nx - 2, beta, c->pq_r));
   }
   if (ok && yline) {
     c->yline = 1;

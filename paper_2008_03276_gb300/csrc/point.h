@@ -36,6 +36,7 @@ struct PtCtx {
   double *band = nullptr, *jh = nullptr, *dg = nullptr, *rhs = nullptr, *sigma = nullptr;
   uint8_t* act = nullptr;
   void* pq_ws = nullptr;
+  int pq_r = 0;  // partitions per x-line system of the Krylov preconditioner: 0 the rule, else autotuned
   int* pq_info = nullptr;
   void* fstore = nullptr;
   // Newton-Krylov
@@ -69,7 +70,7 @@ struct PtCtx {
 
 cudaError_t pt_alloc(PtCtx* c, void** p, size_t bytes);
 ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int max_iter, int krylov_dim,
-                   int precision = 0, int deform = 0, int yline = 0);
+                   int precision = 0, int deform = 0, int yline = 0, int autotune = 0);
 void pt_free(PtCtx* c);
 // state (film, lubricant, faces, residual, block partials) at (P, H0); all [n_inst][ny][nx]
 cudaError_t pt_state(PtCtx* c, const double* P, const double* H0, const double* rough, const int* skip);

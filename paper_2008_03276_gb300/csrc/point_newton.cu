@@ -613,6 +613,7 @@ static cudaError_t pn_paqif(PtCtx* c, const double* rhs, double* x, bool factor)
   L.x = x;
   L.iters = nullptr;
   L.info = c->pq_info;
+  L.parts = c->pq_r;
   // double-float sweeps at every precision: with float32 x-line solves the 2-D Newton
   // iteration stalls (C4: 60 steps without convergence, against 14 in double-float)
   return factor ? launch_paqif_factor(L, c->fstore, c->st) : launch_paqif_resolve(L, c->fstore, c->st);

@@ -43,3 +43,20 @@ def test_context_with_autotuned_preconditioner():
     P0, H0, it0, r0, code0 = c0.solve(check=False)
     assert code1 == 0 and code0 == 0
     assert float((P1 - P0).abs().max() / P0.abs().max()) <= 1e-9
+
+
+def test_point_context_with_autotuned_xlines():
+    """257^2 point contact (the bench's configuration) with the FFT deformation and the x-line
+    partition count autotuned: converged, and the oracle's own residual at the solution is small."""
+    from oracle import point_ref as ptr
+    n = 257
+    p = ops.default_params(2, nx=n, ny=n, M=100.0, L=10.0, limiter=0, halfband=2, method=1, tol=1e-8, max_iter=60,
+                           coarse_min_nodes=33, deform=1, autotune=1)
+    ctx = ops.Context(p)
+    P, H0, iters, res, code = ctx.solve(check=False)
+    assert code == 0
+    Pn, H0n = P.cpu().numpy()[0], float(H0.cpu()[0])
+    pb = ptr.PointProblem(n, n, 100.0, 10.0)
+    Pint = Pn.T[1:-1, 1:-1].ravel()
+    R = ptr.residual(pb, Pint, H0n)
+    assert np.max(np.abs(np.minimum(Pint, R))) <= max(2e-8, ptr.rounding_floor(pb, Pint, H0n))
