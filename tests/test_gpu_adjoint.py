@@ -214,3 +214,54 @@ def test_adjoint_c5_full_amplitude_reports():
         err = np.max(np.abs(gr[k] - ref["rough"])) / scale
         print(f"instance {k}: scaled condition {kappa:.2e}, gradient difference {err:.2e}")
         assert err <= max(1e-8, 1e-14 * kappa)   # forward-error bound kappa u with a constant of ~100
+
+
+@pytest.mark.slow
+def test_adjoint_c5_full_amplitude_matches_resolved_differences():
+    """The adjoint workload at its full roughness amplitude (N = 1025, M = 50, L = 10, van Leer,
+    beta 8, 0.1 sin(2 pi X / 0.25) + field (0.05, 0.1)): on the first instance of the batch whose
+    forward solve converges, the adjoint gradient of the central film H_c with respect to M, L
+    and three roughness nodes near the centre agrees with central differences of re-converged
+    solves (step 1e-6) to 1e-5 relative -- the finite-difference check at the size and amplitude
+    the workload states, whatever the scaled condition number of the bordered system."""
+    N, M, L, n = 1025, 50.0, 10.0, 8
+    rgh = c5_roughness(N, n)
+    ctx = make(N, M, L, 1, 8, tol=1e-12, n_inst=n)
+    P, H0, iters, res, code = ctx.solve(rough=dev(rgh), check=False)
+    r = np.abs(res.cpu().numpy())
+    ok = np.nonzero((r[:, 0] <= 1e-10) & (r[:, 1] <= 1e-10))[0]
+    assert len(ok) > 0
+    k = int(ok[0])
+    rk = rgh[k]
+    pb = lr.LineProblem(N, M, L, limiter="vanleer", rough=rk)
+    c = int(np.argmin(np.abs(pb.X)))
+    P1, H01 = P[k:k + 1].contiguous(), H0[k:k + 1].contiguous()
+    single = make(N, M, L, 1, 8, tol=1e-12)
+    Ps, H0s, _, rs, code = single.solve(P1, H01, rough=dev(rows(rk)), check=False)
+    assert float(rs.abs().max()) <= 1e-10
+
+    def value(rg, M_=M, L_=L):
+        cx = make(N, M_, L_, 1, 8, tol=1e-12)
+        Pp, H0p, it, res_, code_ = cx.solve(Ps, H0s, rough=dev(rows(rg)), check=False)
+        assert float(res_.abs().max()) <= 1e-10
+        _, H, _ = cx.residual(Pp, H0p, dev(rows(rg)))
+        return float(H[0, c].cpu())
+
+    gH = np.zeros((1, N))
+    gH[0, c] = 1.0
+    gr, gml, rel, code = single.adjoint(Ps, H0s, None, dev(gH), None, rough=dev(rows(rk)), tol=1e-12, max_cycles=20,
+                                        check=False)
+    gr, gml = gr.cpu().numpy()[0], gml.cpu().numpy()[0]
+    assert float(rel.cpu()[0]) <= 1e-10
+    d = 1e-6
+    for node in (c - 40, c - 10, c + 20):
+        rp, rm = rk.copy(), rk.copy()
+        rp[node] += d
+        rm[node] -= d
+        fd = (value(rp) - value(rm)) / (2 * d)
+        assert abs(fd - gr[node]) <= 1e-5 * abs(fd) + 1e-7 * np.max(np.abs(gr)), (node, fd, gr[node])
+    fdM = (value(rk, M * (1 + d)) - value(rk, M * (1 - d))) / (2 * d * M)
+    fdL = (value(rk, L_=L * (1 + d)) - value(rk, L_=L * (1 - d))) / (2 * d * L)
+    print(f"instance {k}: dH_c/dM adjoint {gml[0]:.8e} fd {fdM:.8e}; dH_c/dL adjoint {gml[1]:.8e} fd {fdL:.8e}")
+    assert abs(fdM - gml[0]) <= 1e-5 * abs(fdM)
+    assert abs(fdL - gml[1]) <= 1e-5 * abs(fdL)
