@@ -118,7 +118,9 @@ __global__ void k_unit_diagonal(double* __restrict__ band, size_t rows, int bw, 
 static bool point_grid_ok(const ehl_params& p) {
   if (p.dim != 2) return true;
   const double hx = (p.xb - p.xa) / (p.nx - 1), hy = (p.yb - p.ya) / (p.ny - 1);
-  return p.ny >= 5 && p.ny <= 4097 && p.nx <= 4097 && p.yb > p.ya && fabs(hx - hy) <= 1e-12 * hx && p.method == 1;
+  // graph mode 2 captures the Krylov products too: the cuBLAS GEMMs of precision 1-4 stay out
+  return p.ny >= 5 && p.ny <= 4097 && p.nx <= 4097 && p.yb > p.ya && fabs(hx - hy) <= 1e-12 * hx && p.method == 1 &&
+         p.graph != 1 && (p.graph != 2 || p.precision == 0 || p.deform == 1);
 }
 
 static bool params_ok(const ehl_params& p) {
@@ -410,6 +412,7 @@ static ehl_status create_point(const ehl_params* p, int n_inst, const ehl_params
   ctx->pt->st = stream;
   if (const char* tr = getenv("EHL_TRACE")) ctx->pt->trace = atoi(tr) > 0 ? atoi(tr) : 0;
   ehl_status st = pt_init(ctx->pt, insts, p->halfband, p->max_iter, p->krylov_dim, p->precision, p->deform, p->yline, p->autotune);
+  ctx->pt->graph_mode = p->graph;
   // coarse grids: halve the intervals in both directions while both stay even and
   // the coarse grid keeps coarse_min_nodes nodes per direction
   int gx = p->nx, gy = p->ny;
@@ -435,6 +438,7 @@ static ehl_status create_point(const ehl_params* p, int n_inst, const ehl_params
     l->trace = ctx->pt->trace;
     ctx->ptlv.push_back(l);
     st = pt_init(l, ci, p->halfband, std::min(p->max_iter, kCoarseMaxIter), p->krylov_dim, p->precision, p->deform, p->yline, p->autotune);
+    l->graph_mode = p->graph;
     double* r = nullptr;
     if (st == EHL_OK && pt_alloc(l, (void**)&r, sizeof(double) * n_inst * (size_t)l->NN) != cudaSuccess) {
       cudaGetLastError();
@@ -628,8 +632,69 @@ static ehl_status pt_residual_api(ehl_ctx* ctx, const double* P, const double* H
 }
 
 // outer iterations of one point-contact grid from (Pw, H0w); done flags in hdone
+// Graph mode 2 for point contact: the grid's iteration is one graph with device-side loops,
+// captured on a private stream (a capture needs one; the caller's may be the legacy stream)
+// forked from and joined back to the context's stream.
+static cudaError_t pt_iterate_device_graph(PtCtx* c, const double* rough, std::vector<int>& hdone) {
+  cudaError_t e = cudaSuccess;
+  if (!c->gs1) {
+    e = cudaStreamCreateWithFlags(&c->gs0, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->gs1, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->gs2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->gev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  const cudaStream_t user = c->st;
+  e = cudaEventRecord(c->gev, user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->gs0, c->gev, 0);
+  if (e != cudaSuccess) return e;
+  c->st = c->gs0;
+  if (!c->graph || c->g_P != c->Pw || c->g_H0 != c->H0w || c->g_rough != rough) {
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    const unsigned long long l0 = thread_launches();
+    e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      PtGraphCounts n;
+      const cudaError_t es = pt_nk_capture_solve(c, c->Pw, c->H0w, rough, c->gs1, c->gs2, n);
+      e = cudaStreamEndCapture(c->st, &g);
+      add_launches(-(long long)(thread_launches() - l0));  // captured, not run
+      if (es != cudaSuccess) e = es;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e == cudaSuccess) {
+        c->gcounts = n;
+        c->g_P = c->Pw;
+        c->g_H0 = c->H0w;
+        c->g_rough = rough;
+      } else {
+        c->graph = nullptr;
+        cudaGetLastError();
+      }
+    }
+  }
+  int loops[8] = {0};
+  if (e == cudaSuccess) e = cudaGraphLaunch(c->graph, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(loops, c->loop, sizeof(loops), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hdone.data(), c->done, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e == cudaSuccess)
+    add_launches(c->gcounts.fixed + (long long)loops[0] * c->gcounts.newton +
+                 (long long)loops[3] * c->gcounts.krylov + (long long)loops[4] * c->gcounts.trial);
+  c->st = user;
+  return e;
+}
+
 static cudaError_t pt_iterate(PtCtx* c, const double* rough, std::vector<int>& hdone) {
   const int ni = c->n_inst;
+  if (c->graph_mode == 2) {
+    hdone.assign(ni, 0);
+    return pt_iterate_device_graph(c, rough, hdone);
+  }
   cudaError_t e = cudaMemsetAsync(c->done, 0, sizeof(int) * ni, c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->iters, 0, sizeof(int) * ni, c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->best, 0x7f, sizeof(double) * ni, c->st);

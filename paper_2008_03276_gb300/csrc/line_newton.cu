@@ -22,6 +22,7 @@
 
 #include "ehl_internal.h"
 #include "line.h"
+#include "graph_loop.h"
 
 namespace ehl {
 
@@ -670,49 +671,6 @@ cudaError_t nk_loop(LineCtx* c, cudaGraphConditionalHandle h, int slot, int tota
                                   c->done, other, c->n_inst);
   note_launch();
   return cudaGetLastError();
-}
-
-// A while-node appended to the graph captured on `outer`: `start` (launched on outer) sets the
-// first condition, the body is captured from what `body` launches on `inner`; c->st follows.
-template <class Start, class Body>
-cudaError_t capture_while(LineCtx* c, cudaStream_t outer, cudaStream_t inner, Start start, Body body,
-                          long long* body_launches) {
-  cudaStreamCaptureStatus stt;
-  cudaGraph_t g = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t nd = 0;
-  cudaError_t e = cudaStreamGetCaptureInfo(outer, &stt, nullptr, &g, nullptr, nullptr, nullptr);
-  if (e != cudaSuccess) return e;
-  if (stt != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
-  cudaGraphConditionalHandle h = 0;
-  e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
-  if (e != cudaSuccess) return e;
-  c->st = outer;
-  e = start(h);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamGetCaptureInfo(outer, &stt, nullptr, &g, &deps, nullptr, &nd);
-  if (e != cudaSuccess) return e;
-  cudaGraphNodeParams p = {};
-  p.type = cudaGraphNodeTypeConditional;
-  p.conditional.handle = h;
-  p.conditional.type = cudaGraphCondTypeWhile;
-  p.conditional.size = 1;
-  cudaGraphNode_t node = nullptr;
-  e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p);
-  if (e != cudaSuccess) return e;
-  cudaGraph_t bg = p.conditional.phGraph_out[0];
-  e = cudaStreamUpdateCaptureDependencies(outer, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-  if (e != cudaSuccess) return e;
-  e = cudaStreamBeginCaptureToGraph(inner, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return e;
-  c->st = inner;
-  const unsigned long long l0 = thread_launches();
-  const cudaError_t eb = body(h);
-  if (body_launches) *body_launches = (long long)(thread_launches() - l0);
-  cudaGraph_t out = nullptr;
-  e = cudaStreamEndCapture(inner, &out);
-  c->st = outer;
-  return eb != cudaSuccess ? eb : e;
 }
 
 }  // namespace

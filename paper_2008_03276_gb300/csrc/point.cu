@@ -592,6 +592,14 @@ cudaError_t pt_alloc(PtCtx* c, void** p, size_t bytes) {
 }
 
 void pt_free(PtCtx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  if (c->gs0) cudaStreamDestroy(c->gs0);
+  if (c->gs1) cudaStreamDestroy(c->gs1);
+  if (c->gs2) cudaStreamDestroy(c->gs2);
+  if (c->gev) cudaEventDestroy(c->gev);
+  c->gs0 = c->gs1 = c->gs2 = nullptr;
+  c->gev = nullptr;
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   pt_adj_free(c);
@@ -712,6 +720,7 @@ ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int 
   A((void**)&c->dots, sizeof(double) * ni * (size_t)c->nvb * (m + 2));
   A((void**)&c->hcol, sizeof(double) * ni * (size_t)(m + 2));
   A((void**)&c->pq_info, sizeof(int) * c->lines);
+  A((void**)&c->loop, sizeof(int) * 8);
   c->pq_r = 0;
   if (ok && autotune) {
     // the fastest partition count of the x-line systems (ny - 2 per instance, order nx - 2), timed

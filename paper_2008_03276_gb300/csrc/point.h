@@ -20,6 +20,11 @@ struct PointInst {
   double xa, ya, h;
 };
 
+// kernels a device-driven solve graph holds outside its loops and in each loop body
+struct PtGraphCounts {
+  long long fixed = 0, newton = 0, krylov = 0, trial = 0;
+};
+
 struct PtCtx {
   int n_inst = 0, nx = 0, ny = 0, NN = 0, n = 0, lines = 0, beta = 2, max_iter = 0, m = 30;
   cudaStream_t st = nullptr;
@@ -37,6 +42,14 @@ struct PtCtx {
   uint8_t* act = nullptr;
   void* pq_ws = nullptr;
   int pq_r = 0;  // partitions per x-line system of the Krylov preconditioner: 0 the rule, else autotuned
+  // graph mode 2: the grid's iteration as one graph with device-side loops
+  int graph_mode = 0;
+  int* loop = nullptr;  // [8] loop counters and totals (newton, krylov, trial, krylov total, trial total)
+  cudaStream_t gs0 = nullptr, gs1 = nullptr, gs2 = nullptr;
+  cudaEvent_t gev = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  const double *g_P = nullptr, *g_H0 = nullptr, *g_rough = nullptr;
+  PtGraphCounts gcounts;
   int* pq_info = nullptr;
   void* fstore = nullptr;
   // Newton-Krylov
@@ -100,5 +113,8 @@ cudaError_t pt_adjoint(PtCtx* c, const double* P, const double* H0, const double
                        double tol, int max_cycles);
 void pt_adj_free(PtCtx* c);
 cudaError_t pt_nk_step(PtCtx* c, double* P, double* H0, const double* rough);
+// graph mode 2: the Newton / GMRES / line-search loops of this grid captured on c->st (capturing)
+cudaError_t pt_nk_capture_solve(PtCtx* c, double* P, double* H0, const double* rough, cudaStream_t s1, cudaStream_t s2,
+                                PtGraphCounts& n);
 
 }  // namespace ehl

@@ -20,6 +20,7 @@
 
 #include "ehl_internal.h"
 #include "point.h"
+#include "graph_loop.h"
 
 namespace ehl {
 
@@ -38,6 +39,8 @@ struct PtView {  // device pointers the vector kernels need
   // y-line stage (yline = 1): rhs and solution of the y-line systems (column-major interior
   // order r_y = (i-1)(ny-2) + (j-1)), their bordered correction zHy (row-major) and den_y, xi_y
   double *rhs_y, *sig_y, *zHy, *deny, *xiy;
+  // device-driven solve: the Krylov index is read from here when not null
+  const int* jd;
 };
 
 __device__ __forceinline__ double nk_block_sum(double v, double* sh) {
@@ -150,6 +153,19 @@ __device__ __forceinline__ double pn_total(const PtView& v, int z, int q, double
   return nk_block_sum(s, sh);
 }
 
+// partial sums of Z_j[0:n] into slot 0, j from v.jd (the device-driven solve)
+__global__ void __launch_bounds__(kNB) k_pn_psum_zj(PtView v) {
+  const int z = blockIdx.y;
+  if (v.skip[z]) return;
+  __shared__ double sh[kNB];
+  const int j = *v.jd;
+  const double* a = v.Z + ((size_t)z * v.m + j) * v.n1;
+  double s = 0.0;
+  NK_FOR(r, v.n) s += a[r];
+  s = nk_block_sum(s, sh);
+  if (threadIdx.x == 0) v.dots[((size_t)z * v.nvb + blockIdx.x) * (v.m + 2)] = s;
+}
+
 // zH = sigma; den = h^2 sum zH (after k_pn_psum of sigma into slot 0); first PAQIF input = V_0[0:n]
 __global__ void __launch_bounds__(kNB) k_pn_border(PtView v) {
   const int z = blockIdx.x;
@@ -167,6 +183,7 @@ __global__ void __launch_bounds__(kNB) k_pn_border(PtView v) {
 
 // xi = (h^2 sum sigma - V_j[n]) / den  (after k_pn_psum of sigma into slot 0)
 __global__ void __launch_bounds__(kNB) k_pn_prec2(PtView v, int j) {
+  if (v.jd) j = *v.jd;
   const int z = blockIdx.x;
   if (v.skip[z]) return;
   __shared__ double sh[kNB];
@@ -182,6 +199,7 @@ __global__ void __launch_bounds__(kNB) k_pn_prec2(PtView v, int j) {
 
 // Z_j = sigma - xi zH on the interior; the nodal copy for the deformation (0 on the boundary)
 __global__ void __launch_bounds__(kNB) k_pn_prec3(PtView v, int j) {
+  if (v.jd) j = *v.jd;
   const int z = blockIdx.y;
   if (v.skip[z]) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -232,6 +250,7 @@ __global__ void __launch_bounds__(kNB) k_pn_yden(PtView v) {
 
 // rhs_y = (V_j - J z1)[0:n] in column-major order (w holds J z1)
 __global__ void __launch_bounds__(kNB) k_pn_yrhs(PtView v, int j) {
+  if (v.jd) j = *v.jd;
   const int z = blockIdx.y;
   if (v.skip[z]) return;
   const double* Vj = v.V + ((size_t)z * (v.m + 1) + j) * v.n1;
@@ -242,6 +261,7 @@ __global__ void __launch_bounds__(kNB) k_pn_yrhs(PtView v, int j) {
 // xi_y = (h^2 sum sig_y - (V_j[n] - w[n])) / den_y (after k_pn_psum of sig_y into slot 0); the
 // border component of Z_j and of the deformation input grows by xi_y
 __global__ void __launch_bounds__(kNB) k_pn_yprec2(PtView v, int j) {
+  if (v.jd) j = *v.jd;
   const int z = blockIdx.x;
   if (v.skip[z]) return;
   __shared__ double sh[kNB];
@@ -259,6 +279,7 @@ __global__ void __launch_bounds__(kNB) k_pn_yprec2(PtView v, int j) {
 
 // Z_j += sig_y - xi_y zHy on the interior; the nodal copy for the deformation (0 on the boundary)
 __global__ void __launch_bounds__(kNB) k_pn_yprec3(PtView v, int j) {
+  if (v.jd) j = *v.jd;
   const int z = blockIdx.y;
   if (v.skip[z]) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -280,6 +301,7 @@ struct PnRowArgs {
   const double *P, *H, *rho, *drho, *deta_rel, *eps, *psia, *psib, *dH;
 };
 __global__ void __launch_bounds__(kNB) k_pn_jv(PtView v, PnRowArgs q, int j) {
+  if (v.jd) j = *v.jd;
   const int z = blockIdx.y;
   if (v.skip[z]) return;
   const PointInst in = v.inst[z];
@@ -341,6 +363,7 @@ __global__ void __launch_bounds__(kNB) k_pn_force(PtView v) {
 
 // partial dot products w . V_i, i = 0..j, into dots slots 0..j
 __global__ void __launch_bounds__(kNB) k_pn_dots(PtView v, int j) {
+  if (v.jd) j = *v.jd;
   const int z = blockIdx.y;
   if (v.skip[z]) return;
   __shared__ double sh[kNB];
@@ -356,6 +379,7 @@ __global__ void __launch_bounds__(kNB) k_pn_dots(PtView v, int j) {
 
 // h_i = sum of the partials; H(:, j) = h (first pass) or += h (second pass)
 __global__ void __launch_bounds__(kNB) k_pn_hsum(PtView v, int j, int pass) {
+  if (v.jd) j = *v.jd;
   const int z = blockIdx.x;
   if (v.skip[z]) return;
   __shared__ double sh[kNB];
@@ -371,6 +395,7 @@ __global__ void __launch_bounds__(kNB) k_pn_hsum(PtView v, int j, int pass) {
 
 // w -= sum_i h_i V_i
 __global__ void __launch_bounds__(kNB) k_pn_orth(PtView v, int j) {
+  if (v.jd) j = *v.jd;
   const int z = blockIdx.y;
   if (v.skip[z]) return;
   const double* hz = v.hcol + (size_t)z * (v.m + 2);
@@ -396,6 +421,7 @@ __global__ void __launch_bounds__(kNB) k_pn_norm(PtView v) {
 
 // H(j+1, j) = |w|; Givens rotations; convergence; 1/|w| for the normalisation
 __global__ void __launch_bounds__(kNB) k_pn_givens(PtView v, int j) {
+  if (v.jd) j = *v.jd;
   const int z = blockIdx.x;
   if (v.skip[z]) return;
   __shared__ double sh[kNB];
@@ -428,6 +454,7 @@ __global__ void __launch_bounds__(kNB) k_pn_givens(PtView v, int j) {
 
 // V_{j+1} = w / |w|, next PAQIF input
 __global__ void __launch_bounds__(kNB) k_pn_next(PtView v, int j) {
+  if (v.jd) j = *v.jd;
   const int z = blockIdx.y;
   if (v.skip[z]) return;
   const double a = v.hcol[(size_t)z * (v.m + 2) + v.m + 1];
@@ -597,6 +624,7 @@ static PtView pt_view(PtCtx* c, const int* skip) {
   v.zHy = c->zHy;
   v.deny = c->deny;
   v.xiy = c->xiy;
+  v.jd = nullptr;
   return v;
 }
 
@@ -794,6 +822,164 @@ cudaError_t pt_nk_step(PtCtx* c, double* P, double* H0, const double* rough) {
   return cudaGetLastError();
 }
 
+
+// ============================================= device-driven solve (graph mode 2)
+// The Newton steps of one grid, their GMRES iterations and line-search trials as three nested
+// while-nodes of one CUDA graph (as for line contact): the kernels of pt_nk_step, the Krylov index
+// read from a device counter, each loop's condition set by k_nk_loop.
+namespace {
+cudaError_t pn_loop(PtCtx* c, cudaGraphConditionalHandle h, int slot, int total_slot, int cap, int next,
+                    const int* other) {
+  k_nk_loop<<<1, 256, 0, c->st>>>(h, c->loop + slot, total_slot >= 0 ? c->loop + total_slot : nullptr, cap, next,
+                                  c->done, other, c->n_inst);
+  note_launch();
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t pt_nk_capture_solve(PtCtx* c, double* P, double* H0, const double* rough, cudaStream_t s1, cudaStream_t s2,
+                                PtGraphCounts& n) {
+  const int ni = c->n_inst;
+  const cudaStream_t s0 = c->st;
+  const dim3 gv(c->nvb, ni), gn((c->NN + 255) / 256, ni);
+  PtView vd = pt_view(c, c->done);
+  PtView vs = pt_view(c, c->skip);
+  vs.jd = c->loop + 1;
+  const PnRowArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH};
+  const unsigned long long l0 = thread_launches();
+  cudaError_t e = cudaMemsetAsync(c->done, 0, sizeof(int) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->iters, 0, sizeof(int) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->best, 0x7f, sizeof(double) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->stall, 0, sizeof(int) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->loop, 0, sizeof(int) * 8, s0);
+  auto krylov_body = [&](cudaGraphConditionalHandle hk) -> cudaError_t {
+    k_pn_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, c->gm_conv, c->skip, ni);
+    note_launch();
+    cudaError_t ee = pn_paqif(c, c->rhs, c->sigma, false);
+    if (ee != cudaSuccess) return ee;
+    k_pn_psum<<<gv, kNB, 0, c->st>>>(vs, c->sigma, (size_t)c->n, 0, c->skip);
+    note_launch();
+    k_pn_prec2<<<ni, kNB, 0, c->st>>>(vs, 0);
+    note_launch();
+    k_pn_prec3<<<gn, 256, 0, c->st>>>(vs, 0);
+    note_launch();
+    if (c->yline) {
+      ee = pt_deform_dir(c, c->znode, c->zh0, c->skip);
+      if (ee != cudaSuccess) return ee;
+      k_pn_jv<<<gv, kNB, 0, c->st>>>(vs, q, 0);
+      note_launch();
+      k_pn_psum_zj<<<gv, kNB, 0, c->st>>>(vs);
+      note_launch();
+      k_pn_force<<<ni, kNB, 0, c->st>>>(vs);
+      note_launch();
+      k_pn_yrhs<<<gv, kNB, 0, c->st>>>(vs, 0);
+      note_launch();
+      ee = pn_paqif_y(c, false);
+      if (ee != cudaSuccess) return ee;
+      k_pn_psum<<<gv, kNB, 0, c->st>>>(vs, c->sig_y, (size_t)c->n, 0, c->skip);
+      note_launch();
+      k_pn_yprec2<<<ni, kNB, 0, c->st>>>(vs, 0);
+      note_launch();
+      k_pn_yprec3<<<gn, 256, 0, c->st>>>(vs, 0);
+      note_launch();
+    }
+    ee = pt_deform_dir(c, c->znode, c->zh0, c->skip);
+    if (ee != cudaSuccess) return ee;
+    k_pn_jv<<<gv, kNB, 0, c->st>>>(vs, q, 0);
+    note_launch();
+    k_pn_psum_zj<<<gv, kNB, 0, c->st>>>(vs);
+    note_launch();
+    k_pn_force<<<ni, kNB, 0, c->st>>>(vs);
+    note_launch();
+    for (int pass = 0; pass < 2; ++pass) {
+      k_pn_dots<<<gv, kNB, 0, c->st>>>(vs, 0);
+      note_launch();
+      k_pn_hsum<<<ni, kNB, 0, c->st>>>(vs, 0, pass);
+      note_launch();
+      k_pn_orth<<<gv, kNB, 0, c->st>>>(vs, 0);
+      note_launch();
+    }
+    k_pn_norm<<<gv, kNB, 0, c->st>>>(vs);
+    note_launch();
+    k_pn_givens<<<ni, kNB, 0, c->st>>>(vs, 0);
+    note_launch();
+    k_pn_next<<<gv, kNB, 0, c->st>>>(vs, 0);
+    note_launch();
+    return pn_loop(c, hk, 1, 3, c->m, 1, c->gm_conv);
+  };
+  auto trial_body = [&](cudaGraphConditionalHandle ht) -> cudaError_t {
+    k_pn_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, c->lsdone, c->skip, ni);
+    note_launch();
+    k_pn_trial<<<gn, 256, 0, c->st>>>(vs, P, H0);
+    note_launch();
+    cudaError_t ee = pt_state(c, c->Pt, c->H0t, rough, c->skip);
+    if (ee == cudaSuccess) ee = pt_finalize(c, nullptr, nullptr);
+    if (ee != cudaSuccess) return ee;
+    k_pn_merit1<<<gv, kNB, 0, c->st>>>(vs);
+    note_launch();
+    k_pn_merit2<<<ni, kNB, 0, c->st>>>(vs, H0);
+    note_launch();
+    k_pn_accept<<<gn, 256, 0, c->st>>>(vs, P);
+    note_launch();
+    return pn_loop(c, ht, 2, 4, 64, 1, c->lsdone);
+  };
+  auto newton_body = [&](cudaGraphConditionalHandle hn) -> cudaError_t {
+    const unsigned long long m0 = thread_launches();
+    cudaError_t ee = pt_state(c, P, H0, rough, c->done);
+    if (ee == cudaSuccess) ee = pt_finalize(c, c->done, c->iters);
+    if (ee == cudaSuccess) ee = pt_jac_band(c, P, c->band, c->act, c->jh, c->dg, c->done);
+    if (ee != cudaSuccess) return ee;
+    k_pn_setup<<<gv, kNB, 0, c->st>>>(vd, P);
+    note_launch();
+    k_pn_setup2<<<ni, kNB, 0, c->st>>>(vd);
+    note_launch();
+    k_pn_scale<<<gv, kNB, 0, c->st>>>(vd, c->V, (size_t)(c->m + 1) * (c->n + 1), 0, c->done);
+    note_launch();
+    if (c->yline) {
+      ee = pt_jac_yband(c, P, c->act, c->dg, c->band_y, 1, c->done);
+      if (ee != cudaSuccess) return ee;
+      k_pn_ytrans<<<gv, kNB, 0, c->st>>>(vd, c->rhs, c->rhs_y, c->done);
+      note_launch();
+      ee = pn_paqif_y(c, true);
+      if (ee != cudaSuccess) return ee;
+      k_pn_ytrans_back<<<gv, kNB, 0, c->st>>>(vd, c->done);
+      note_launch();
+      k_pn_psum<<<gv, kNB, 0, c->st>>>(vd, c->zHy, (size_t)c->n, 0, c->done);
+      note_launch();
+      k_pn_yden<<<ni, kNB, 0, c->st>>>(vd);
+      note_launch();
+    }
+    ee = pn_paqif(c, c->rhs, c->sigma, true);
+    if (ee != cudaSuccess) return ee;
+    k_pn_psum<<<gv, kNB, 0, c->st>>>(vd, c->sigma, (size_t)c->n, 0, c->done);
+    note_launch();
+    k_pn_border<<<ni, kNB, 0, c->st>>>(vd);
+    note_launch();
+    const cudaStream_t here = c->st;
+    ee = capture_while(
+        c, here, s2, [&](cudaGraphConditionalHandle hk) { return pn_loop(c, hk, 1, -1, c->m, 0, c->gm_conv); },
+        krylov_body, &n.krylov);
+    if (ee != cudaSuccess) return ee;
+    k_pn_ysolve<<<ni, kNB, 0, c->st>>>(vd);
+    note_launch();
+    k_pn_delta<<<gv, kNB, 0, c->st>>>(vd);
+    note_launch();
+    ee = capture_while(
+        c, here, s2, [&](cudaGraphConditionalHandle ht) { return pn_loop(c, ht, 2, -1, 64, 0, c->lsdone); },
+        trial_body, &n.trial);
+    if (ee != cudaSuccess) return ee;
+    ee = pn_loop(c, hn, 0, -1, c->max_iter, 1, nullptr);
+    n.newton = (long long)(thread_launches() - m0) - n.krylov - n.trial;
+    return ee;
+  };
+  if (e == cudaSuccess)
+    e = capture_while(
+        c, s0, s1, [&](cudaGraphConditionalHandle hn) { return pn_loop(c, hn, 0, -1, c->max_iter, 0, nullptr); },
+        newton_body, nullptr);
+  c->st = s0;
+  n.fixed = (long long)(thread_launches() - l0) - n.newton - n.krylov - n.trial;
+  return e;
+}
 
 // ===================================================================== adjoint
 // Sensitivities of a converged point-contact state, as for line contact: the

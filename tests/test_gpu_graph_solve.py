@@ -76,3 +76,40 @@ def test_high_load_nested_grids():
     P2, H2, it2, r2, c2, _, _ = solve(2, nx=1025, M=200.0, limiter=1, halfband=8, tol=1e-8)
     assert c2 == 0
     assert np.max(np.abs(r2)) <= 1e-8
+
+
+def point_solve(graph, n=33, **kw):
+    q = dict(nx=n, ny=n, M=20.0, L=10.0, limiter=0, halfband=2, method=1, tol=1e-11, max_iter=80,
+             coarse_min_nodes=17, krylov_dim=40)
+    q.update(kw)
+    ctx = ops.Context(ops.default_params(2, graph=graph, **q))
+    P, H0, iters, res, code = ctx.solve(check=False)
+    torch.cuda.synchronize()
+    return P.cpu().numpy(), H0.cpu().numpy(), iters.cpu().numpy(), res.cpu().numpy(), code
+
+
+@pytest.mark.parametrize("deform,yline", [(0, 0), (1, 0), (1, 1)])
+def test_point_matches_host_driven_and_oracle(deform, yline):
+    from oracle import point_ref as pr
+    pb = pr.PointProblem(33, 33, 20.0, 10.0)
+    Pr, H0r, info = pr.solve(pb, tol=1e-11)
+    assert info["converged"]
+    P2, H2, it2, r2, c2 = point_solve(2, deform=deform, yline=yline)
+    P0, H00, it0, r0, c0 = point_solve(0, deform=deform, yline=yline)
+    assert c2 == 0 and c0 == 0
+    assert np.array_equal(it2, it0)
+    assert np.max(np.abs(P2 - P0)) <= 1e-12 * np.max(P0)
+    assert np.max(np.abs(P2[0, 1:-1, 1:-1] - pb.full(Pr)[1:-1, 1:-1].T)) <= 1e-8 * np.max(Pr)
+    assert abs(H2[0] - H0r) <= 1e-8 * abs(H0r)
+
+
+def test_point_257_fft_device_driven():
+    from oracle import point_ref as pr
+    n = 257
+    P, H0, it, res, code = point_solve(2, n=n, M=100.0, tol=1e-8, max_iter=60, coarse_min_nodes=33, krylov_dim=200,
+                                       deform=1, autotune=1)
+    assert code == 0
+    pb = pr.PointProblem(n, n, 100.0, 10.0)
+    Pint = P[0].T[1:-1, 1:-1].ravel()
+    R = pr.residual(pb, Pint, float(H0[0]))
+    assert np.max(np.abs(np.minimum(Pint, R))) <= max(2e-8, pr.rounding_floor(pb, Pint, float(H0[0])))
