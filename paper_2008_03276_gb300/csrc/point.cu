@@ -721,6 +721,7 @@ ehl_status pt_init(PtCtx* c, const std::vector<PointInst>& insts, int beta, int 
   A((void**)&c->hcol, sizeof(double) * ni * (size_t)(m + 2));
   A((void**)&c->pq_info, sizeof(int) * c->lines);
   A((void**)&c->loop, sizeof(int) * 8);
+  A((void**)&c->jc, sizeof(double) * 4 * NNt);
   c->pq_r = 0;
   if (ok && autotune) {
     // the fastest partition count of the x-line systems (ny - 2 per instance, order nx - 2), timed

@@ -45,6 +45,7 @@ struct PtCtx {
   // graph mode 2: the grid's iteration as one graph with device-side loops
   int graph_mode = 0;
   int* loop = nullptr;  // [8] loop counters and totals (newton, krylov, trial, krylov total, trial total)
+  double* jc = nullptr; // [n_inst][NN][4] Jacobian-product factors of the current Newton step
   cudaStream_t gs0 = nullptr, gs1 = nullptr, gs2 = nullptr;
   cudaEvent_t gev = nullptr;
   cudaGraphExec_t graph = nullptr;

@@ -41,6 +41,8 @@ struct PtView {  // device pointers the vector kernels need
   double *rhs_y, *sig_y, *zHy, *deny, *xiy;
   // device-driven solve: the Krylov index is read from here when not null
   const int* jd;
+  // per node, fixed for a Newton step: drho H, 3 eps / H, eps (drho / rho - deta), 1 / d (interior)
+  double* jc;
 };
 
 __device__ __forceinline__ double nk_block_sum(double v, double* sh) {
@@ -300,6 +302,28 @@ __global__ void __launch_bounds__(kNB) k_pn_yprec3(PtView v, int j) {
 struct PnRowArgs {
   const double *P, *H, *rho, *drho, *deta_rel, *eps, *psia, *psib, *dH;
 };
+// The direction-independent factors of the Jacobian product, once per Newton step, so that a
+// Krylov product needs no float64 division (the FP64 pipe runs at 1/64 of the FP32 rate)
+__global__ void __launch_bounds__(256) k_pn_jvcoef(PtView v, PnRowArgs q) {
+  const int z = blockIdx.y;
+  if (v.done[z]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= v.NN) return;
+  const size_t k = (size_t)z * v.NN + t;
+  const double e = q.eps[k], Hk = q.H[k];
+  double4 c;
+  c.x = q.drho[k] * Hk;
+  c.y = 3.0 * e / Hk;
+  c.z = e * (q.drho[k] / q.rho[k] - q.deta_rel[k]);
+  c.w = 0.0;
+  const int jj = t / v.nx, ii = t % v.nx;
+  if (ii >= 1 && ii <= v.nx - 2 && jj >= 1 && jj <= v.ny - 2) {
+    const int r = (jj - 1) * (v.nx - 2) + (ii - 1);
+    c.w = 1.0 / v.dg[(size_t)z * v.n + r];
+  }
+  reinterpret_cast<double4*>(v.jc)[k] = c;
+}
+
 __global__ void __launch_bounds__(kNB) k_pn_jv(PtView v, PnRowArgs q, int j) {
   if (v.jd) j = *v.jd;
   const int z = blockIdx.y;
@@ -308,7 +332,7 @@ __global__ void __launch_bounds__(kNB) k_pn_jv(PtView v, PnRowArgs q, int j) {
   const int nx = v.nx;
   const size_t base = (size_t)z * v.NN;
   const double* Zj = v.Z + ((size_t)z * v.m + j) * v.n1;
-  const double h = in.h;
+  const double ih = 1.0 / in.h, ih2 = ih * ih;
   NK_FOR(r, v.n) {
     const size_t o = (size_t)z * v.n + r;
     const int i = r % (nx - 2) + 1, jj = r / (nx - 2) + 1;
@@ -319,13 +343,15 @@ __global__ void __launch_bounds__(kNB) k_pn_jv(PtView v, PnRowArgs q, int j) {
       auto idx = [&](int p, int qq) { return base + (size_t)qq * nx + p; };
       auto dH = [&](int p, int qq) { return q.dH[idx(p, qq)]; };
       auto zn = [&](int p, int qq) { return v.znode[idx(p, qq)]; };
+      const double4* jc = reinterpret_cast<const double4*>(v.jc);
       auto dU = [&](int p, int qq) {
         const size_t k = idx(p, qq);
-        return q.rho[k] * dH(p, qq) + q.drho[k] * q.H[k] * zn(p, qq);
+        return q.rho[k] * dH(p, qq) + jc[k].x * zn(p, qq);
       };
       auto dE = [&](int p, int qq) {
         const size_t k = idx(p, qq);
-        return (3.0 * q.eps[k] / q.H[k]) * dH(p, qq) + q.eps[k] * (q.drho[k] / q.rho[k] - q.deta_rel[k]) * zn(p, qq);
+        const double4 cc = jc[k];
+        return cc.y * dH(p, qq) + cc.z * zn(p, qq);
       };
       auto dF = [&](int f, int qq) {
         const double d0 = dU(f, qq);
@@ -338,12 +364,12 @@ __global__ void __launch_bounds__(kNB) k_pn_jv(PtView v, PnRowArgs q, int j) {
       const double ex1 = 0.5 * (e + q.eps[c + 1]), ex0 = 0.5 * (q.eps[c - 1] + e);
       const double ey1 = 0.5 * (e + q.eps[c + nx]), ey0 = 0.5 * (q.eps[c - nx] + e);
       const double dEc = dE(i, jj), z0 = zn(i, jj);
-      const double dC = (dF(i, jj) - dF(i - 1, jj)) / h;
+      const double dC = (dF(i, jj) - dF(i - 1, jj)) * ih;
       const double dq = 0.5 * (dEc + dE(i + 1, jj)) * (q.P[c + 1] - p) + ex1 * (zn(i + 1, jj) - z0) -
                         0.5 * (dE(i - 1, jj) + dEc) * (p - q.P[c - 1]) - ex0 * (z0 - zn(i - 1, jj)) +
                         0.5 * (dEc + dE(i, jj + 1)) * (q.P[c + nx] - p) + ey1 * (zn(i, jj + 1) - z0) -
                         0.5 * (dE(i, jj - 1) + dEc) * (p - q.P[c - nx]) - ey0 * (z0 - zn(i, jj - 1));
-      out = (dC - dq / (h * h)) / v.dg[o];
+      out = (dC - dq * ih2) * jc[c].w;
     }
     v.w[(size_t)z * v.n1 + r] = out;
   }
@@ -625,6 +651,7 @@ static PtView pt_view(PtCtx* c, const int* skip) {
   v.deny = c->deny;
   v.xiy = c->xiy;
   v.jd = nullptr;
+  v.jc = c->jc;
   return v;
 }
 
@@ -685,6 +712,11 @@ cudaError_t pt_nk_step(PtCtx* c, double* P, double* H0, const double* rough) {
   note_launch();
   k_pn_setup2<<<ni, kNB, 0, c->st>>>(vd);
   note_launch();
+  {
+    const PnRowArgs qc{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH};
+    k_pn_jvcoef<<<gn, 256, 0, c->st>>>(vd, qc);
+    note_launch();
+  }
   k_pn_scale<<<gv, kNB, 0, c->st>>>(vd, c->V, (size_t)(c->m + 1) * (c->n + 1), 0, c->done);
   note_launch();
   if (c->yline) {
@@ -932,6 +964,8 @@ cudaError_t pt_nk_capture_solve(PtCtx* c, double* P, double* H0, const double* r
     k_pn_setup<<<gv, kNB, 0, c->st>>>(vd, P);
     note_launch();
     k_pn_setup2<<<ni, kNB, 0, c->st>>>(vd);
+    note_launch();
+    k_pn_jvcoef<<<gn, 256, 0, c->st>>>(vd, q);
     note_launch();
     k_pn_scale<<<gv, kNB, 0, c->st>>>(vd, c->V, (size_t)(c->m + 1) * (c->n + 1), 0, c->done);
     note_launch();
