@@ -178,6 +178,30 @@ __device__ __forceinline__ df df_from_double(double d) {
   return r;
 }
 
+// The same split as df_from_double, bit for bit, without branches: every range's result is formed
+// and the right one selected.  lo = rest * 2^p with p = fe - 179 scaled in two steps (both factors
+// normal floats for p >= -152), which is the one multiply of the fast window whenever the product
+// is normal.  For code whose throughput suffers from the branches (long straight-line kernels).
+__device__ __forceinline__ df df_from_double_sel(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hw = (unsigned)(b >> 32);
+  const unsigned lw = (unsigned)b;
+  const unsigned sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7ffu);
+  const int fe = e - 896;  // float biased exponent of hi
+  const unsigned m23 = ((hw & 0xfffffu) << 3) | (lw >> 29);
+  const bool normal = (e >= 923) && (e < 1151);  // |d| in [2^-100, 2^128)
+  const int p = normal ? fe - 179 : 0;
+  const float s1 = __uint_as_float((unsigned)((p / 2) + 127) << 23);
+  const float s2 = __uint_as_float((unsigned)((p - p / 2) + 127) << 23);
+  const float lo = __fmul_rn(__fmul_rn(__uint2float_rn(lw & 0x1fffffffu), s1), s2);
+  const unsigned big = sign | 0x7f800000u | ((e == 0x7ff && ((hw & 0xfffffu) | lw)) ? 0x400000u : 0u);
+  df r;
+  r.hi = __uint_as_float(normal ? (sign | ((unsigned)fe << 23) | m23) : (e >= 1151 ? big : sign));
+  r.lo = normal ? __uint_as_float(__float_as_uint(lo) | sign) : 0.f;
+  return r;
+}
+
 __device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
 
 }  // namespace ehl

@@ -74,7 +74,7 @@ int main(int argc, char** argv) {
   const int n = std::atoi(argv[2]);
   g_state = std::strtoull(argv[3], nullptr, 10);
   for (int k = 0; k < n; ++k) {
-    if (!std::strcmp(op, "from_double")) {
+    if (!std::strcmp(op, "from_double") || !std::strcmp(op, "from_double_sel")) {
       double d;
       const int kind = k % 8;
       if (kind < 5) {
@@ -88,7 +88,7 @@ int main(int argc, char** argv) {
                              0x1p+128, 0x1p-100, 0x1.fffffffffffffp-101, 4.9e-324, 0x1p-74, 0x1.fffffffp-75};
         d = sp[(k / 8) % (int)(sizeof(sp) / sizeof(sp[0]))];
       }
-      const df r = ehl::df_from_double(d);
+      const df r = std::strcmp(op, "from_double") ? ehl::df_from_double_sel(d) : ehl::df_from_double(d);
       std::printf("%016llx", dbits(d));
       pdf(r);
       std::printf("\n");

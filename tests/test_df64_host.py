@@ -113,6 +113,15 @@ def test_split_of_float64(harness):
             assert lo == nearest_float(F(d) - F(hi)), dh
 
 
+def test_branch_free_split_is_the_same_split(harness):
+    """df_from_double_sel (no branches, for long straight-line kernels) returns the bits of
+    df_from_double on every input class the split test draws (fast window, all of float64, the
+    flush edge, zeros, infinities, NaN, the range limits)."""
+    a = run(harness, "from_double", 40000, 11)
+    b = run(harness, "from_double_sel", 40000, 11)
+    assert a == b
+
+
 @pytest.mark.parametrize("op,bound", [("add", 9), ("mul", 12), ("div", 24), ("mul_f", 3)])
 def test_binary_operations_within_their_bounds(harness, op, bound):
     worst = F(0)
