@@ -57,6 +57,7 @@
 
 #include "df64.cuh"
 #include "ehl_internal.h"
+#include "paqif_pair.h"
 
 namespace ehl {
 
@@ -1105,7 +1106,11 @@ static bool geom(int n_sys, int n, int beta, int parts, Geom& g) {
 size_t paqif_stack_bytes(int n_sys, int n, int beta, int parts) {
   Geom g;
   if (!geom(n_sys, n, beta, parts, g)) return 0;
-  return (size_t)g.grid * groups_per_cta(beta) * (size_t)g.sp * (size_t)(2 * beta + 1) * sizeof(float4);
+  const size_t own = (size_t)g.grid * groups_per_cta(beta) * (size_t)g.sp * (size_t)(2 * beta + 1) * sizeof(float4);
+  // the automatic choice may run the lane-pair kernel (modes 0 and 1): room for its stack too
+  const int rp = parts == 0 ? paqif_pair_parts(n_sys, n, beta, 0, false, false) : 0;
+  const size_t pair = rp > 0 ? paqif_pair_stack_bytes(n_sys, n, beta, rp) : 0;
+  return own > pair ? own : pair;
 }
 
 static size_t reduced_store_bytes(const Geom& g, int beta) {
@@ -1225,7 +1230,16 @@ static cudaError_t dispatch4(const PaqifLaunch& L, cudaStream_t st, void* fstore
   }
 }
 
-cudaError_t launch_paqif(const PaqifLaunch& L, cudaStream_t st) { return dispatch4(L, st, nullptr, false); }
+// The automatic choice (parts = 0) of a solve in modes 0 and 1 with float64 sweeps, b <= 4 and a
+// band array on a 16-byte boundary runs the lane-pair kernel (paqif_pair.cu); everything else (a
+// requested partition count, mode 2, float32 sweeps, a stored factorization, b > 4) this file's.
+cudaError_t launch_paqif(const PaqifLaunch& L, cudaStream_t st) {
+  if (L.parts == 0 && (reinterpret_cast<uintptr_t>(L.band) & 15u) == 0) {
+    const int rp = paqif_pair_parts(L.n_sys, L.n, L.beta, L.mode, L.f32, false);
+    if (rp > 0) return launch_paqif_pair(L, rp, st);
+  }
+  return dispatch4(L, st, nullptr, false);
+}
 
 cudaError_t launch_paqif_factor(const PaqifLaunch& L, void* fstore, cudaStream_t st) {
   if (L.mode == 2 || !fstore) return cudaErrorInvalidValue;
