@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(kPairThreads, PC<B>::MINB) paqif_pair_kernel(P
   // ---- Z0 sweep: levels sf-1 .. 0, from the block's ends towards its middle; the stack levels
   // are read D levels ahead into a register ring (the window's registers are free by now)
   {
-    constexpr int D = 4;
+    constexpr int D = 2;
     const float4* st = p.stk;
     float4 ring4[D][C::NQ];
 #pragma unroll
