@@ -47,12 +47,12 @@ PAQIF_NSYS, PAQIF_N, PAQIF_BETA, PAQIF_MODE = 4096, 1024, 4, 1
 EHL = dict(N=1025, M=200.0, L=10.0, limiter=1, beta=8, tol=1e-8)
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes (read + write) of one full-size paqif4_kernel<4, double-float> launch from the ncu
-# capture summarised in profiles/, valid only for the kernel sources with these
-# sha256 prefixes; any other source reports traffic = null.
-PAQIF_TRAFFIC = {("7ec492ea359502ff", "6a71297bc569ed85"): 564364800 + 309009152}
+# DRAM bytes (read + write) of one full-size paqif_pair_kernel<4> launch (leg A) from the ncu
+# capture summarised in profiles/, valid only for the kernel sources with these sha256
+# prefixes; any other source reports traffic = null.
+PAQIF_TRAFFIC = {('f7d8f0ad2cfa04b3', '7992305e7ad41559'): 641414912 + 351703040}
 # smsp__inst_executed.sum of the same launch and capture: the kernel is bound by instruction issue
-PAQIF_WARP_INSTRUCTIONS = {("7ec492ea359502ff", "6a71297bc569ed85"): 852480330}
+PAQIF_WARP_INSTRUCTIONS = {('f7d8f0ad2cfa04b3', '7992305e7ad41559'): 302703616}
 SCHEDULERS = 152 * 4  # SMs x warp schedulers per SM, one warp instruction issued per scheduler and cycle
 
 
@@ -64,7 +64,7 @@ def _paqif_source_key():
             return hashlib.sha256(f.read()).hexdigest()[:16]
 
     try:
-        return h("paqif4.cu"), h("df64.cuh")
+        return h("paqif_pair.cu"), h("df64.cuh")
     except OSError:
         return None
 
@@ -379,7 +379,7 @@ def run_ours(args):
         "mixed_precision": mixed,
         "roofline": {"bound": "hbm", "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "traffic": paqif_traffic(),
-                     "kernel": "paqif4_kernel<4> (leg A)", "peak_source": src, "issue": issue},
+                     "kernel": "paqif_pair_kernel<4> (leg A)", "peak_source": src, "issue": issue},
         "e2e": {"value": round(job_rate(world, B, e2e_b), 3) if e2e_b else None, "unit": "converged solves/s",
                 "h2d_bytes_per_step": B * EHL["N"] * 8, "d2h_bytes_per_step": B * (EHL["N"] + 1 + 2) * 8 + B * 4,
                 "inputs": "the surface roughness of every instance (zeros: smooth surfaces) copied from pinned "
