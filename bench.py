@@ -80,6 +80,45 @@ def issue_fraction(warp_instructions, ms, sm_mhz):
     return warp_instructions / (SCHEDULERS * sm_mhz * 1e6 * ms * 1e-3)
 
 
+def resolve_bytes(n_sys, n, beta):
+    """Algorithmic bytes of one resolve with a stored factorization (Sec. 2.2.1-2.2.3): per level
+    (two unknowns) the W0 multipliers and Pi^-1 rows (2 beta + 2 double-float pairs) and the folded
+    Z0 rows (2 beta + 1 pairs) read, the level's folded rhs pair written; rhs read, x written."""
+    levels = (n + 1) // 2
+    return n_sys * (levels * ((2 * beta + 2) + (2 * beta + 1) + 1) * 16 + 2 * n * 8)
+
+
+def resolve_roofline(ops, inputs, torch, dev, hbm, reps=10):
+    """The preconditioner resolve of leg B alone: the PAQIF kernel that solves with a stored
+    factorization (paqif4_solve_kernel<8>), on leg B's shape (512 systems of the N = 1025 grid's
+    1023 unknowns, beta = 8; seeded diagonally dominant bands), timed with CUDA events around the
+    one launch of ehl_paqif_resolve."""
+    n_sys, n, beta = 512, EHL["N"] - 2, EHL["beta"]
+    band_h, rhs_h = inputs.dd_band_systems(n_sys, n, beta, seed=11)
+    band, rhs = torch.from_numpy(band_h).to(dev), torch.from_numpy(rhs_h).to(dev)
+    x, info, fac = ops.paqif_factor(band, rhs, beta, 0)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        ops.paqif_resolve(fac, rhs, beta, 0, x=x)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda._sleep(200000)  # the stream is busy while the host records and launches
+        e0.record(stream)
+        ops.paqif_resolve(fac, rhs, beta, 0, x=x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    nb = resolve_bytes(n_sys, n, beta)
+    gbs = nb / (ms * 1e-3) / 1e9
+    return {"kernel": "paqif4_solve_kernel<8> (leg B's preconditioner resolve)", "n_sys": n_sys, "n": n,
+            "beta": beta, "partitions": ops.paqif_partitions(n_sys, n, beta), "bytes_per_launch": nb,
+            "ms": round(ms, 4), "achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+            "info_ok": bool((info == 0).all().item())}
+
+
 def paqif_bytes(n_sys, n, beta):
     """Algorithmic bytes of one batched solve: band + rhs read, x written."""
     return n_sys * (n * (2 * beta + 1) * 8 + 2 * n * 8)
@@ -390,6 +429,11 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s": round(wall, 3),
     }
+    if world == 1 and B > 0:
+        try:
+            line["paqif_resolve"] = resolve_roofline(ops, inputs, torch, dev, hbm)
+        except Exception as ex:  # a failed side measurement must not lose the line
+            line["paqif_resolve"] = {"error": f"{type(ex).__name__}: {ex}"}
     if world == 1 and not args.no_configs:
         line["configs"] = config_legs(ops, inputs, torch, dev, paqif=(band, rhs))
         c3 = line["configs"].get("C3", {})
@@ -517,13 +561,15 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
     Href = None
     for key, prec, deform in (("C4", 0, 0), ("C4_mixed", 2, 0), ("C4_fft", 0, 1)):
         p = ops.default_params(2, nx=257, ny=257, M=100.0, L=10.0, limiter=0, halfband=2, method=1, tol=1e-8,
-                               max_iter=60, coarse_min_nodes=33, precision=prec, deform=deform, autotune=deform)
+                               max_iter=60, coarse_min_nodes=33, precision=prec, deform=deform, autotune=deform,
+                               graph=2 if deform else 0)
         ctx = ops.Context(p)
         ms, out = _timed(torch, lambda: ctx.solve(check=False), warm=0 if deform == 0 else 1)
         d = dict(workload="point contact 257x257, M=100, L=10, minmod, beta=2 (x-line PAQIF preconditioner), "
                           "tol 1e-8, nested 33-65-129-257",
                  precision=PRECISION[prec], deformation=("float64 FFT convolution (512 x 512 cyclic); x-line "
                                                          "partition count autotuned" if deform else "direct sum"),
+                 loop="device-driven graph per grid (graph = 2)" if deform else "host-driven",
                  ms=round(ms, 1), solves_per_s=round(1e3 / ms, 4))
         d.update(summary(out[2], out[3], out[4], 1e-8))
         _, H, _ = ctx.residual(out[0], out[1])

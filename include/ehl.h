@@ -65,8 +65,9 @@ unsigned long long ehl_kernel_launches(void);
  * from the middle of the matrix outwards, W0 Y = F solved from the middle
  * outwards and Z0 U = Y from both ends towards the middle), Sec. 2.2.2 and
  * Sec. 2.2.4 Steps 5 and 7 (projection of the computed solution onto
- * U >= 0).  One system is one partition (r = 1): the projection follows the
- * full solve.
+ * U >= 0).  The library picks the partition count r of Sec. 2.2.4 from the
+ * batch shape (ehl_paqif_partitions); every r gives the same solution up to
+ * rounding, and the projection follows the full solve.
  *
  * Solves n_sys independent banded systems A_s x_s = b_s of order n with
  * half-bandwidth beta.
@@ -159,6 +160,36 @@ ehl_status ehl_paqif_partitions(int n_sys, int n, int beta, int partitions, int*
  * EHL_EINVAL, EHL_ENOMEM, EHL_ECUDA or a status of the timed solves. */
 ehl_status ehl_paqif_autotune(int n_sys, int n, int beta, int mode, const double* band, const double* rhs,
                               double* x, int reps, void* stream, int* best_r, float* ms_per_r);
+
+/* Factor once, resolve many (Sec. 2.2.1-2.2.3: the factorization L0 = W0 Z0
+ * does not depend on the right-hand side; a new F runs the W0 Y = F sweep
+ * with the stored multipliers and the Z0 U = Y sweep with the stored folded
+ * pivot rows, and the partitioned reduced system of Sec. 2.2.4 with its
+ * stored block factors).  This is what a Newton iteration's preconditioner
+ * does between two Jacobian updates.
+ *
+ * ehl_paqif_factor_size: bytes of the factorization object of a batch
+ *   (the per-level multipliers and Pi^-1 rows, the folded Z0 rows and the
+ *   reduced-system factors, double-float), for the automatic partition
+ *   count of ehl_paqif_partitions(..., 0, ...).
+ * ehl_paqif_factor: factors the n_sys systems (band as for ehl_paqif_solve)
+ *   into `factor` (device, >= ehl_paqif_factor_size bytes, 256-byte
+ *   aligned, owned by the caller and kept unchanged until the next factor
+ *   call on it) and solves them for `rhs` into x.
+ * ehl_paqif_resolve: solves the factored systems for a new rhs into x; reads
+ *   `factor` (and writes the rhs part of its folded rows: two resolves on
+ *   one factorization must not overlap on the GPU).  band is not needed.
+ *   mode  0 or 1 as for ehl_paqif_solve (no active rows, no LCP loop).
+ *   info  (nullable) [n_sys] int32: EHL_INFO_* (the factor call reports a
+ *         singular pivot; a resolve reports non-finite results).
+ * Same limits as ehl_paqif_solve; stream-ordered, nothing is allocated.
+ * Returns EHL_EINVAL for bad sizes, modes, NULL or misaligned pointers or a
+ * factor_bytes below the size; EHL_ECUDA if a launch fails; else EHL_OK. */
+ehl_status ehl_paqif_factor_size(int n_sys, int n, int beta, size_t* bytes);
+ehl_status ehl_paqif_factor(int n_sys, int n, int beta, const double* band, const double* rhs, int mode, double* x,
+                            int* info, void* factor, size_t factor_bytes, void* stream);
+ehl_status ehl_paqif_resolve(int n_sys, int n, int beta, const double* rhs, int mode, double* x, int* info,
+                             void* factor, size_t factor_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
  * EHL problem: context, residual, band Jacobian, solve

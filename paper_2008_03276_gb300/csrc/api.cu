@@ -124,6 +124,63 @@ extern "C" ehl_status ehl_paqif_solve(int n_sys, int n, int beta, const double* 
 // admissible r is timed on the caller's batch with CUDA events (one untimed launch, then the best
 // of `reps`), the fastest returned.  The workspace is allocated stream-ordered for the largest r
 // and released; the stream is synchronised.
+// factorization object: the Z-stack (the folded Z0 rows, and the rhs column a resolve rewrites),
+// then the factor store (multipliers, Pi^-1 rows, reduced-system factors)
+static size_t paqif_factor_stack_part(int n_sys, int n, int beta) {
+  return align_up(paqif_stack_bytes(n_sys, n, beta, 0), kWorkspaceAlign);
+}
+
+extern "C" ehl_status ehl_paqif_factor_size(int n_sys, int n, int beta, size_t* bytes) {
+  if (!bytes || !paqif_args_ok(n_sys, n, beta, 0) || paqif_parts(n_sys, n, beta, 0) < 1) return EHL_EINVAL;
+  *bytes = paqif_factor_stack_part(n_sys, n, beta) + paqif_factor_store_bytes(n_sys, n, beta, 0);
+  return EHL_OK;
+}
+
+static ehl_status paqif_factor_or_resolve(bool factor, int n_sys, int n, int beta, const double* band,
+                                          const double* rhs, int mode, double* x, int* info, void* fac,
+                                          size_t fac_bytes, void* stream) {
+  if (!rhs || !x || !fac || (factor && !band) || mode < 0 || mode > 1 || !paqif_args_ok(n_sys, n, beta, mode))
+    return EHL_EINVAL;
+  if ((const void*)x == (const void*)rhs || (factor && (const void*)x == (const void*)band)) return EHL_EINVAL;
+  size_t need = 0;
+  if (ehl_paqif_factor_size(n_sys, n, beta, &need) != EHL_OK) return EHL_EINVAL;
+  if (fac_bytes < need || ((uintptr_t)fac % kWorkspaceAlign) != 0) return EHL_EINVAL;
+  unsigned char* f = (unsigned char*)fac;
+  PaqifLaunch L;
+  L.n_sys = n_sys;
+  L.n = n;
+  L.beta = beta;
+  L.mode = mode;
+  L.band = band;
+  L.rhs = rhs;
+  L.stack = f;
+  L.act = nullptr;
+  L.x = x;
+  L.iters = nullptr;
+  L.info = info;
+  void* fstore = f + paqif_factor_stack_part(n_sys, n, beta);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  // the resolve kernel writes only the systems that report something
+  if (!factor && info) e = cudaMemsetAsync(info, 0, sizeof(int) * (size_t)n_sys, st);
+  if (e == cudaSuccess) e = factor ? launch_paqif_factor(L, fstore, st) : launch_paqif_resolve(L, fstore, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return EHL_ECUDA;
+  }
+  return EHL_OK;
+}
+
+extern "C" ehl_status ehl_paqif_factor(int n_sys, int n, int beta, const double* band, const double* rhs, int mode,
+                                       double* x, int* info, void* factor, size_t factor_bytes, void* stream) {
+  return paqif_factor_or_resolve(true, n_sys, n, beta, band, rhs, mode, x, info, factor, factor_bytes, stream);
+}
+
+extern "C" ehl_status ehl_paqif_resolve(int n_sys, int n, int beta, const double* rhs, int mode, double* x, int* info,
+                                        void* factor, size_t factor_bytes, void* stream) {
+  return paqif_factor_or_resolve(false, n_sys, n, beta, nullptr, rhs, mode, x, info, factor, factor_bytes, stream);
+}
+
 extern "C" ehl_status ehl_paqif_autotune(int n_sys, int n, int beta, int mode, const double* band, const double* rhs,
                                          double* x, int reps, void* stream, int* best_r, float* ms_per_r) {
   if (!band || !rhs || !x || !best_r || !paqif_args_ok(n_sys, n, beta, mode) || reps < 1 || reps > 100)

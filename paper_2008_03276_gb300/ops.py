@@ -94,6 +94,46 @@ def paqif_solve(band, rhs, beta, mode=0, active=None, x=None, workspace=None, st
     return x, iters, info
 
 
+def paqif_factor_size(n_sys, n, beta):
+    lib = _ffi.load()
+    out = ctypes.c_size_t(0)
+    _ffi.check(lib.ehl_paqif_factor_size(n_sys, n, beta, ctypes.byref(out)), "ehl_paqif_factor_size")
+    return out.value
+
+
+def paqif_factor(band, rhs, beta, mode=0, x=None, factor=None, stream=None):
+    """Factor a batch once (and solve it for ``rhs``).  Returns ``(x, info, factor)``; pass
+    ``factor`` (uint8 CUDA tensor) to :func:`paqif_resolve` for new right-hand sides."""
+    lib = _ffi.load()
+    n_sys, n, w = band.shape
+    if w != 2 * beta + 1 or rhs.shape != (n_sys, n) or band.dtype != torch.float64 or rhs.dtype != torch.float64:
+        raise ValueError("band must be float64 [n_sys, n, 2*beta+1] and rhs float64 [n_sys, n]")
+    if x is None:
+        x = torch.empty_like(rhs)
+    if factor is None:
+        factor = torch.empty(paqif_factor_size(n_sys, n, beta), dtype=torch.uint8, device=band.device)
+    info = torch.empty(n_sys, dtype=torch.int32, device=band.device)
+    _check_dev(band, rhs, x, factor)
+    _ffi.check(lib.ehl_paqif_factor(n_sys, n, beta, _ptr(band), _ptr(rhs), mode, _ptr(x), _ptr(info), _ptr(factor),
+                                    factor.numel(), _stream(stream)), "ehl_paqif_factor")
+    return x, info, factor
+
+
+def paqif_resolve(factor, rhs, beta, mode=0, x=None, stream=None):
+    """Solve a batch factored by :func:`paqif_factor` for a new ``rhs [n_sys, n]``.  Returns ``(x, info)``."""
+    lib = _ffi.load()
+    n_sys, n = rhs.shape
+    if rhs.dtype != torch.float64:
+        raise ValueError("rhs must be float64")
+    if x is None:
+        x = torch.empty_like(rhs)
+    info = torch.empty(n_sys, dtype=torch.int32, device=rhs.device)
+    _check_dev(rhs, x, factor)
+    _ffi.check(lib.ehl_paqif_resolve(n_sys, n, beta, _ptr(rhs), mode, _ptr(x), _ptr(info), _ptr(factor),
+                                     factor.numel(), _stream(stream)), "ehl_paqif_resolve")
+    return x, info
+
+
 def default_params(dim=1, **overrides):
     """``ehl_params`` filled by ``ehl_params_default`` with keyword overrides."""
     lib = _ffi.load()
