@@ -248,7 +248,7 @@ def run_ours(args):
     ws = torch.empty(ops.paqif_workspace_size(n_sys, PAQIF_N, PAQIF_BETA, PAQIF_MODE), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     B = args.ehl_batch
-    ctx = ops.Context(ehl_params(ops), n_inst=B) if B > 0 else None
+    ctx = ops.Context(ehl_params(ops, graph=args.ehl_graph), n_inst=B) if B > 0 else None
     sol = {}
 
     def leg_a():
@@ -307,7 +307,7 @@ def run_ours(args):
     # stays float64): solves/s and its difference from the plain path
     mixed = None
     if ctx is not None:
-        pm = ehl_params(ops, graph=2)
+        pm = ehl_params(ops, graph=args.ehl_graph)
         pm.precision = 5
         ctx_m = ops.Context(pm, n_inst=B)
         barrier()
@@ -400,8 +400,9 @@ def run_ours(args):
         "config": {
             "workload": "high-load line contact: batch of converged solves N=1025, M=200, L=10, van Leer, "
                         "beta=8, tol 1e-8, plus the standalone PAQIF batch (4096 x n=1024, beta=4, mode 1)",
-            "ehl_loop": "device-driven: each grid's Newton, GMRES and line-search loops are one CUDA graph launch "
-                        "with conditional while-nodes (graph = 2)",
+            "ehl_loop": ("device-driven: each grid's Newton, GMRES and line-search loops are one CUDA graph launch "
+                         "with conditional while-nodes (graph = 2)") if args.ehl_graph == 2 else
+                        "host-driven (graph = 0)",
             "ehl_batch": B, "ehl_N": EHL["N"], "ehl_M": EHL["M"], "ehl_L": EHL["L"], "ehl_beta": EHL["beta"],
             "ehl_ms": round(ms_b, 3), "ehl_newton_iters_min_max": ehl_iters,
             "ehl_newton_iters_per_s": round(job_rate(world, ehl_iter_sum, ms_b), 1) if ehl_iter_sum else None,
@@ -824,6 +825,9 @@ def main():
     ap.add_argument("--ehl-batch", type=int, default=512, help="line-contact instances solved per step")
     ap.add_argument("--paqif-nsys", type=int, default=PAQIF_NSYS,
                     help="systems in the PAQIF batch (smaller only for profiling captures)")
+    ap.add_argument("--ehl-graph", type=int, default=2, choices=[0, 2],
+                    help="leg B's loop: 2 device-driven CUDA graph (default); 0 host-driven, for ncu launch lists "
+                         "(ncu does not list the kernels inside conditional graph nodes)")
     ap.add_argument("--profile", choices=["tc_gemm"], help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile:

@@ -32,7 +32,8 @@ def test_resolve_matches_dense_lu(n_sys, n, beta, mode):
             if mode == 1:
                 ref = np.maximum(ref, 0.0)
             assert np.max(np.abs(xs[s] - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
-    assert torch.equal(x1, x3)
+    # the resolve kernel sums in another order than the factor kernel's sweeps: same tolerance
+    assert float((x1 - x3).abs().max()) <= 1e-12 * max(1.0, float(x1.abs().max()))
 
 
 def test_resolve_agrees_with_the_solve_entry():
