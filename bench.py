@@ -790,7 +790,12 @@ def profile_case(name):
     """Small fixed cases for ncu captures of one kernel (no timing, no JSON line).
 
     tc_gemm: three ehl_jacobian_apply calls on the 512-instance N = 1025, M = 200 context with the
-    tensor-core Krylov products (precision 5), each one launch of the TF32x3 tcgen05 kernel."""
+    tensor-core Krylov products (precision 5), each one launch of the TF32x3 tcgen05 kernel.
+    c4_fft: the point-contact configuration (257^2, M = 100, L = 10, minmod, beta 2, FFT
+    deformation, autotuned x-line partitions) solved once host-driven (graph 0), so that a launch
+    list sees every kernel.
+    pt_deform: three residual evaluations of a 129^2 point contact with the direct-sum deformation
+    (deform 0), each one launch of the float64 direct-sum kernel."""
     import torch
 
     from paper_2008_03276_gb300 import ops
@@ -810,6 +815,24 @@ def profile_case(name):
         for _ in range(3):
             ctx.jacobian_apply(P, H0, v, vh)
         torch.cuda.synchronize()
+    elif name == "c4_fft":
+        p = ops.default_params(2, nx=257, ny=257, M=100.0, L=10.0, limiter=0, halfband=2, method=1, tol=1e-8,
+                               max_iter=60, coarse_min_nodes=33, deform=1, autotune=1, graph=0)
+        ctx = ops.Context(p)
+        out = ctx.solve(check=False)
+        torch.cuda.synchronize()
+        print("c4_fft: status", int(out[4]), "newton", out[2].tolist())
+    elif name == "pt_deform":
+        n = 129
+        p = ops.default_params(2, nx=n, ny=n, M=100.0, L=10.0, limiter=0, halfband=2, method=1, deform=0)
+        ctx = ops.Context(p)
+        xs = torch.linspace(-4.5, 1.5, n, dtype=torch.float64, device="cuda")
+        ys = torch.linspace(-3.0, 3.0, n, dtype=torch.float64, device="cuda")
+        P = torch.sqrt(torch.clamp(1 - xs[None, :] ** 2 - ys[:, None] ** 2, min=0)).unsqueeze(0).contiguous()
+        H0 = torch.full((1,), 0.1, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            ctx.residual(P, H0)
+        torch.cuda.synchronize()
 
 
 def main():
@@ -828,7 +851,7 @@ def main():
     ap.add_argument("--ehl-graph", type=int, default=2, choices=[0, 2],
                     help="leg B's loop: 2 device-driven CUDA graph (default); 0 host-driven, for ncu launch lists "
                          "(ncu does not list the kernels inside conditional graph nodes)")
-    ap.add_argument("--profile", choices=["tc_gemm"], help="run a small case for an ncu capture and exit")
+    ap.add_argument("--profile", choices=["tc_gemm", "c4_fft", "pt_deform"], help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile:
         profile_case(args.profile)

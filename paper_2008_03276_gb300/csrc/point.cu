@@ -37,7 +37,7 @@ constexpr int kPtTJ = 4;        //                   output rows
 constexpr int kPtSK = 128;      // source chunk along x (one partial sum per chunk)
 constexpr int kPtSL = 8;        // source rows per shared-memory stage
 constexpr int kPtVB = 256;      // threads of the vector kernels
-constexpr int kPtVPT = 8;       // vector elements per thread
+constexpr int kPtVPT = 2;       // vector elements per thread (the Krylov kernels' kNV)
 
 __device__ __forceinline__ double pt_block_sum(double v, double* sh) {
   sh[threadIdx.x] = v;

@@ -25,7 +25,7 @@
 namespace ehl {
 
 constexpr int kNB = 256;   // threads of the vector kernels
-constexpr int kNV = 8;     // elements per thread
+constexpr int kNV = 2;     // elements per thread (a 257^2 grid spreads over 128 blocks)
 
 struct PtView {  // device pointers the vector kernels need
   const PointInst* inst;
@@ -45,16 +45,22 @@ struct PtView {  // device pointers the vector kernels need
   double* jc;
 };
 
+// the block's total of v, to every thread: warp shuffles, then one value per warp in shared
+// memory (two barriers; the leading one lets a previous call's readers finish)
+__device__ __forceinline__ double nk_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 __device__ __forceinline__ double nk_block_sum(double v, double* sh) {
-  sh[threadIdx.x] = v;
+  v = nk_warp_sum(v);
   __syncthreads();
-  for (int s = kNB / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double r = sh[0];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
-  return r;
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kNB / 32; ++w) t += sh[w];
+  return t;
 }
 
 __device__ __forceinline__ int nk_node(int r, int nx) { return (r / (nx - 2) + 1) * nx + (r % (nx - 2)) + 1; }
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(256) k_pn_jvcoef(PtView v, PnRowArgs q) {
   if (t >= v.NN) return;
   const size_t k = (size_t)z * v.NN + t;
   const double e = q.eps[k], Hk = q.H[k];
-  double4 c;
+  double4_32a c;
   c.x = q.drho[k] * Hk;
   c.y = 3.0 * e / Hk;
   c.z = e * (q.drho[k] / q.rho[k] - q.deta_rel[k]);
@@ -321,7 +327,7 @@ __global__ void __launch_bounds__(256) k_pn_jvcoef(PtView v, PnRowArgs q) {
     const int r = (jj - 1) * (v.nx - 2) + (ii - 1);
     c.w = 1.0 / v.dg[(size_t)z * v.n + r];
   }
-  reinterpret_cast<double4*>(v.jc)[k] = c;
+  reinterpret_cast<double4_32a*>(v.jc)[k] = c;
 }
 
 __global__ void __launch_bounds__(kNB) k_pn_jv(PtView v, PnRowArgs q, int j) {
@@ -343,14 +349,14 @@ __global__ void __launch_bounds__(kNB) k_pn_jv(PtView v, PnRowArgs q, int j) {
       auto idx = [&](int p, int qq) { return base + (size_t)qq * nx + p; };
       auto dH = [&](int p, int qq) { return q.dH[idx(p, qq)]; };
       auto zn = [&](int p, int qq) { return v.znode[idx(p, qq)]; };
-      const double4* jc = reinterpret_cast<const double4*>(v.jc);
+      const double4_32a* jc = reinterpret_cast<const double4_32a*>(v.jc);
       auto dU = [&](int p, int qq) {
         const size_t k = idx(p, qq);
         return q.rho[k] * dH(p, qq) + jc[k].x * zn(p, qq);
       };
       auto dE = [&](int p, int qq) {
         const size_t k = idx(p, qq);
-        const double4 cc = jc[k];
+        const double4_32a cc = jc[k];
         return cc.y * dH(p, qq) + cc.z * zn(p, qq);
       };
       auto dF = [&](int f, int qq) {
@@ -388,31 +394,58 @@ __global__ void __launch_bounds__(kNB) k_pn_force(PtView v) {
 }
 
 // partial dot products w . V_i, i = 0..j, into dots slots 0..j
+// the block's partials of V_i . w for i = 0..j: per i a warp-shuffle sum, one word per warp in
+// shared memory, and every 32 dot products one combine of the warps (two barriers per 32)
 __global__ void __launch_bounds__(kNB) k_pn_dots(PtView v, int j) {
   if (v.jd) j = *v.jd;
   const int z = blockIdx.y;
   if (v.skip[z]) return;
-  __shared__ double sh[kNB];
+  __shared__ double sh[kNB / 32][32];
   const double* wz = v.w + (size_t)z * v.n1;
-  for (int i = 0; i <= j; ++i) {
-    const double* Vi = v.V + ((size_t)z * (v.m + 1) + i) * v.n1;
-    double s = 0.0;
-    NK_FOR(r, v.n1) s += wz[r] * Vi[r];
-    s = nk_block_sum(s, sh);
-    if (threadIdx.x == 0) v.dots[((size_t)z * v.nvb + blockIdx.x) * (v.m + 2) + i] = s;
+  double wv[kNV];
+  int rr[kNV];
+#pragma unroll
+  for (int k = 0; k < kNV; ++k) {
+    rr[k] = blockIdx.x * (kNB * kNV) + threadIdx.x + k * kNB;
+    wv[k] = rr[k] < v.n1 ? wz[rr[k]] : 0.0;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* out = v.dots + ((size_t)z * v.nvb + blockIdx.x) * (v.m + 2);
+  for (int i0 = 0; i0 <= j; i0 += 32) {
+    const int i1 = min(j + 1, i0 + 32);
+    for (int i = i0; i < i1; ++i) {
+      const double* Vi = v.V + ((size_t)z * (v.m + 1) + i) * v.n1;
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < kNV; ++k)
+        if (rr[k] < v.n1) s += wv[k] * Vi[rr[k]];
+      s = nk_warp_sum(s);
+      if (lane == 0) sh[warp][i - i0] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < i1 - i0) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < kNB / 32; ++w) t += sh[w][threadIdx.x];
+      out[i0 + threadIdx.x] = t;
+    }
+    __syncthreads();
   }
 }
 
 // h_i = sum of the partials; H(:, j) = h (first pass) or += h (second pass)
+// one warp per h_i: its lanes sum the blocks' partials with shuffles (no block barriers)
 __global__ void __launch_bounds__(kNB) k_pn_hsum(PtView v, int j, int pass) {
   if (v.jd) j = *v.jd;
   const int z = blockIdx.x;
   if (v.skip[z]) return;
-  __shared__ double sh[kNB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* H = v.Hh + (size_t)z * (v.m + 1) * v.m;
-  for (int i = 0; i <= j; ++i) {
-    const double s = pn_total(v, z, i, sh);
-    if (threadIdx.x == 0) {
+  for (int i = warp; i <= j; i += kNB / 32) {
+    double s = 0.0;
+    for (int b = lane; b < v.nvb; b += 32) s += v.dots[((size_t)z * v.nvb + b) * (v.m + 2) + i];
+    s = nk_warp_sum(s);
+    if (lane == 0) {
       v.hcol[(size_t)z * (v.m + 2) + i] = s;
       H[i + (size_t)j * (v.m + 1)] = pass == 0 ? s : H[i + (size_t)j * (v.m + 1)] + s;
     }
