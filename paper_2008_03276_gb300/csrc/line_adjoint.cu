@@ -42,16 +42,18 @@ struct AdjBuf {
   void* fstore = nullptr;
 };
 
+// the block's total of v, to every thread: warp shuffles, then one value per warp in shared
+// memory (two barriers; the leading one lets a previous call's readers finish)
 __device__ __forceinline__ double adj_block_sum(double v, double* sh) {
-  sh[threadIdx.x] = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
-  for (int s = kAdjBlock / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double r = sh[0];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
-  return r;
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kAdjBlock / 32; ++w) t += sh[w];
+  return t;
 }
 
 // Node state the transposed stencil reads (from line_state).

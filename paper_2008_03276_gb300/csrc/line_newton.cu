@@ -44,16 +44,18 @@ struct NkBuf {
   int* loop = nullptr;
 };
 
+// the block's total of v, to every thread: warp shuffles, then one value per warp in shared
+// memory (two barriers; the leading one lets a previous call's readers finish)
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-  sh[threadIdx.x] = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
-  for (int s = kNkBlock / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double r = sh[0];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
-  return r;
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kNkBlock / 32; ++w) t += sh[w];
+  return t;
 }
 
 // skip[z] = done[z] | other[z]
