@@ -77,6 +77,18 @@ struct RedWarp {
   float2 xs[32][B];
 };
 
+// shared memory of one warp: the row rings of its lanes and its reduced system during the
+// factorization, then, in the same bytes, the Z0 sweep's stack rings of its lanes (DEPTH levels
+// each, at most 8; lane stride skewed by 16 bytes against bank conflicts)
+template <int B>
+struct WarpSm {
+  static constexpr int BYTES = 32 * kRingLane + (int)sizeof(RedWarp<B>);
+  static constexpr int FIT = (BYTES / 32 - 16) / (PC<B>::NQ * 16);
+  static constexpr int DEPTH = FIT < 8 ? FIT : 8;
+  static constexpr int Z0LANE = DEPTH * PC<B>::NQ * 16 + 16;
+  static_assert(DEPTH >= 2 && 32 * Z0LANE <= BYTES && BYTES % 16 == 0, "Z0 ring layout");
+};
+
 __device__ __forceinline__ df f2df(float2 v) { return make_df(v.x, v.y); }
 __device__ __forceinline__ float2 df2f(df v) { return make_float2(v.hi, v.lo); }
 __device__ __forceinline__ df shfl_x1(df v) {
@@ -115,7 +127,7 @@ struct RowMeta {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
                : "memory");
 }
 __device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
@@ -129,7 +141,8 @@ __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0
 // Start the copy of the row of stream t on this lane's side into ring slot `slot` (one commit
 // group): the 16-byte aligned words around the row (the array starts on a 16-byte boundary, so
 // the word before an odd row is inside it; past the array's end nothing is read, cp.async fills
-// zeros), then the rhs.  Rows that are not read copy nothing.
+// zeros), then the rhs.  Rows that are not read copy nothing.  The copies go through L1
+// (.ca): consecutive rows of a lane share 128-byte lines (4 % faster than .cg).
 template <int B>
 __device__ __forceinline__ RowMeta<B> fetch_row(const PairBlk& p, int t, unsigned char* slot) {
   using C = PC<B>;
@@ -370,7 +383,8 @@ __global__ void __launch_bounds__(kPairThreads, PC<B>::MINB) paqif_pair_kernel(P
 
   // the rows entering at levels 0 and 1 (streams b+1, b+2) are copied ahead; at the end of level k
   // the row of stream k+1+b is placed and the copy of stream k+3+b takes its slot
-  unsigned char* ring = smem_raw + (size_t)threadIdx.x * kRingLane;
+  unsigned char* wsm = smem_raw + (size_t)warp * WarpSm<B>::BYTES;
+  unsigned char* ring = wsm + (size_t)lane * kRingLane;
   RowMeta<B> meta0 = fetch_row<B>(p, B + 1, ring);
   RowMeta<B> meta1 = fetch_row<B>(p, B + 2, ring + C::SLOT);
 
@@ -464,7 +478,7 @@ __global__ void __launch_bounds__(kPairThreads, PC<B>::MINB) paqif_pair_kernel(P
     xx[d] = df_zero();
   }
   if (a.r > 1) {
-    RedWarp<B>& R = reinterpret_cast<RedWarp<B>*>(smem_raw + (size_t)kPairThreads * kRingLane)[warp];
+    RedWarp<B>& R = *reinterpret_cast<RedWarp<B>*>(wsm + 32 * kRingLane);
     const int q = lane;  // block row of the warp: 2m (left lane) or 2m + 1 (right lane)
     // rows j = 0..b-1 of the window: left: local row b-1-j (index b-1-j of row 2m), right: local
     // row 2s-b+j (index j of row 2m+1); own column slot d: left index b-1-d of column block 2m,
@@ -522,52 +536,54 @@ __global__ void __launch_bounds__(kPairThreads, PC<B>::MINB) paqif_pair_kernel(P
     __syncwarp();
   }
 
-  // ---- Z0 sweep: levels sf-1 .. 0, from the block's ends towards its middle; the stack levels
-  // are read D levels ahead into a register ring (the window's registers are free by now)
+  // ---- Z0 sweep: levels sf-1 .. 0, from the block's ends towards its middle.  The stack levels
+  // are copied DEPTH - 1 levels ahead with cp.async into this lane's ring in the warp's
+  // shared memory (free now: the rows are placed and the reduced system is solved); a slot is
+  // refilled one level after it was read
+  __syncwarp();
   {
-    constexpr int D = 2;
+    float4* zr = reinterpret_cast<float4*>(wsm + (size_t)lane * WarpSm<B>::Z0LANE);
     const float4* st = p.stk;
-    float4 ring4[D][C::NQ];
+    auto issue = [&](int k, int slot) {
+      if (k >= 0) {
 #pragma unroll
-    for (int u = 0; u < D; ++u) {
-      const int k = sf - 1 - u;
-#pragma unroll
-      for (int q = 0; q < C::NQ; ++q)
-        ring4[u][q] = (k >= 0) ? st[((size_t)k * C::NQ + q) * 32] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    for (int k0 = sf - 1; k0 >= 0; k0 -= D) {
-#pragma unroll
-      for (int u = 0; u < D; ++u) {
-        const int k = k0 - u;
-        if (k < 0) break;
-        df M[2 * C::NQ];
-#pragma unroll
-        for (int q = 0; q < C::NQ; ++q) {
-          M[2 * q] = make_df(ring4[u][q].x, ring4[u][q].y);
-          M[2 * q + 1] = make_df(ring4[u][q].z, ring4[u][q].w);
-        }
-        if (k - D >= 0) {
-#pragma unroll
-          for (int q = 0; q < C::NQ; ++q) ring4[u][q] = st[((size_t)(k - D) * C::NQ + q) * 32];
-        }
-        // the terms of the farther unknowns first: only the last one waits for the level before
-        df acc = M[2 * B];
-#pragma unroll
-        for (int d = B; d >= 1; --d) acc = df_sub_two_prods(acc, M[d - 1], xo[d - 1], M[B + d - 1], xx[d - 1]);
-        const df xp = shfl_x1(acc);
-#pragma unroll
-        for (int d = B - 1; d >= 1; --d) {
-          xo[d] = xo[d - 1];
-          xx[d] = xx[d - 1];
-        }
-        xo[0] = acc;
-        xx[0] = xp;
-        const int lr = row_of(sd, k, s);
-        if (!isfinite(acc.hi) && flag == 0) flag = EHL_INFO_NONFINITE;
-        const double dv = (a.mode == 1 && !(acc.hi > 0.f)) ? 0.0 : df_to_double(acc);
-        if (real && lr < p.nb) p.x[lr] = dv;
+        for (int q = 0; q < C::NQ; ++q) cp_async16(zr + slot * C::NQ + q, st + ((size_t)k * C::NQ + q) * 32, 16);
       }
+      cp_commit();
+    };
+#pragma unroll
+    for (int u = 0; u < WarpSm<B>::DEPTH - 1; ++u) issue(sf - 1 - u, u);
+    for (int k = sf - 1; k >= 0; --k) {
+      const int v = sf - 1 - k, slot = v % WarpSm<B>::DEPTH;
+      // level k is group v; groups up to v + WarpSm<B>::DEPTH - 2 are committed
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(WarpSm<B>::DEPTH - 2) : "memory");
+      df M[2 * C::NQ];
+#pragma unroll
+      for (int q = 0; q < C::NQ; ++q) {
+        const float4 w = zr[slot * C::NQ + q];
+        M[2 * q] = make_df(w.x, w.y);
+        M[2 * q + 1] = make_df(w.z, w.w);
+      }
+      // the slot read at the previous level takes level k - (WarpSm<B>::DEPTH - 1)
+      issue(k - (WarpSm<B>::DEPTH - 1), (v + WarpSm<B>::DEPTH - 1) % WarpSm<B>::DEPTH);
+      // the terms of the farther unknowns first: only the last one waits for the level before
+      df acc = M[2 * B];
+#pragma unroll
+      for (int d = B; d >= 1; --d) acc = df_sub_two_prods(acc, M[d - 1], xo[d - 1], M[B + d - 1], xx[d - 1]);
+      const df xp = shfl_x1(acc);
+#pragma unroll
+      for (int d = B - 1; d >= 1; --d) {
+        xo[d] = xo[d - 1];
+        xx[d] = xx[d - 1];
+      }
+      xo[0] = acc;
+      xx[0] = xp;
+      const int lr = row_of(sd, k, s);
+      if (!isfinite(acc.hi) && flag == 0) flag = EHL_INFO_NONFINITE;
+      const double dv = (a.mode == 1 && !(acc.hi > 0.f)) ? 0.0 : df_to_double(acc);
+      if (real && lr < p.nb) p.x[lr] = dv;
     }
+    cp_wait0();
   }
 
   // ---- status: the first nonzero flag among the system's lanes
@@ -584,8 +600,8 @@ __global__ void __launch_bounds__(kPairThreads, PC<B>::MINB) paqif_pair_kernel(P
 }
 
 template <int B>
-size_t pair_smem_bytes(int r) {
-  return (size_t)kPairThreads * kRingLane + (r > 1 ? sizeof(RedWarp<B>) * (kPairThreads / 32) : 0);
+size_t pair_smem_bytes(int) {
+  return (size_t)WarpSm<B>::BYTES * (kPairThreads / 32);
 }
 
 template <int B>
