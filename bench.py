@@ -491,7 +491,8 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
                     converged=int(np.sum((r[:, 0] <= 10 * tol) & (r[:, 1] <= 10 * tol))), status=int(code))
 
     # C1: N = 129, M = 20, L = 10, minmod, beta 2, one instance
-    for key, method, graph in (("C1_method0", 0, 0), ("C1_method1", 1, 0), ("C1_method1_graph", 1, 2)):
+    for key, method, graph in (("C1_method0", 0, 0), ("C1_method0_graph", 0, 2), ("C1_method1", 1, 0),
+                               ("C1_method1_graph", 1, 2)):
         p = ops.default_params(1, nx=129, M=20.0, L=10.0, limiter=0, halfband=2, method=method, tol=1e-8,
                                max_iter=4000 if method == 0 else 60, graph=graph)
         ctx = ops.Context(p)
@@ -499,8 +500,10 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
         ms, out = _timed(torch, lambda: ctx.solve(check=False), reps=5)
         d = dict(workload="line N=129, M=20, L=10, minmod, beta=2, 1 instance, tol 1e-8",
                  method=("paper relaxation" if method == 0 else "Newton-Krylov"),
-                 loop=("device-driven graph (Newton, GMRES, line search as graph while-loops)" if graph == 2
-                       else "host-driven"), ms=round(ms, 3), solves_per_s=round(1e3 / ms, 2),
+                 loop=("host-driven" if graph == 0 else
+                       "device-driven graph (the iterations as a graph while-loop)" if method == 0 else
+                       "device-driven graph (Newton, GMRES, line search as graph while-loops)"),
+                 ms=round(ms, 3), solves_per_s=round(1e3 / ms, 2),
                  kernels_per_solve=int((ops.kernel_launches() - n0) // 6))
         d.update(summary(out[2], out[3], out[4], 1e-8))
         res[key] = d

@@ -270,6 +270,9 @@ typedef struct {
                         /*   Newton, GMRES and line-search loops run as device-side while   */
                         /*   loops whose conditions the kernels set from the instances'     */
                         /*   flags (no host round trip inside a grid; precision 0 or 5);  */
+                        /*   line contact, method 0: 2 = the paper's iterations of each    */
+                        /*   grid as one device-side while loop (same kernels, same        */
+                        /*   iterates as 0), 1 is ignored;                                  */
                         /*   0 = launched kernel by kernel with early exits (default)      */
   double kappa;         /* kappa of limiter 2, -1..1 (0: Fromm, 1/3: third-order upwind    */
                         /*   biased, -1: second-order upwind)                              */

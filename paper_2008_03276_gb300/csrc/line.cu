@@ -11,6 +11,7 @@
 #include "df64.cuh"
 #include "ehl_internal.h"
 #include "line_kernels.cuh"
+#include "graph_loop.h"
 #include "line.h"
 #include "tc_gemm.h"
 
@@ -164,8 +165,7 @@ __global__ void k_line_film(const LineInst* __restrict__ inst, const float2* __r
     Dd = df_to_double(D);
   }
   if (mode == 0) {
-    const double X = inst[z].xa + i * inst[z].h;
-    double H = H0[z] + 0.5 * X * X - Dd;
+    double H = line_film_h(inst[z], i, H0[z], Dd);
     if (rough) H += rough[(size_t)z * rstride + i];
     out[(size_t)z * N + i] = H;
   } else {
@@ -183,15 +183,18 @@ __global__ void k_line_nodes(const LineInst* __restrict__ inst, const double* __
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const LineInst q = inst[z];
-  const size_t o = (size_t)z * N + i;
-  double r, dr, ln_eta, de;
-  line_material(q, P[o], r, dr, ln_eta, de);
-  const double Hh = H[o];
-  rho[o] = r;
-  drho[o] = dr;
-  deta_rel[o] = de;
-  eps[o] = r * Hh * Hh * Hh / q.lam * exp(-ln_eta);
-  u[o] = r * Hh;
+  line_node(q, (size_t)z * N + i, P, H, rho, drho, deta_rel, eps, u);
+}
+
+// face j (0..N-2) at offset o: limited face value and the limiter's derivatives
+__device__ __forceinline__ void line_face(const LineInst& q, size_t o, int j, const double* u, double* F,
+                                          double* psi, double* psia, double* psib) {
+  double ps = 0.0, pa = 0.0, pb = 0.0;
+  if (j >= 1) line_limiter(q.limiter, q.kappa, u[o] - u[o - 1], u[o + 1] - u[o], ps, pa, pb);
+  F[o] = u[o] + 0.5 * ps;
+  psi[o] = ps;
+  psia[o] = pa;
+  psib[o] = pb;
 }
 
 // faces j = 0..N-2: limited face value and limiter derivatives
@@ -202,30 +205,18 @@ __global__ void k_line_faces(const LineInst* __restrict__ inst, const double* __
   if (skip && skip[z]) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N - 1) return;
-  const size_t o = (size_t)z * N + j;
-  double ps = 0.0, pa = 0.0, pb = 0.0;
-  if (j >= 1) line_limiter(inst[z].limiter, inst[z].kappa, u[o] - u[o - 1], u[o + 1] - u[o], ps, pa, pb);
-  F[o] = u[o] + 0.5 * ps;
-  psi[o] = ps;
-  psia[o] = pa;
-  psib[o] = pb;
+  line_face(inst[z], (size_t)z * N + j, j, u, F, psi, psia, psib);
 }
 
-// residual at interior nodes; block partials of max|min(P,R)|, sum P and min H
-__global__ void __launch_bounds__(kNodeBlock) k_line_residual(const LineInst* __restrict__ inst,
-                                                              const double* __restrict__ P,
-                                                              const double* __restrict__ H,
-                                                              const double* __restrict__ eps,
-                                                              const double* __restrict__ F,
-                                                              const int* __restrict__ skip, double* __restrict__ R,
-                                                              double* __restrict__ blk, int nblk, int N) {
-  const int z = blockIdx.y;
-  if (skip && skip[z]) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const double h = inst[z].h;
+// R_i at node i of the instance at offset base (0 at the boundary nodes) and the block's
+// reductions of max|min(P,R)|, sum P, min H and the largest term of R into out[0..3] (one
+// thread per node, kNodeBlock threads, a tree over the block)
+__device__ __forceinline__ void line_residual_block(double h, const double* P, const double* H, const double* eps,
+                                                    const double* F, double* R, double* out, size_t base, int i,
+                                                    int N) {
   double cres = 0.0, sp = 0.0, hmin = INFINITY, term = 0.0;
   if (i < N) {
-    const size_t o = (size_t)z * N + i;
+    const size_t o = base + i;
     hmin = H[o];
     if (i >= 1 && i <= N - 2) {
       const double C = (F[o] - F[o - 1]) / h;
@@ -259,12 +250,54 @@ __global__ void __launch_bounds__(kNodeBlock) k_line_residual(const LineInst* __
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double* b = blk + ((size_t)z * nblk + blockIdx.x) * 4;
-    b[0] = s_c[0];
-    b[1] = s_s[0];
-    b[2] = s_h[0];
-    b[3] = s_t[0];
+    out[0] = s_c[0];
+    out[1] = s_s[0];
+    out[2] = s_h[0];
+    out[3] = s_t[0];
   }
+}
+
+// residual at interior nodes; block partials of max|min(P,R)|, sum P and min H
+__global__ void __launch_bounds__(kNodeBlock) k_line_residual(const LineInst* __restrict__ inst,
+                                                              const double* __restrict__ P,
+                                                              const double* __restrict__ H,
+                                                              const double* __restrict__ eps,
+                                                              const double* __restrict__ F,
+                                                              const int* __restrict__ skip, double* __restrict__ R,
+                                                              double* __restrict__ blk, int nblk, int N) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  line_residual_block(inst[z].h, P, H, eps, F, R, blk + ((size_t)z * nblk + blockIdx.x) * 4, (size_t)z * N, i, N);
+}
+
+// line_state of an instance of at most kNodeBlock nodes in one CTA, one thread per node: the
+// film from k_line_deform64's float64 chunk sums, the lubricant state, the limited faces and the
+// residual with its block reductions.  The arithmetic of k_line_film, k_line_nodes, k_line_faces
+// and k_line_residual in the same order (one residual block, nblk = 1), so the same results
+// bit for bit, in one launch instead of four.
+__global__ void __launch_bounds__(kNodeBlock) k_line_state_small(
+    const LineInst* __restrict__ inst, const double* __restrict__ partial, int ksplit, const double* __restrict__ H0,
+    const double* __restrict__ rough, const double* __restrict__ P, const int* __restrict__ skip, double* H,
+    double* rho, double* drho, double* deta_rel, double* eps, double* u, double* F, double* psi, double* psia,
+    double* psib, double* R, double* __restrict__ blk, int n_inst, int N) {
+  const int z = blockIdx.x;
+  if (skip && skip[z]) return;
+  const int i = threadIdx.x;
+  const LineInst q = inst[z];
+  const size_t base = (size_t)z * N;
+  if (i < N) {
+    double Dd = 0.0;
+    for (int y = 0; y < ksplit; ++y) Dd += partial[((size_t)y * n_inst + z) * N + i];
+    double Hv = line_film_h(q, i, H0[z], Dd);
+    if (rough) Hv += rough[base + i];
+    H[base + i] = Hv;
+    line_node(q, base + i, P, H, rho, drho, deta_rel, eps, u);
+  }
+  __syncthreads();
+  if (i < N - 1) line_face(q, base + i, i, u, F, psi, psia, psib);
+  __syncthreads();
+  line_residual_block(q.h, P, H, eps, F, R, blk + (size_t)z * 4, base, i, N);
 }
 
 // red[z] = (max|min(P,R)|, h sum P - pi/2, sum P, min H); convergence flag and iteration count
@@ -648,6 +681,13 @@ cudaError_t line_state(LineCtx* c, const double* P, const double* H0, const doub
                        int* iters_done_flag_mode) {
   cudaError_t e = line_deform64(c, P, c->N, skip);
   if (e != cudaSuccess) return e;
+  if (c->fuse && c->N <= kNodeBlock) {
+    k_line_state_small<<<c->n_inst, kNodeBlock, 0, c->st>>>(
+        c->inst, reinterpret_cast<const double*>(c->partial), c->ksplit, H0, rough, P, skip, c->H, c->rho, c->drho,
+        c->deta_rel, c->eps, c->u, c->F, c->psi, c->psia, c->psib, c->R, c->blk, c->n_inst, c->N);
+    note_launch();
+    return cudaGetLastError();
+  }
   dim3 gn((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
   k_line_film<<<gn, kNodeBlock, 0, c->st>>>(c->inst, c->partial, c->ksplit, H0, rough, c->N, skip, c->H,
                                              c->n_inst, c->N, 0, 1);
@@ -766,6 +806,46 @@ cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double
   k_line_h0_update<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(c->inst, c->blk, c->nblk, c->done, H0, c->n_inst);
   note_launch();
   return cudaGetLastError();
+}
+
+// The paper's iteration of one grid as one graph: a while-node whose body is one pass of
+// line_paper_iteration and whose condition k_nk_loop sets on the device (some instance not done
+// and fewer than max_iter passes), then the state and reductions at the final iterate, as the
+// host-driven loop ends.  Same kernels, same order, so the same iterates.
+cudaError_t line_paper_capture_solve(LineCtx* c, double* P, double* H0, const double* rough, cudaStream_t s1,
+                                     SolveGraphCounts& n) {
+  const int ni = c->n_inst;
+  const cudaStream_t s0 = c->st;
+  c->capturing = true;
+  const unsigned long long l0 = thread_launches();
+  // fresh flags, no residual seen yet (bytes 0x7f: 1.4e306), no stall, pass counter 0
+  cudaError_t e = cudaMemsetAsync(c->done, 0, sizeof(int) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->iters, 0, sizeof(int) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->best, 0x7f, sizeof(double) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->stall, 0, sizeof(int) * ni, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->loop0, 0, sizeof(int) * 8, s0);
+  auto loop = [&](cudaGraphConditionalHandle h, int next) -> cudaError_t {
+    k_nk_loop<<<1, 256, 0, c->st>>>(h, c->loop0, nullptr, c->max_iter, next, c->done, nullptr, ni);
+    note_launch();
+    return cudaGetLastError();
+  };
+  long long body = 0;
+  if (e == cudaSuccess)
+    e = capture_while(
+        c, s0, s1, [&](cudaGraphConditionalHandle h) { return loop(h, 0); },
+        [&](cudaGraphConditionalHandle h) {
+          cudaError_t ee = line_paper_iteration(c, P, H0, rough);
+          return ee == cudaSuccess ? loop(h, 1) : ee;
+        },
+        &body);
+  c->st = s0;
+  if (e == cudaSuccess) e = line_state(c, P, H0, rough, nullptr, nullptr);
+  if (e == cudaSuccess) e = line_finalize(c, nullptr, nullptr);
+  c->capturing = false;
+  n = SolveGraphCounts();
+  n.newton = body;
+  n.fixed = (long long)(thread_launches() - l0) - body;
+  return e;
 }
 
 }  // namespace ehl

@@ -49,6 +49,7 @@ struct LineCtx {
   int *done = nullptr, *iters = nullptr;
   double* best = nullptr;  // smallest ||min(P,R)||_inf seen (stall test of the rounding-floor stop)
   int* stall = nullptr;    // outer iterations since it last halved
+  int* loop0 = nullptr;    // graph mode 2 of the paper's iteration: pass counter of its while-loop
   std::vector<void*> allocs;
   // Newton-Krylov buffers (line_newton.cu)
   void* nk = nullptr;
@@ -56,6 +57,10 @@ struct LineCtx {
   void* adj = nullptr;
   // EHL_TRACE=k in the environment: one line per Newton step for the first k instances (stderr)
   int trace = 0;
+  // small instances (N <= 256 for the state, N <= kNkSmallN for a Krylov step) run the stages of
+  // one instance in one CTA, with the same arithmetic as the multi-kernel stages;
+  // EHL_FUSE=0 in the environment turns this off (to check the two against each other)
+  bool fuse = true;
   // graph mode: one Newton step captured as a CUDA graph (no host checks inside; the first
   // kGraphTrials line-search trials), replayed each outer iteration
   bool use_graph = false, capturing = false;
@@ -79,6 +84,12 @@ cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, u
                           double* dg, const int* skip);
 cudaError_t line_start(LineCtx* c, double* P, double* H0, const double* rough);
 cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double* rough);
+// Graph mode 2 of the paper's iteration: the iterations of one grid as a device-side while-loop
+// (the kernels of line_paper_iteration, done instances skipped) captured on c->st, which must be
+// capturing; s1 is a stream of the same device for the loop body.  n.newton counts the kernels
+// of one pass, n.fixed those outside the loop; c->loop0[0] holds the passes a replay ran.
+cudaError_t line_paper_capture_solve(LineCtx* c, double* P, double* H0, const double* rough, cudaStream_t s1,
+                                     SolveGraphCounts& n);
 cudaError_t line_init_tables(LineCtx* c);
 // The same sums in float64 (the residual's deformation; also the adjoint's products)
 cudaError_t line_deform64(LineCtx* c, const double* V, int vstride, const int* skip);

@@ -203,6 +203,7 @@ static void free_ctx(ehl_ctx* ctx) {
 static ehl_status init_line(LineCtx* c, const std::vector<LineInst>& insts, int N, const ehl_params& p) {
   const int n_inst = (int)insts.size();
   if (const char* tr = getenv("EHL_TRACE")) c->trace = atoi(tr) > 0 ? atoi(tr) : 0;
+  if (const char* fu = getenv("EHL_FUSE")) c->fuse = atoi(fu) != 0;
   c->n_inst = n_inst;
   c->N = N;
   c->n = N - 2;
@@ -239,6 +240,7 @@ static ehl_status init_line(LineCtx* c, const std::vector<LineInst>& insts, int 
   A((void**)&c->iters, sizeof(int) * n_inst);
   A((void**)&c->best, sizeof(double) * n_inst);
   A((void**)&c->stall, sizeof(int) * n_inst);
+  A((void**)&c->loop0, sizeof(int) * 8);
   // preconditioner blocks: the largest divisor r of n with r <= precond_blocks and n / r >= 32
   c->pq_parts = 1;
   if (p.method == 1)
@@ -291,7 +293,7 @@ static ehl_status init_line(LineCtx* c, const std::vector<LineInst>& insts, int 
   if (e == cudaSuccess && c->method == 1) e = line_mixed_init(c, p.precision);
   if (e == cudaSuccess) e = paqif_prepare(c->beta);  // no attribute calls inside a graph capture
   c->use_graph = c->method == 1 && p.graph == 1;
-  c->graph_mode = c->method == 1 ? p.graph : 0;
+  c->graph_mode = (c->method == 1 || p.graph == 2) ? p.graph : 0;
   if (e != cudaSuccess) {
     cudaGetLastError();
     return EHL_ECUDA;
@@ -499,7 +501,7 @@ static ehl_status ehl_create_impl(const ehl_params* p, int n_inst, const ehl_par
   ctx->st = (cudaStream_t)stream;
   ctx->direct = sizes.size() == 1;
   // a graph cannot be captured on the legacy default stream the caller may pass
-  ctx->own_streams = !ctx->direct || (p->graph >= 1 && p->method == 1);
+  ctx->own_streams = !ctx->direct || (p->graph >= 1 && p->method == 1) || p->graph == 2;
   for (size_t q = 0; q < sizes.size(); ++q) {
     Bucket* b = new Bucket();
     ctx->buckets.push_back(b);
@@ -890,9 +892,10 @@ static cudaError_t iterate_graph(LineCtx* c, const double* rough, std::vector<in
   return e;
 }
 
-// Graph mode 2: the whole iteration of this grid as one graph with device-side loops (Newton
-// steps, GMRES, line search), captured once per (P, H0, rough) and launched once per solve; the
-// host reads the done flags and the loop totals afterwards.
+// Graph mode 2: the whole iteration of this grid as one graph with device-side loops (method 1:
+// Newton steps, GMRES, line search; method 0: the paper's iteration), captured once per
+// (P, H0, rough) and launched once per solve; the host reads the done flags and the loop totals
+// afterwards.
 static cudaError_t iterate_device_graph(LineCtx* c, const double* rough, std::vector<int>& hdone) {
   cudaError_t e = cudaSuccess;
   if (!c->gs1) {
@@ -910,7 +913,8 @@ static cudaError_t iterate_device_graph(LineCtx* c, const double* rough, std::ve
     e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     SolveGraphCounts n;
-    const cudaError_t es = line_nk_capture_solve(c, c->Pw, c->H0w, rough, c->gs1, c->gs2, n);
+    const cudaError_t es = c->method == 0 ? line_paper_capture_solve(c, c->Pw, c->H0w, rough, c->gs1, n)
+                                          : line_nk_capture_solve(c, c->Pw, c->H0w, rough, c->gs1, c->gs2, n);
     e = cudaStreamEndCapture(c->st, &g);
     add_launches(-(long long)(thread_launches() - l0));  // captured, not run
     if (es != cudaSuccess) e = es;
@@ -929,7 +933,8 @@ static cudaError_t iterate_device_graph(LineCtx* c, const double* rough, std::ve
   int loops[8] = {0};
   e = cudaGraphLaunch(c->graph, c->st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(loops, line_nk_loop_counters(c), sizeof(loops), cudaMemcpyDeviceToHost, c->st);
+    e = cudaMemcpyAsync(loops, c->method == 0 ? c->loop0 : line_nk_loop_counters(c), sizeof(loops),
+                        cudaMemcpyDeviceToHost, c->st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(hdone.data(), c->done, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
@@ -948,7 +953,7 @@ static cudaError_t iterate(LineCtx* c, const double* rough, std::vector<int>& hd
   if (e == cudaSuccess) e = cudaMemsetAsync(c->best, 0x7f, sizeof(double) * c->n_inst, c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stall, 0, sizeof(int) * c->n_inst, c->st);
   hdone.assign(c->n_inst, 0);
-  if (e == cudaSuccess && c->method == 1 && c->graph_mode == 2) return iterate_device_graph(c, rough, hdone);
+  if (e == cudaSuccess && c->graph_mode == 2) return iterate_device_graph(c, rough, hdone);
   if (e == cudaSuccess && c->method == 1 && c->use_graph) return iterate_graph(c, rough, hdone);
   const int check_every = 8;
   for (int it = 0; it < c->max_iter && e == cudaSuccess; ++it) {

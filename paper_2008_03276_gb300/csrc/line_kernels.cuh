@@ -91,6 +91,51 @@ __device__ __forceinline__ void line_limiter(int kind, double kappa, double a, d
   }
 }
 
+// Film H_i = H0 + X_i^2/2 - D_i at node i (the roughness is added by the caller).
+__device__ __forceinline__ double line_film_h(const LineInst& q, int i, double H0, double D) {
+  const double X = q.xa + i * q.h;
+  return H0 + 0.5 * X * X - D;
+}
+
+// rho, eps, u and the material derivatives of node o from P[o] and H[o] (float64).
+// (No restrict qualifiers: a fused kernel reads back what its other threads wrote.)
+__device__ __forceinline__ void line_node(const LineInst& q, size_t o, const double* P, const double* H, double* rho,
+                                          double* drho, double* deta_rel, double* eps, double* u) {
+  double r, dr, ln_eta, de;
+  line_material(q, P[o], r, dr, ln_eta, de);
+  const double Hh = H[o];
+  rho[o] = r;
+  drho[o] = dr;
+  deta_rel[o] = de;
+  eps[o] = r * Hh * Hh * Hh / q.lam * exp(-ln_eta);
+  u[o] = r * Hh;
+}
+
+// One chunk k0 .. k0 + kmax - 1 of the deformation sum of node i in double-float,
+// sum_k K_{|i-k|} V_k, accumulated in order by the Ogita-Rump-Oishi Dot2 scheme (error-free
+// products and sums, the errors summed in float32) and normalised to (hi, lo).
+__device__ __forceinline__ float2 line_deform_chunk(const float2* __restrict__ gtab, const double* __restrict__ V,
+                                                    int i, int k0, int kmax) {
+  float s = 0.f, c = 0.f;
+  for (int k = 0; k < kmax; ++k) {
+    int d = i - (k0 + k);
+    d = d < 0 ? -d : d;
+    const float2 g = gtab[d];
+    const df vd = df_from_double(V[k0 + k]);
+    const float p = __fmul_rn(g.x, vd.hi);
+    float e = __fmaf_rn(g.x, vd.hi, -p);
+    e = __fmaf_rn(g.x, vd.lo, e);
+    e = __fmaf_rn(g.y, vd.hi, e);
+    float t1, t2;
+    two_sum(s, p, t1, t2);
+    s = t1;
+    c = __fadd_rn(c, __fadd_rn(t2, e));
+  }
+  float hi, lo;
+  fast_two_sum(s, c, hi, lo);
+  return make_float2(hi, lo);
+}
+
 // Cell integral of log|x_i - x'| over a cell at distance d (in cells), float64.
 __device__ __forceinline__ double line_cell_integral(int d, double h) {
   const double tp = (d + 0.5) * h, tm = (d - 0.5) * h;

@@ -139,13 +139,8 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_border(const LineInst* __restri
 
 // z_j = M^-1 v_j from z1 = Jb^-1 v_j[0:n]: xi = (h sum z1 - v_j[n]) / den, z = z1 - xi zH
 // (jd != null: the Krylov index is read from device memory, the loop counter of a device-driven solve)
-__global__ void __launch_bounds__(kNkBlock) k_nk_prec(const LineInst* __restrict__ inst, NkBuf b, int j,
-                                                      const double* __restrict__ sigma, const int* __restrict__ skip,
-                                                      int N, const int* __restrict__ jd) {
-  const int z = blockIdx.x;
-  if (skip[z]) return;
-  if (jd) j = *jd;
-  __shared__ double sh[kNkBlock];
+__device__ __forceinline__ void nk_prec(const LineInst* inst, const NkBuf& b, int j, const double* sigma, int N, int z,
+                                        double* sh) {
   const int n = N - 2, n1 = n + 1;
   double s = 0.0;
   for (int r = threadIdx.x; r < n; r += kNkBlock) s += sigma[(size_t)z * n + r];
@@ -165,6 +160,16 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_prec(const LineInst* __restrict
     zn[N - 1] = 0.0;
     b.zh0[z] = xi;
   }
+}
+
+__global__ void __launch_bounds__(kNkBlock) k_nk_prec(const LineInst* __restrict__ inst, NkBuf b, int j,
+                                                      const double* __restrict__ sigma, const int* __restrict__ skip,
+                                                      int N, const int* __restrict__ jd) {
+  const int z = blockIdx.x;
+  if (skip[z]) return;
+  if (jd) j = *jd;
+  __shared__ double sh[kNkBlock];
+  nk_prec(inst, b, j, sigma, N, z, sh);
 }
 
 // Exact directional derivative of R_i: (dR/dP) v + (dR/dH0) v_H0, given the
@@ -236,6 +241,17 @@ __device__ __forceinline__ double line_jv_row_c(const JvArgs& q, const double* _
   return (F1 - F0) * ih - dq * ih2;
 }
 
+// w = J_Phi z at interior node i (the force row is added by the Arnoldi step)
+__device__ __forceinline__ void nk_jv(const LineInst* inst, const NkBuf& b, const JvArgs& q, const uint8_t* act, int z,
+                                      int i, int N) {
+  const int n = N - 2, n1 = n + 1;
+  const size_t base = (size_t)z * N;
+  const double h = inst[z].h;
+  const double jv = line_jv_row_c(q, b.jc, base, i, 1.0 / h, 1.0 / (h * h));
+  const size_t o = (size_t)z * n + (i - 1);
+  b.w[(size_t)z * n1 + (i - 1)] = act[o] ? q.zn[base + i] : jv * b.jc[4 * (base + i) + 3];
+}
+
 // w = J_Phi z for the interior rows (the force row is added in k_nk_arnoldi)
 __global__ void k_nk_jv(const LineInst* __restrict__ inst, NkBuf b, JvArgs q, const uint8_t* __restrict__ act,
                         const int* __restrict__ skip, int N) {
@@ -243,12 +259,7 @@ __global__ void k_nk_jv(const LineInst* __restrict__ inst, NkBuf b, JvArgs q, co
   if (skip[z]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;  // interior node
   if (i > N - 2) return;
-  const int n = N - 2, n1 = n + 1;
-  const size_t base = (size_t)z * N;
-  const double h = inst[z].h;
-  const double jv = line_jv_row_c(q, b.jc, base, i, 1.0 / h, 1.0 / (h * h));
-  const size_t o = (size_t)z * n + (i - 1);
-  b.w[(size_t)z * n1 + (i - 1)] = act[o] ? q.zn[base + i] : jv * b.jc[4 * (base + i) + 3];
+  nk_jv(inst, b, q, act, z, i, N);
 }
 
 // out[z][i] = (dR_i/dP) v + (dR_i/dH0) v_H0 at interior nodes, 0 at the boundary
@@ -261,13 +272,8 @@ __global__ void k_line_jv_raw(const LineInst* __restrict__ inst, JvArgs q, doubl
 }
 
 // Arnoldi step j with modified Gram-Schmidt, Givens update, convergence test
-__global__ void __launch_bounds__(kNkBlock) k_nk_arnoldi(const LineInst* __restrict__ inst, NkBuf b, int j,
-                                                         const int* __restrict__ skip, double* __restrict__ rhs,
-                                                         int N, const int* __restrict__ jd) {
-  const int z = blockIdx.x;
-  if (skip[z]) return;
-  if (jd) j = *jd;
-  __shared__ double sh[kNkBlock];
+__device__ __forceinline__ void nk_arnoldi(const LineInst* inst, const NkBuf& b, int j, double* rhs, int N, int z,
+                                           double* sh) {
   const int n = N - 2, n1 = n + 1, m = b.m;
   double* w = b.w + (size_t)z * n1;
   const double* Zj = b.Z + ((size_t)z * m + j) * n1;
@@ -319,6 +325,59 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_arnoldi(const LineInst* __restr
     b.gm_k[z] = j + 1;
     if (fabs(g[j + 1]) <= b.rtol[z] * b.beta0[z] || j + 1 == m || nn == 0.0) b.gm_conv[z] = 1;
   }
+}
+
+__global__ void __launch_bounds__(kNkBlock) k_nk_arnoldi(const LineInst* __restrict__ inst, NkBuf b, int j,
+                                                         const int* __restrict__ skip, double* __restrict__ rhs,
+                                                         int N, const int* __restrict__ jd) {
+  const int z = blockIdx.x;
+  if (skip[z]) return;
+  if (jd) j = *jd;
+  __shared__ double sh[kNkBlock];
+  nk_arnoldi(inst, b, j, rhs, N, z, sh);
+}
+
+// One Krylov step of an instance of at most kNkSmallN nodes in one CTA: the preconditioned
+// vector z_j (k_nk_prec), the film's directional derivative dH = -K z + xi in double-float
+// (k_line_deform's chunks of kDefChunk sources, summed as k_line_film sums them), w = J z
+// (k_nk_jv) and the Arnoldi step (k_nk_arnoldi), with block barriers in place of the kernel
+// boundaries.  The same arithmetic in the same order, so the same results bit for bit, in one
+// launch instead of five.
+constexpr int kNkSmallN = 257;
+constexpr int kDefChunk = 128;  // sources per chunk of k_line_deform
+__global__ void __launch_bounds__(kNkBlock) k_nk_krylov_small(const LineInst* __restrict__ inst, NkBuf b, int j,
+                                                              const double* __restrict__ sigma,
+                                                              const int* __restrict__ skip, int N,
+                                                              const int* __restrict__ jd,
+                                                              const float2* __restrict__ gtab, JvArgs q,
+                                                              const uint8_t* __restrict__ act,
+                                                              double* __restrict__ rhs) {
+  const int z = blockIdx.x;
+  if (skip[z]) return;
+  if (jd) j = *jd;
+  __shared__ double sh[kNkBlock];
+  nk_prec(inst, b, j, sigma, N, z, sh);
+  __syncthreads();
+  const size_t base = (size_t)z * N;
+  const double xi = b.zh0[z];
+  const bool elastic = inst[z].elastic != 0;
+  double* dH = const_cast<double*>(q.dH);
+  for (int i = threadIdx.x; i < N; i += kNkBlock) {
+    double Dd = 0.0;
+    if (elastic) {
+      df D = df_zero();
+      for (int k0 = 0; k0 < N; k0 += kDefChunk) {
+        const float2 p = line_deform_chunk(gtab + base, b.znode + base, i, k0, min(kDefChunk, N - k0));
+        D = df_add(D, make_df(p.x, p.y));
+      }
+      Dd = df_to_double(D);
+    }
+    dH[base + i] = -Dd + xi;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x + 1; i <= N - 2; i += kNkBlock) nk_jv(inst, b, q, act, z, i, N);
+  __syncthreads();
+  nk_arnoldi(inst, b, j, rhs, N, z, sh);
 }
 
 // y = R^-1 g over the k Arnoldi steps, delta = sum y_j z_j
@@ -510,6 +569,30 @@ static cudaError_t paqif_on(LineCtx* c, const double* rhs, double* x, bool facto
   return factor ? launch_paqif_factor(L, b.fstore, c->st) : launch_paqif_resolve(L, b.fstore, c->st);
 }
 
+// Krylov step j (or the index at jd, in a device-driven solve) after the preconditioner's
+// PAQIF solve: z_j, the film derivative, w = J z and the Arnoldi step; one CTA per instance for
+// small plain-precision instances, else the stage kernels.
+static cudaError_t krylov_step(LineCtx* c, const double* P, int j, const int* jd) {
+  NkBuf& b = *(NkBuf*)c->nk;
+  const int ni = c->n_inst, N = c->N;
+  JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, b.znode};
+  if (c->fuse && c->precision == 0 && N <= kNkSmallN) {
+    k_nk_krylov_small<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, b.skip, N, jd, c->gtab, q, c->act,
+                                                  c->rhs);
+    note_launch();
+    return cudaGetLastError();
+  }
+  k_nk_prec<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, b.skip, N, jd);
+  note_launch();
+  cudaError_t e = line_krylov_deform(c, b.znode, b.zh0, b.skip);
+  if (e != cudaSuccess) return e;
+  k_nk_jv<<<dim3((N + 255) / 256, ni), 256, 0, c->st>>>(c->inst, b, q, c->act, b.skip, N);
+  note_launch();
+  k_nk_arnoldi<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, b.skip, c->rhs, N, jd);
+  note_launch();
+  return cudaGetLastError();
+}
+
 static bool all_set(LineCtx* c, const int* a, const int* b2, cudaError_t& e) {
   std::vector<int> ha(c->n_inst), hb(c->n_inst);
   e = cudaMemcpyAsync(ha.data(), a, sizeof(int) * c->n_inst, cudaMemcpyDeviceToHost, c->st);
@@ -585,15 +668,8 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
     note_launch();
     e = paqif_on(c, c->rhs, c->sigma, false);
     if (e != cudaSuccess) return e;
-    k_nk_prec<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, b.skip, N, nullptr);
-    note_launch();
-    e = line_krylov_deform(c, b.znode, b.zh0, b.skip);
+    e = krylov_step(c, P, j, nullptr);
     if (e != cudaSuccess) return e;
-    JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, b.znode};
-    k_nk_jv<<<gn, 256, 0, c->st>>>(c->inst, b, q, c->act, b.skip, N);
-    note_launch();
-    k_nk_arnoldi<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, b.skip, c->rhs, N, nullptr);
-    note_launch();
     if (!c->capturing && (j + 1) % 8 == 0 && j + 1 < b.m) {
       if (all_set(c, c->done, b.gm_conv, e)) break;
       if (e != cudaSuccess) return e;
@@ -697,15 +773,8 @@ cudaError_t line_nk_capture_solve(LineCtx* c, double* P, double* H0, const doubl
     note_launch();
     cudaError_t ee = paqif_on(c, c->rhs, c->sigma, false);
     if (ee != cudaSuccess) return ee;
-    k_nk_prec<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, 0, c->sigma, b.skip, N, b.loop + 1);
-    note_launch();
-    ee = line_krylov_deform(c, b.znode, b.zh0, b.skip);
+    ee = krylov_step(c, P, 0, b.loop + 1);
     if (ee != cudaSuccess) return ee;
-    JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, b.znode};
-    k_nk_jv<<<gn, 256, 0, c->st>>>(c->inst, b, q, c->act, b.skip, N);
-    note_launch();
-    k_nk_arnoldi<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, 0, b.skip, c->rhs, N, b.loop + 1);
-    note_launch();
     return nk_loop(c, hk, 1, 3, b.m, 1, b.gm_conv);
   };
   auto trial_body = [&](cudaGraphConditionalHandle ht) -> cudaError_t {

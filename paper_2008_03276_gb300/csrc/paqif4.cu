@@ -1146,6 +1146,8 @@ static cudaError_t p4_attrs() {
 }
 
 cudaError_t paqif_prepare(int beta) {
+  const cudaError_t e = paqif_pair_prepare(beta);
+  if (e != cudaSuccess) return e;
   switch (beta) {
 #define EHL_CASE(BB) \
   case BB:           \

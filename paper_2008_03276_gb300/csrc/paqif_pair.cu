@@ -696,6 +696,21 @@ static cudaError_t launch_pair(const PaqifLaunch& L, int r, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t paqif_pair_prepare(int beta) {
+  switch (beta) {
+    case 1:
+      return pair_attrs<1>();
+    case 2:
+      return pair_attrs<2>();
+    case 3:
+      return pair_attrs<3>();
+    case 4:
+      return pair_attrs<4>();
+    default:
+      return cudaSuccess;
+  }
+}
+
 cudaError_t launch_paqif_pair(const PaqifLaunch& L, int r, cudaStream_t st) {
   if (L.mode == 2 || L.f32 || (reinterpret_cast<uintptr_t>(L.band) & 15u) != 0) return cudaErrorInvalidValue;
   switch (L.beta) {

@@ -16,5 +16,8 @@ size_t paqif_pair_stack_bytes(int n_sys, int n, int beta, int r);
 // One launch with r blocks per system (L.stack: paqif_pair_stack_bytes bytes, 16-byte aligned;
 // L.band on a 16-byte boundary).
 cudaError_t launch_paqif_pair(const PaqifLaunch& L, int r, cudaStream_t st);
+// Its shared-memory attribute for half-band beta on the current device (nothing for beta > 4),
+// set once per device; called by paqif_prepare, before any stream capture.
+cudaError_t paqif_pair_prepare(int beta);
 
 }  // namespace ehl

@@ -113,3 +113,40 @@ def test_point_257_fft_device_driven():
     Pint = P[0].T[1:-1, 1:-1].ravel()
     R = pr.residual(pb, Pint, float(H0[0]))
     assert np.max(np.abs(np.minimum(Pint, R))) <= max(2e-8, pr.rounding_floor(pb, Pint, float(H0[0])))
+
+
+def paper_solve(graph, n_inst=1, per=None, **kw):
+    q = dict(nx=129, M=20.0, L=10.0, limiter=0, halfband=2, method=0, tol=1e-8, max_iter=4000, levels=0)
+    q.update(kw)
+    p = ops.default_params(1, graph=graph, **q)
+    per_inst = None if per is None else [ops.default_params(1, graph=graph, **{**q, **d}) for d in per]
+    ctx = ops.Context(p, n_inst=n_inst, per_inst=per_inst)
+    P, H0, iters, res, code = ctx.solve(check=False)
+    torch.cuda.synchronize()
+    return P.cpu().numpy(), H0.cpu().numpy(), iters.cpu().numpy(), res.cpu().numpy(), code, ctx
+
+
+def test_paper_iteration_device_driven_matches_host_driven():
+    """Method 0 (the paper's iteration, Sec. 3.3.3-3.3.4) as one device-side loop: the same
+    kernels in the same order, so the same iteration count and the same iterate bit for bit;
+    and the oracle's restatement of the iteration to the tolerance of its own test."""
+    P2, H2, it2, r2, c2, ctx = paper_solve(2)
+    P0, H00, it0, r0, c0, _ = paper_solve(0)
+    assert c2 == 0 and c0 == 0
+    assert np.array_equal(it2, it0)
+    assert np.array_equal(P2, P0) and np.array_equal(H2, H00)
+    pb = lr.LineProblem(129, 20.0, 10.0, limiter="minmod", dist_weight=0.5)
+    Pr, H0r, info = lr.solve_paper(pb, tol=1e-8)
+    assert info["converged"] and abs(int(it2[0]) - info["iters"]) <= 3
+    P3, H3, it3, r3, c3 = ctx.solve(check=False)  # the graph is replayed
+    assert int(c3) == 0 and np.array_equal(P3.cpu().numpy(), P2)
+
+
+def test_paper_iteration_device_driven_batch():
+    """A batch of loads, each instance leaving the device loop when it converges."""
+    per = [dict(M=m, L=l) for m, l in ((10.0, 5.0), (15.0, 8.0), (25.0, 10.0))]
+    P2, H2, it2, r2, c2, _ = paper_solve(2, n_inst=3, per=per)
+    P0, H00, it0, r0, c0, _ = paper_solve(0, n_inst=3, per=per)
+    assert c2 == 0 and c0 == 0
+    assert np.array_equal(it2, it0) and len(set(it2.tolist())) > 1
+    assert np.array_equal(P2, P0) and np.array_equal(H2, H00)
