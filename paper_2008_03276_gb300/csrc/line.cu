@@ -504,7 +504,8 @@ struct LineRowCtx {
 // Also writes dR/dH0 (jh, frozen or exact) and |J_ii| (dg, kind 1) per row.
 __global__ void k_line_jac_band(const LineInst* __restrict__ inst, LineRowCtx c, const double* __restrict__ R,
                                 const int* __restrict__ skip, int kind, int beta, double* __restrict__ band,
-                                uint8_t* __restrict__ act, double* __restrict__ jh, double* __restrict__ dg) {
+                                uint8_t* __restrict__ act, double* __restrict__ jh, double* __restrict__ dg,
+                                double* __restrict__ rhs_out, int* __restrict__ act32) {
   const int z = blockIdx.y;
   if (skip && skip[z]) return;
   const int N = c.N, n = N - 2;
@@ -557,6 +558,9 @@ __global__ void k_line_jac_band(const LineInst* __restrict__ inst, LineRowCtx c,
     if (dg) dg[(size_t)z * n + r] = d;
   }
   act[(size_t)z * n + r] = a ? 1 : 0;
+  // the paper iteration's right-hand side and PAQIF's int32 row flags, when asked for
+  if (rhs_out) rhs_out[(size_t)z * n + r] = a ? 0.0 : -Ri;
+  if (act32) act32[(size_t)z * n + r] = a ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- paper relaxation
@@ -569,6 +573,11 @@ __global__ void k_line_paper_rhs(const double* __restrict__ R, const uint8_t* __
   rhs[(size_t)z * n + r] = act[(size_t)z * n + r] ? 0.0 : -R[(size_t)z * N + r + 1];
 }
 
+// H0 - c (pi/2 - h s), s = h-less sum of P (Sec. 3.3.4, Eq. eqn75 with the line-contact load)
+__device__ __forceinline__ double line_h0_step(const LineInst& q, double H0, double s) {
+  return H0 - q.c_h0 * (0.5 * M_PI - q.h * s);
+}
+
 // P <- max(0, P + omega D sigma) (Sec. 3.3.4, Eq. eqn69); block partial sums of the new P
 // (one thread per node, the same blocks as k_line_residual)
 __global__ void __launch_bounds__(kNodeBlock) k_line_paper_update(const LineInst* __restrict__ inst,
@@ -576,7 +585,7 @@ __global__ void __launch_bounds__(kNodeBlock) k_line_paper_update(const LineInst
                                                                   const double* __restrict__ eps,
                                                                   const int* __restrict__ skip,
                                                                   double* __restrict__ P, double* __restrict__ blk,
-                                                                  int nblk, int N) {
+                                                                  int nblk, int N, double* __restrict__ H0) {
   const int z = blockIdx.y, n = N - 2;
   if (skip && skip[z]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -603,6 +612,12 @@ __global__ void __launch_bounds__(kNodeBlock) k_line_paper_update(const LineInst
     __syncthreads();
   }
   if (threadIdx.x == 0) blk[((size_t)z * nblk + blockIdx.x) * 4 + 1] = s[0];
+  // one block holds the whole sum: the H0 update of k_line_h0_update here
+  if (H0 && nblk == 1 && threadIdx.x == 0) {
+    double t = 0.0;
+    t += s[0];
+    H0[z] = line_h0_step(q, H0[z], t);
+  }
 }
 
 // H0 <- H0 - c (pi/2 - h sum P)   (Sec. 3.3.4, Eq. eqn75 with the line-contact load)
@@ -612,7 +627,7 @@ __global__ void k_line_h0_update(const LineInst* __restrict__ inst, const double
   if (z >= n_inst || (skip && skip[z])) return;
   double s = 0.0;
   for (int b = 0; b < nblk; ++b) s += blk[((size_t)z * nblk + b) * 4 + 1];
-  H0[z] -= inst[z].c_h0 * (0.5 * M_PI - inst[z].h * s);
+  H0[z] = line_h0_step(inst[z], H0[z], s);
 }
 
 // ---------------------------------------------------------------- start
@@ -711,11 +726,11 @@ cudaError_t line_finalize(LineCtx* c, int* done, int* iters) {
 }
 
 cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, uint8_t* act, double* jh,
-                          double* dg, const int* skip) {
+                          double* dg, const int* skip, double* rhs_out, int* act32) {
   LineRowCtx q = line_row_ctx(c);
   q.P = P;
   dim3 g((c->n + 127) / 128, c->n_inst);
-  k_line_jac_band<<<g, 128, 0, c->st>>>(c->inst, q, c->R, skip, kind, c->beta, band, act, jh, dg);
+  k_line_jac_band<<<g, 128, 0, c->st>>>(c->inst, q, c->R, skip, kind, c->beta, band, act, jh, dg, rhs_out, act32);
   note_launch();
   return cudaGetLastError();
 }
@@ -779,11 +794,17 @@ cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double
   if (e != cudaSuccess) return e;
   e = line_finalize(c, c->done, c->iters);
   if (e != cudaSuccess) return e;
-  e = line_jac_band(c, P, 0, c->band, c->act, nullptr, nullptr, c->done);
+  int* act32 = (int*)((unsigned char*)c->pq_ws + align_up(paqif_stack_bytes(c->n_inst, c->n, c->beta), kWorkspaceAlign));
+  // with fuse the band kernel also writes the right-hand side and PAQIF's row flags, and the
+  // update kernel of a one-block instance updates H0 (the same values, three launches fewer)
+  e = line_jac_band(c, P, 0, c->band, c->act, nullptr, nullptr, c->done, c->fuse ? c->rhs : nullptr,
+                    c->fuse ? act32 : nullptr);
   if (e != cudaSuccess) return e;
-  dim3 g((c->n + 127) / 128, c->n_inst);
-  k_line_paper_rhs<<<g, 128, 0, c->st>>>(c->R, c->act, c->done, c->rhs, c->N);
-  note_launch();
+  if (!c->fuse) {
+    dim3 g((c->n + 127) / 128, c->n_inst);
+    k_line_paper_rhs<<<g, 128, 0, c->st>>>(c->R, c->act, c->done, c->rhs, c->N);
+    note_launch();
+  }
   PaqifLaunch L;
   L.n_sys = c->n_inst;
   L.n = c->n;
@@ -791,20 +812,26 @@ cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double
   L.mode = 0;
   L.band = c->band;
   L.rhs = c->rhs;
-  L.act = (int*)((unsigned char*)c->pq_ws + align_up(paqif_stack_bytes(c->n_inst, c->n, c->beta), kWorkspaceAlign));
+  L.act = act32;
   L.stack = c->pq_ws;
   L.x = c->sigma;
   L.iters = nullptr;
   L.info = c->pq_info;
-  e = launch_expand_active(c->act, L.act, (size_t)c->n_inst * c->n, c->st);
-  if (e != cudaSuccess) return e;
+  if (!c->fuse) {
+    e = launch_expand_active(c->act, L.act, (size_t)c->n_inst * c->n, c->st);
+    if (e != cudaSuccess) return e;
+  }
   e = launch_paqif(L, c->st);
   if (e != cudaSuccess) return e;
+  const bool h0_here = c->fuse && c->nblk == 1;
   dim3 gu((c->N + kNodeBlock - 1) / kNodeBlock, c->n_inst);
-  k_line_paper_update<<<gu, kNodeBlock, 0, c->st>>>(c->inst, c->sigma, c->eps, c->done, P, c->blk, c->nblk, c->N);
+  k_line_paper_update<<<gu, kNodeBlock, 0, c->st>>>(c->inst, c->sigma, c->eps, c->done, P, c->blk, c->nblk, c->N,
+                                                     h0_here ? H0 : nullptr);
   note_launch();
-  k_line_h0_update<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(c->inst, c->blk, c->nblk, c->done, H0, c->n_inst);
-  note_launch();
+  if (!h0_here) {
+    k_line_h0_update<<<(c->n_inst + 127) / 128, 128, 0, c->st>>>(c->inst, c->blk, c->nblk, c->done, H0, c->n_inst);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 

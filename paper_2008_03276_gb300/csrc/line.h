@@ -81,7 +81,7 @@ cudaError_t line_state(LineCtx* c, const double* P, const double* H0, const doub
                        int* unused);
 cudaError_t line_finalize(LineCtx* c, int* done, int* iters);
 cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, uint8_t* act, double* jh,
-                          double* dg, const int* skip);
+                          double* dg, const int* skip, double* rhs_out = nullptr, int* act32 = nullptr);
 cudaError_t line_start(LineCtx* c, double* P, double* H0, const double* rough);
 cudaError_t line_paper_iteration(LineCtx* c, double* P, double* H0, const double* rough);
 // Graph mode 2 of the paper's iteration: the iterations of one grid as a device-side while-loop

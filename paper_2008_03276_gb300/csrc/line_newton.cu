@@ -345,15 +345,17 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_arnoldi(const LineInst* __restr
 // launch instead of five.
 constexpr int kNkSmallN = 257;
 constexpr int kDefChunk = 128;  // sources per chunk of k_line_deform
+// (It skips an instance that is done or whose GMRES has converged itself, so no skip kernel
+// runs before it.)
 __global__ void __launch_bounds__(kNkBlock) k_nk_krylov_small(const LineInst* __restrict__ inst, NkBuf b, int j,
                                                               const double* __restrict__ sigma,
-                                                              const int* __restrict__ skip, int N,
+                                                              const int* __restrict__ done, int N,
                                                               const int* __restrict__ jd,
                                                               const float2* __restrict__ gtab, JvArgs q,
                                                               const uint8_t* __restrict__ act,
                                                               double* __restrict__ rhs) {
   const int z = blockIdx.x;
-  if (skip[z]) return;
+  if (done[z] || b.gm_conv[z]) return;
   if (jd) j = *jd;
   __shared__ double sh[kNkBlock];
   nk_prec(inst, b, j, sigma, N, z, sh);
@@ -569,19 +571,23 @@ static cudaError_t paqif_on(LineCtx* c, const double* rhs, double* x, bool facto
   return factor ? launch_paqif_factor(L, b.fstore, c->st) : launch_paqif_resolve(L, b.fstore, c->st);
 }
 
+static bool krylov_fused(const LineCtx* c) { return c->fuse && c->precision == 0 && c->N <= kNkSmallN; }
+
 // Krylov step j (or the index at jd, in a device-driven solve) after the preconditioner's
 // PAQIF solve: z_j, the film derivative, w = J z and the Arnoldi step; one CTA per instance for
-// small plain-precision instances, else the stage kernels.
+// small plain-precision instances, else the skip flags and the stage kernels.
 static cudaError_t krylov_step(LineCtx* c, const double* P, int j, const int* jd) {
   NkBuf& b = *(NkBuf*)c->nk;
   const int ni = c->n_inst, N = c->N;
   JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, b.znode};
-  if (c->fuse && c->precision == 0 && N <= kNkSmallN) {
-    k_nk_krylov_small<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, b.skip, N, jd, c->gtab, q, c->act,
+  if (krylov_fused(c)) {
+    k_nk_krylov_small<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, c->done, N, jd, c->gtab, q, c->act,
                                                   c->rhs);
     note_launch();
     return cudaGetLastError();
   }
+  k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.gm_conv, b.skip, ni);
+  note_launch();
   k_nk_prec<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, b.skip, N, jd);
   note_launch();
   cudaError_t e = line_krylov_deform(c, b.znode, b.zh0, b.skip);
@@ -662,10 +668,7 @@ cudaError_t line_nk_step(LineCtx* c, double* P, double* H0, const double* rough)
   if (e != cudaSuccess) return e;
   k_nk_border<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, c->sigma, c->done, c->rhs, N);
   note_launch();
-  const dim3 gn((N + 255) / 256, ni);
   for (int j = 0; j < b.m; ++j) {
-    k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.gm_conv, b.skip, ni);
-    note_launch();
     e = paqif_on(c, c->rhs, c->sigma, false);
     if (e != cudaSuccess) return e;
     e = krylov_step(c, P, j, nullptr);
@@ -769,8 +772,6 @@ cudaError_t line_nk_capture_solve(LineCtx* c, double* P, double* H0, const doubl
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stall, 0, sizeof(int) * ni, s0);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.loop, 0, sizeof(int) * kLoopSlots, s0);
   auto krylov_body = [&](cudaGraphConditionalHandle hk) -> cudaError_t {
-    k_nk_skip<<<(ni + 127) / 128, 128, 0, c->st>>>(c->done, b.gm_conv, b.skip, ni);
-    note_launch();
     cudaError_t ee = paqif_on(c, c->rhs, c->sigma, false);
     if (ee != cudaSuccess) return ee;
     ee = krylov_step(c, P, 0, b.loop + 1);
