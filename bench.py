@@ -50,9 +50,9 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one full-size paqif_pair_kernel<4> launch (leg A) from the ncu
 # capture summarised in profiles/, valid only for the kernel sources with these sha256
 # prefixes; any other source reports traffic = null.
-PAQIF_TRAFFIC = {('f7d8f0ad2cfa04b3', '7992305e7ad41559'): 641414912 + 351703040}
+PAQIF_TRAFFIC = {('11059c952dd15f25', '7992305e7ad41559'): 637709568 + 350767616}
 # smsp__inst_executed.sum of the same launch and capture: the kernel is bound by instruction issue
-PAQIF_WARP_INSTRUCTIONS = {('f7d8f0ad2cfa04b3', '7992305e7ad41559'): 302703616}
+PAQIF_WARP_INSTRUCTIONS = {('11059c952dd15f25', '7992305e7ad41559'): 301534208}
 SCHEDULERS = 152 * 4  # SMs x warp schedulers per SM, one warp instruction issued per scheduler and cycle
 
 
@@ -491,10 +491,11 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
                     converged=int(np.sum((r[:, 0] <= 10 * tol) & (r[:, 1] <= 10 * tol))), status=int(code))
 
     # C1: N = 129, M = 20, L = 10, minmod, beta 2, one instance
-    for key, method, graph in (("C1_method0", 0, 0), ("C1_method0_graph", 0, 2), ("C1_method1", 1, 0),
-                               ("C1_method1_graph", 1, 2)):
+    for key, method, graph, tune in (("C1_method0", 0, 0, 0), ("C1_method0_graph", 0, 2, 0),
+                                     ("C1_method1", 1, 0, 0), ("C1_method1_graph", 1, 2, 0),
+                                     ("C1_method1_graph_autotuned", 1, 2, 1)):
         p = ops.default_params(1, nx=129, M=20.0, L=10.0, limiter=0, halfband=2, method=method, tol=1e-8,
-                               max_iter=4000 if method == 0 else 60, graph=graph)
+                               max_iter=4000 if method == 0 else 60, graph=graph, autotune=tune)
         ctx = ops.Context(p)
         n0 = ops.kernel_launches()
         ms, out = _timed(torch, lambda: ctx.solve(check=False), reps=5)
@@ -502,7 +503,8 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
                  method=("paper relaxation" if method == 0 else "Newton-Krylov"),
                  loop=("host-driven" if graph == 0 else
                        "device-driven graph (the iterations as a graph while-loop)" if method == 0 else
-                       "device-driven graph (Newton, GMRES, line search as graph while-loops)"),
+                       "device-driven graph (Newton, GMRES, line search as graph while-loops)") +
+                      (", preconditioner partition count autotuned" if tune else ""),
                  ms=round(ms, 3), solves_per_s=round(1e3 / ms, 2),
                  kernels_per_solve=int((ops.kernel_launches() - n0) // 6))
         d.update(summary(out[2], out[3], out[4], 1e-8))
@@ -560,10 +562,9 @@ def config_legs(ops, inputs, torch, dev, paqif=None):
         res["C3" if prec == 0 else "C3_mixed"] = d
         del ctx
     # C4: point contact 257 x 257, M = 100, L = 10, minmod, beta 2: the direct-sum deformation in
-    # float64 / double-float (the paper's), with the Krylov products as float32 GEMMs, and the same
-    # convolution through the float64 FFT
+    # float64 / double-float (the paper's), and the same convolution through the float64 FFT
     Href = None
-    for key, prec, deform in (("C4", 0, 0), ("C4_mixed", 2, 0), ("C4_fft", 0, 1)):
+    for key, prec, deform in (("C4", 0, 0), ("C4_fft", 0, 1)):
         p = ops.default_params(2, nx=257, ny=257, M=100.0, L=10.0, limiter=0, halfband=2, method=1, tol=1e-8,
                                max_iter=60, coarse_min_nodes=33, precision=prec, deform=deform, autotune=deform,
                                graph=2 if deform else 0)
@@ -798,7 +799,9 @@ def profile_case(name):
     deformation, autotuned x-line partitions) solved once host-driven (graph 0), so that a launch
     list sees every kernel.
     pt_deform: three residual evaluations of a 129^2 point contact with the direct-sum deformation
-    (deform 0), each one launch of the float64 direct-sum kernel."""
+    (deform 0), each one launch of the float64 direct-sum kernel.
+    c1_nk, c1_paper: one C1 solve (N = 129, M = 20, L = 10, minmod, beta 2) by Newton-Krylov or
+    by the paper's iteration, host-driven (graph 0), so that a launch list sees every kernel."""
     import torch
 
     from paper_2008_03276_gb300 import ops
@@ -836,6 +839,14 @@ def profile_case(name):
         for _ in range(3):
             ctx.residual(P, H0)
         torch.cuda.synchronize()
+    elif name in ("c1_nk", "c1_paper"):
+        method = 1 if name == "c1_nk" else 0
+        p = ops.default_params(1, nx=129, M=20.0, L=10.0, limiter=0, halfband=2, method=method, tol=1e-8,
+                               max_iter=60 if method else 4000, graph=0)
+        ctx = ops.Context(p)
+        out = ctx.solve(check=False)
+        torch.cuda.synchronize()
+        print(name, "status", int(out[4]), "iterations", out[2].tolist())
 
 
 def main():
@@ -854,7 +865,8 @@ def main():
     ap.add_argument("--ehl-graph", type=int, default=2, choices=[0, 2],
                     help="leg B's loop: 2 device-driven CUDA graph (default); 0 host-driven, for ncu launch lists "
                          "(ncu does not list the kernels inside conditional graph nodes)")
-    ap.add_argument("--profile", choices=["tc_gemm", "c4_fft", "pt_deform"], help="run a small case for an ncu capture and exit")
+    ap.add_argument("--profile", choices=["tc_gemm", "c4_fft", "pt_deform", "c1_nk", "c1_paper"],
+                    help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile:
         profile_case(args.profile)
