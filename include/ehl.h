@@ -67,7 +67,13 @@ unsigned long long ehl_kernel_launches(void);
  * Sec. 2.2.4 Steps 5 and 7 (projection of the computed solution onto
  * U >= 0).  The library picks the partition count r of Sec. 2.2.4 from the
  * batch shape (ehl_paqif_partitions); every r gives the same solution up to
- * rounding, and the projection follows the full solve.
+ * rounding, and the projection follows the full solve.  For beta <= 4 in
+ * modes 0 and 1 the solve runs a kernel with one lane per block side and
+ * r in {1, 2, 4, 8, 16}, chosen by the same measure (elimination levels
+ * plus 2 beta r for the reduced system) among the r whose blocks fit in
+ * one round of its resident lanes; ehl_paqif_partitions reports the count
+ * of the general kernel, which the other cases and the factor-once entry
+ * points use.
  *
  * Solves n_sys independent banded systems A_s x_s = b_s of order n with
  * half-bandwidth beta.

@@ -729,8 +729,12 @@ cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, u
                           double* dg, const int* skip, double* rhs_out, int* act32) {
   LineRowCtx q = line_row_ctx(c);
   q.P = P;
-  dim3 g((c->n + 127) / 128, c->n_inst);
-  k_line_jac_band<<<g, 128, 0, c->st>>>(c->inst, q, c->R, skip, kind, c->beta, band, act, jh, dg, rhs_out, act32);
+  // one thread per row; the rows' float64 work (kind 0: three frozen-Jacobian entries per band
+  // entry, each with two divisions) is FP64-pipe bound per SM, so a launch that would occupy
+  // fewer CTAs than SMs (a single small instance) uses one warp per CTA and spreads over 4x the SMs
+  const int tpb = (size_t)c->n_inst * ((c->n + 127) / 128) < (size_t)kSmCount ? 32 : 128;
+  dim3 g((c->n + tpb - 1) / tpb, c->n_inst);
+  k_line_jac_band<<<g, tpb, 0, c->st>>>(c->inst, q, c->R, skip, kind, c->beta, band, act, jh, dg, rhs_out, act32);
   note_launch();
   return cudaGetLastError();
 }

@@ -646,17 +646,27 @@ static int pair_min_ctas(int beta) {
   }
 }
 
-// The block count: the largest r whose blocks fit in one round of the resident lane pairs (a
-// second, partial round would double the time of the chain), r = 1 if none does.  Measured for
-// 4096 systems of n = 1024, b = 4 (CUDA events): 2.53, 1.25, 0.55, 0.72 ms for r = 1, 2, 4, 8.
+// The block count: among the r whose blocks fit in one round of the resident lane pairs (a
+// second, partial round would double the time of the chain; r = 1 always qualifies), the one
+// with the shortest chain: its sf elimination levels plus the 2r block steps of the reduced
+// system, about b levels each (the system's lanes eliminate it one block row after another).
+// Measured for 4096 systems of n = 1024, b = 4 (CUDA events): 2.53, 1.25, 0.55, 0.72 ms for
+// r = 1, 2, 4, 8 (the rule takes 4); one system of n = 127, b = 2 took 42 us at r = 16, where
+// the reduced system is the chain.
 int paqif_pair_parts(int n_sys, int n, int beta, int mode, bool f32, bool factor_store) {
   if (beta < 1 || beta > 4 || mode == 2 || f32 || factor_store || n_sys < 1 || n < 1) return 0;
   const long long resident = (long long)kSmCount * pair_min_ctas(beta) * kPairBlocksPerCta;
   int best = 0;
+  long long best_cost = 0;
   for (int r = 1; r <= 16; r *= 2) {
     int s, sf;
     if (!pair_geom(n, beta, r, s, sf)) continue;
-    if (best == 0 || (long long)n_sys * r <= resident) best = r;
+    if (r > 1 && (long long)n_sys * r > resident) continue;
+    const long long cost = sf + (r > 1 ? 2LL * r * beta : 0);
+    if (best == 0 || cost < best_cost) {
+      best = r;
+      best_cost = cost;
+    }
   }
   return best;
 }
