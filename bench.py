@@ -50,9 +50,9 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) of one full-size paqif_pair_kernel<4> launch (leg A) from the ncu
 # capture summarised in profiles/, valid only for the kernel sources with these sha256
 # prefixes; any other source reports traffic = null.
-PAQIF_TRAFFIC = {('11059c952dd15f25', '7992305e7ad41559'): 637709568 + 350767616}
+PAQIF_TRAFFIC = {('748a5ae0e7d4221a', '7992305e7ad41559'): 636606976 + 350771200}
 # smsp__inst_executed.sum of the same launch and capture: the kernel is bound by instruction issue
-PAQIF_WARP_INSTRUCTIONS = {('11059c952dd15f25', '7992305e7ad41559'): 301534208}
+PAQIF_WARP_INSTRUCTIONS = {('748a5ae0e7d4221a', '7992305e7ad41559'): 301534208}
 SCHEDULERS = 152 * 4  # SMs x warp schedulers per SM, one warp instruction issued per scheduler and cycle
 
 

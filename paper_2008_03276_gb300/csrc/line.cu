@@ -563,6 +563,51 @@ __global__ void k_line_jac_band(const LineInst* __restrict__ inst, LineRowCtx c,
   if (act32) act32[(size_t)z * n + r] = a ? 1 : 0;
 }
 
+// kind 0 with one thread per band entry: a row's 2b+1 entries, each with its distributed
+// neighbours, are independent chains of float64 divisions (FP64 latency, not throughput, sets
+// the time of a row), so each entry gets its own thread; the entries are computed by the same
+// code as in k_line_jac_band.  The thread of the diagonal entry also writes the row's dR/dH0
+// and flag and, when asked, the paper iteration's right-hand side and PAQIF's int32 flag.
+__global__ void k_line_jac_band0(const LineInst* __restrict__ inst, LineRowCtx c, const double* __restrict__ R,
+                                 const int* __restrict__ skip, int beta, double* __restrict__ band,
+                                 uint8_t* __restrict__ act, double* __restrict__ jh, double* __restrict__ rhs_out,
+                                 int* __restrict__ act32) {
+  const int z = blockIdx.y;
+  if (skip && skip[z]) return;
+  const int N = c.N, n = N - 2;
+  const int bw = 2 * beta + 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * bw) return;
+  const int r = t / bw, j = t % bw;
+  LineRowCtx q = c;
+  q.base = (size_t)z * N;
+  q.h = inst[z].h;
+  const int i = r + 1;
+  const double ef1 = 0.5 * (c.eps[q.base + i] + c.eps[q.base + i + 1]);
+  const double ef0 = 0.5 * (c.eps[q.base + i - 1] + c.eps[q.base + i]);
+  const double Pi = c.P[q.base + i], Ri = R[q.base + i];
+  const bool a = (Pi <= 0.0) && (Ri > 0.0);
+  const double w = inst[z].dist_w, sw = inst[z].switch_eps_h;
+  const double cs = line_split_coef(inst[z]);
+  const int col = r - beta + j;  // interior column index, node col + 1
+  double v = 0.0;
+  if (col >= 0 && col < n) {
+    const int m = col + 1;
+    v = q.J_frozen(i, m, ef0, ef1, cs);
+    if (c.eps[q.base + m] / q.h <= sw) {
+      if (m - 1 >= 1) v -= w * q.J_frozen(i, m - 1, ef0, ef1, cs);
+      if (m + 1 <= N - 2) v -= w * q.J_frozen(i, m + 1, ef0, ef1, cs);
+    }
+  }
+  band[((size_t)z * n + r) * bw + j] = a ? (j == beta ? 1.0 : 0.0) : v;
+  if (j != beta) return;
+  const size_t o = (size_t)z * n + r;
+  if (jh) jh[o] = a ? 0.0 : q.JH_frozen(i, cs);
+  act[o] = a ? 1 : 0;
+  if (rhs_out) rhs_out[o] = a ? 0.0 : -Ri;
+  if (act32) act32[o] = a ? 1 : 0;
+}
+
 // ---------------------------------------------------------------- paper relaxation
 __global__ void k_line_paper_rhs(const double* __restrict__ R, const uint8_t* __restrict__ act,
                                  const int* __restrict__ skip, double* __restrict__ rhs, int N) {
@@ -729,12 +774,15 @@ cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, u
                           double* dg, const int* skip, double* rhs_out, int* act32) {
   LineRowCtx q = line_row_ctx(c);
   q.P = P;
-  // one thread per row; the rows' float64 work (kind 0: three frozen-Jacobian entries per band
-  // entry, each with two divisions) is FP64-pipe bound per SM, so a launch that would occupy
-  // fewer CTAs than SMs (a single small instance) uses one warp per CTA and spreads over 4x the SMs
-  const int tpb = (size_t)c->n_inst * ((c->n + 127) / 128) < (size_t)kSmCount ? 32 : 128;
-  dim3 g((c->n + tpb - 1) / tpb, c->n_inst);
-  k_line_jac_band<<<g, tpb, 0, c->st>>>(c->inst, q, c->R, skip, kind, c->beta, band, act, jh, dg, rhs_out, act32);
+  if (kind == 0) {  // one thread per band entry
+    const long long entries = (long long)c->n * (2 * c->beta + 1);
+    dim3 g((unsigned)((entries + 127) / 128), c->n_inst);
+    k_line_jac_band0<<<g, 128, 0, c->st>>>(c->inst, q, c->R, skip, c->beta, band, act, jh, rhs_out, act32);
+    note_launch();
+    return cudaGetLastError();
+  }
+  dim3 g((c->n + 127) / 128, c->n_inst);
+  k_line_jac_band<<<g, 128, 0, c->st>>>(c->inst, q, c->R, skip, kind, c->beta, band, act, jh, dg, rhs_out, act32);
   note_launch();
   return cudaGetLastError();
 }

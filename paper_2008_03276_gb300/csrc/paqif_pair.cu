@@ -651,8 +651,9 @@ static int pair_min_ctas(int beta) {
 // with the shortest chain: its sf elimination levels plus the 2r block steps of the reduced
 // system, about b levels each (the system's lanes eliminate it one block row after another).
 // Measured for 4096 systems of n = 1024, b = 4 (CUDA events): 2.53, 1.25, 0.55, 0.72 ms for
-// r = 1, 2, 4, 8 (the rule takes 4); one system of n = 127, b = 2 took 42 us at r = 16, where
-// the reduced system is the chain.
+// r = 1, 2, 4, 8 (the rule takes 4); one system of n = 127, b = 2: 42 us at r = 16, 39 us at the
+// rule's r = 4 (ncu launch times): a lone system's time is the latency of each step, not the
+// choice of r.
 int paqif_pair_parts(int n_sys, int n, int beta, int mode, bool f32, bool factor_store) {
   if (beta < 1 || beta > 4 || mode == 2 || f32 || factor_store || n_sys < 1 || n < 1) return 0;
   const long long resident = (long long)kSmCount * pair_min_ctas(beta) * kPairBlocksPerCta;
