@@ -26,10 +26,6 @@ adjoint_ref   dense adjoint of the converged line-contact state.
 cd_ref        the linear convection-diffusion workload of the line splittings:
               van Leer's kappa-scheme, the Ls0 / Ls1 x-line relaxation (Sec. 3.1, Sec. 6).
 
-Parity unpinned: line_ref.split_coefficient (the Newton matrices of the hybrid
-splittings L_hs1 / L_hs2, Sec. 3.3.2) -- iteration operators that nothing outside
-the oracle fixes.
-
 Every floating-point computation is float64.  Each function cites the passage
 of the paper it restates.  Functions whose result is not pinned by anything
 outside the oracle say "parity unpinned" in their docstring.

@@ -181,8 +181,10 @@ def split_coefficient(pb):
     the ``(1 - kappa)/4 (H_i - H_{i-1})`` that Eq. eqn58 splits off the upwind
     difference (Ls0 / Ls5); the rest of the convective term stays on the right-hand
     side.  Both use the weighted-change distribution where eps/h <= switch.
-    Parity unpinned: these matrices are the paper's iteration operators, which no
-    closed form or limit case fixes; only their fixed point (the residual) is pinned.
+    Pinned by the stencils of Eq. eqn42 and the textbook kappa differences (the coefficient of
+    the upwind difference in each, and of the farther upwind one) and, for the matrix it
+    scales, by central differences of the residual where the first-order upwind difference is
+    exact (tests/test_oracle_line.py).
     """
     if pb.splitting == "hs1":
         return (2.0 - pb.kappa) / 2.0

@@ -378,3 +378,78 @@ def test_kappa_scheme_grid_convergence(kappa):
     (l1a, l2a), (l1b, l2b) = norms(257, 513), norms(513, 1025)
     p1, p2 = np.log2(l1a / l1b), np.log2(l2a / l2b)
     assert 0.6 < p1 < 1.6 and 0.2 < p2 < 1.5, (p1, p2)
+
+
+def _split_coefficient_pin_holds():
+    """The hybrid splittings' Couette coefficient against the kappa stencils (see the test)."""
+    ok = lr.split_coefficient(lr.LineProblem(17, 20.0, 10.0, splitting="frozen")) is None
+    for kappa, *c in np.loadtxt(GOLDEN_KAPPA):
+        cm2, cm1, c0, cp1, cp2 = c
+        assert abs(sum(c)) <= 1e-15 and cp2 == 0.0
+        alpha = -cm2
+        beta = alpha - cm1
+        gamma = cp1
+        assert abs((beta - gamma) - c0) <= 1e-15
+        hs1 = lr.split_coefficient(lr.LineProblem(17, 20.0, 10.0, limiter="kappa", kappa=kappa, splitting="hs1"))
+        hs2 = lr.split_coefficient(lr.LineProblem(17, 20.0, 10.0, limiter="kappa", kappa=kappa, splitting="hs2"))
+        ok = ok and abs(hs1 - beta) <= 1e-15 and abs(hs2 - (beta - alpha)) <= 1e-15
+    return ok
+
+
+def _hybrid_matrix_pin_holds():
+    """The L_hs1 matrix at kappa = 0 against central differences of the residual (see the test)."""
+    N = 33
+    # a low load (M = 1) on a narrow domain keeps eps / h^2 near the size of the Couette terms
+    rough = 0.02 * (-1.0) ** np.arange(N)
+    kw = dict(xa=-0.5, xb=0.5, compressible=False, limiter="minmod", splitting="hs1", kappa=0.0, rough=rough)
+    pb = lr.LineProblem(N, 1.0, 10.0, **kw)
+    P, H0 = np.zeros(pb.n), 0.05
+    d = np.diff(pb.film(P, H0))
+    assert np.all(d[:-1] * d[1:] < 0.0)  # alternating differences: minmod gives psi = 0 at every face
+    J = lr.jacobian_frozen(pb, P, H0)
+    e = 1e-6
+    Jfd = np.zeros_like(J)
+    for k in range(pb.n):
+        dp = np.zeros(pb.n)
+        dp[k] = e
+        Jfd[:, k] = (lr.residual(pb, P + dp, H0) - lr.residual(pb, P - dp, H0)) / (2 * e)
+    # the Couette part is a sizeable share of the matrix (rigid surfaces remove it)
+    pr = lr.LineProblem(N, 1.0, 10.0, elastic=False, **kw)
+    assert np.max(np.abs(lr.jacobian_frozen(pr, P, H0) - J)) > 0.1 * np.max(np.abs(J))
+    return np.max(np.abs(J - Jfd)) <= 1e-7 * np.max(np.abs(Jfd))
+
+
+def test_split_coefficient_is_the_upwind_part_of_the_kappa_stencils():
+    """The hybrid splittings' Couette coefficient (Sec. 3.3.2, Eqs. eqn57-eqn61) from the
+    stencils themselves: a consistent stencil sum_d c_d u_{i+d} is
+    alpha D_{i-1} + beta D_i + gamma D_{i+1} in the differences D_j = u_j - u_{j-1}, with
+    alpha = -c_{-2}, beta = alpha - c_{-1}, gamma = c_{+1}.  L_hs1 keeps the upwind difference
+    beta D_i; L_hs2 also moves the farther upwind difference onto it (D_{i-1} ~ D_i), beta - alpha.
+    The stencils are Eq. eqn42's (kappa = 0) and the textbook second-order upwind, third-order
+    upwind-biased and central differences."""
+    assert _split_coefficient_pin_holds()
+
+
+def test_hybrid_splitting_matrix_is_the_upwind_jacobian():
+    """The Newton matrix of L_hs1 at kappa = 0 (coefficient 1) against central differences of
+    the residual where its pieces are exact: incompressible, P = 0 (the frozen Poiseuille
+    coefficients then carry no error) and a zigzag roughness that puts every limited face on the
+    psi = 0 branch, so the residual's Couette difference is the first-order upwind one."""
+    assert _hybrid_matrix_pin_holds()
+
+
+@pytest.mark.parametrize("slip", ["plus_kappa", "half", "hs2_as_hs1", "sign"])
+def test_splitting_pins_catch_planted_mistakes(monkeypatch, slip):
+    """Each plausible slip in the splitting, planted in the oracle, fails one of the two pins."""
+    good_coef = lr.split_coefficient
+    if slip == "plus_kappa":  # (2 + kappa)/2 for (2 - kappa)/2
+        monkeypatch.setattr(lr, "split_coefficient", lambda pb: None if pb.splitting == "frozen" else
+                            (2.0 + pb.kappa) / 2.0 + (0.0 if pb.splitting == "hs1" else (1.0 - pb.kappa) / 4.0))
+    elif slip == "half":  # the difference's factor 1/2 of the face value applied twice
+        monkeypatch.setattr(lr, "split_coefficient", lambda pb: None if good_coef(pb) is None else 0.5 * good_coef(pb))
+    elif slip == "hs2_as_hs1":  # the moved part with the wrong sign
+        monkeypatch.setattr(lr, "split_coefficient", lambda pb: None if pb.splitting == "frozen" else
+                            (2.0 - pb.kappa) / 2.0 - (0.0 if pb.splitting == "hs1" else (1.0 - pb.kappa) / 4.0))
+    else:  # the difference with its sign flipped
+        monkeypatch.setattr(lr, "split_coefficient", lambda pb: None if good_coef(pb) is None else -good_coef(pb))
+    assert not (_split_coefficient_pin_holds() and _hybrid_matrix_pin_holds())
