@@ -446,8 +446,6 @@ def run_ours(args):
 
 # ------------------------------------------------------------- the other configs
 PRECISION = {0: "Krylov products in double-float (plain path)",
-             2: "Krylov products as float32 cuBLAS GEMMs (BF16x9 emulation requested, SIMT SGEMM kernels "
-                "run), float32 PAQIF preconditioner sweeps in line contact; residual float64",
              5: "Krylov products as the library's TF32x3 tcgen05 GEMM (tensor cores), float32 PAQIF "
                 "preconditioner sweeps; residual float64"}
 
