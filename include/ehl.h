@@ -321,7 +321,12 @@ void ehl_params_default(ehl_params* p, int dim);
  * or > 65536, beta outside 1..8, M <= 0, xb <= xa, ...), EHL_ENOMEM,
  * EHL_ECUDA.  With levels != 0 the context also holds the coarse grids of
  * the nested iteration (nx_l - 1 = (nx - 1) / 2^l while that is an integer
- * and nx_l >= coarse_min_nodes), about as much memory again as the finest. */
+ * and nx_l >= coarse_min_nodes), about as much memory again as the finest.
+ * Two environment variables are read here, for line contact: EHL_TRACE=k
+ * prints one line per Newton step of the first k instances to stderr;
+ * EHL_FUSE=0 runs small instances through the stage kernels instead of the
+ * one-CTA kernels (state for nx <= 256, Krylov step for nx <= 257), which
+ * compute the same stages (to check the two against each other). */
 ehl_status ehl_create(const ehl_params* p, int n_inst, const ehl_params* per_inst, void* stream, ehl_ctx** out);
 
 /* Release the context and its device memory (synchronises its stream). */
