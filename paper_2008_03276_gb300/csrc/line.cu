@@ -499,13 +499,12 @@ struct LineRowCtx {
   }
 };
 
-// kind 0: band of (J_frozen D) with the weighted-change distribution D, cavitated rows -> identity;
-// kind 1: band of the exact Jacobian, rows with P_i <= R_i / |J_ii| -> identity.
-// Also writes dR/dH0 (jh, frozen or exact) and |J_ii| (dg, kind 1) per row.
+// kind 1: band of the exact Jacobian, rows with P_i <= R_i / |J_ii| -> identity (kind 0, the
+// paper's frozen and distributed matrix, is k_line_jac_band0 below).  One thread per row; also
+// writes the exact dR/dH0 (jh) and the row scale (dg) per row.
 __global__ void k_line_jac_band(const LineInst* __restrict__ inst, LineRowCtx c, const double* __restrict__ R,
-                                const int* __restrict__ skip, int kind, int beta, double* __restrict__ band,
-                                uint8_t* __restrict__ act, double* __restrict__ jh, double* __restrict__ dg,
-                                double* __restrict__ rhs_out, int* __restrict__ act32) {
+                                const int* __restrict__ skip, int beta, double* __restrict__ band,
+                                uint8_t* __restrict__ act, double* __restrict__ jh, double* __restrict__ dg) {
   const int z = blockIdx.y;
   if (skip && skip[z]) return;
   const int N = c.N, n = N - 2;
@@ -520,47 +519,23 @@ __global__ void k_line_jac_band(const LineInst* __restrict__ inst, LineRowCtx c,
   const double ef1 = 0.5 * (c.eps[q.base + i] + c.eps[q.base + i + 1]);
   const double ef0 = 0.5 * (c.eps[q.base + i - 1] + c.eps[q.base + i]);
   const double Pi = c.P[q.base + i], Ri = R[q.base + i];
-  bool a;
-  if (kind == 0) {
-    a = (Pi <= 0.0) && (Ri > 0.0);
-    const double w = inst[z].dist_w, sw = inst[z].switch_eps_h;
-    const double cs = line_split_coef(inst[z]);
-    for (int j = 0; j < bw; ++j) {
-      const int col = r - beta + j;  // interior column index, node col + 1
-      double v = 0.0;
-      if (col >= 0 && col < n) {
-        const int m = col + 1;
-        v = q.J_frozen(i, m, ef0, ef1, cs);
-        if (c.eps[q.base + m] / q.h <= sw) {
-          if (m - 1 >= 1) v -= w * q.J_frozen(i, m - 1, ef0, ef1, cs);
-          if (m + 1 <= N - 2) v -= w * q.J_frozen(i, m + 1, ef0, ef1, cs);
-        }
-      }
-      row[j] = a ? (j == beta ? 1.0 : 0.0) : v;
-    }
-    if (jh) jh[(size_t)z * n + r] = a ? 0.0 : q.JH_frozen(i, cs);
-  } else {
-    // row scale d = max(|J_ii|, |J_i|_max / 10) over the band: |J_ii| alone can pass
-    // through zero in the Hertzian zone, where the row is carried by its neighbours
-    double rmax = 0.0, jii = 0.0;
-    q.J_exact_row(i, beta, ef0, ef1, row);
-    for (int j = 0; j < bw; ++j) {
-      const double v = row[j];
-      rmax = fmax(rmax, fabs(v));
-      if (j == beta) jii = v;
-    }
-    double d = fmax(fabs(jii), 0.1 * rmax);
-    d = d > 0.0 ? d : 1.0;
-    a = Pi <= Ri / d;
-    if (a)
-      for (int j = 0; j < bw; ++j) row[j] = (j == beta ? 1.0 : 0.0);
-    if (jh) jh[(size_t)z * n + r] = a ? 0.0 : q.JH_exact(i, ef0, ef1);
-    if (dg) dg[(size_t)z * n + r] = d;
+  // row scale d = max(|J_ii|, |J_i|_max / 10) over the band: |J_ii| alone can pass
+  // through zero in the Hertzian zone, where the row is carried by its neighbours
+  double rmax = 0.0, jii = 0.0;
+  q.J_exact_row(i, beta, ef0, ef1, row);
+  for (int j = 0; j < bw; ++j) {
+    const double v = row[j];
+    rmax = fmax(rmax, fabs(v));
+    if (j == beta) jii = v;
   }
+  double d = fmax(fabs(jii), 0.1 * rmax);
+  d = d > 0.0 ? d : 1.0;
+  const bool a = Pi <= Ri / d;
+  if (a)
+    for (int j = 0; j < bw; ++j) row[j] = (j == beta ? 1.0 : 0.0);
+  if (jh) jh[(size_t)z * n + r] = a ? 0.0 : q.JH_exact(i, ef0, ef1);
+  if (dg) dg[(size_t)z * n + r] = d;
   act[(size_t)z * n + r] = a ? 1 : 0;
-  // the paper iteration's right-hand side and PAQIF's int32 row flags, when asked for
-  if (rhs_out) rhs_out[(size_t)z * n + r] = a ? 0.0 : -Ri;
-  if (act32) act32[(size_t)z * n + r] = a ? 1 : 0;
 }
 
 // kind 0 with one thread per band entry: a row's 2b+1 entries, each with its distributed
@@ -782,7 +757,7 @@ cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, u
     return cudaGetLastError();
   }
   dim3 g((c->n + 127) / 128, c->n_inst);
-  k_line_jac_band<<<g, 128, 0, c->st>>>(c->inst, q, c->R, skip, kind, c->beta, band, act, jh, dg, rhs_out, act32);
+  k_line_jac_band<<<g, 128, 0, c->st>>>(c->inst, q, c->R, skip, c->beta, band, act, jh, dg);
   note_launch();
   return cudaGetLastError();
 }

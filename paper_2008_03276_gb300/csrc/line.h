@@ -80,6 +80,8 @@ cudaError_t line_deform(LineCtx* c, const double* V, int vstride, const int* ski
 cudaError_t line_state(LineCtx* c, const double* P, const double* H0, const double* rough, const int* skip,
                        int* unused);
 cudaError_t line_finalize(LineCtx* c, int* done, int* iters);
+// kind 0 (the paper's matrix) can also write the paper iteration's right-hand side (rhs_out) and
+// PAQIF's int32 row flags (act32); kind 1 (exact) ignores them.
 cudaError_t line_jac_band(LineCtx* c, const double* P, int kind, double* band, uint8_t* act, double* jh,
                           double* dg, const int* skip, double* rhs_out = nullptr, int* act32 = nullptr);
 cudaError_t line_start(LineCtx* c, double* P, double* H0, const double* rough);
