@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_krylov_small(const LineInst* __
                                                               const int* __restrict__ done, int N,
                                                               const int* __restrict__ jd,
                                                               const float2* __restrict__ gtab, JvArgs q,
-                                                              const uint8_t* __restrict__ act,
+                                                              double* dH, const uint8_t* __restrict__ act,
                                                               double* __restrict__ rhs) {
   const int z = blockIdx.x;
   if (done[z] || b.gm_conv[z]) return;
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_krylov_small(const LineInst* __
   const size_t base = (size_t)z * N;
   const double xi = b.zh0[z];
   const bool elastic = inst[z].elastic != 0;
-  double* dH = const_cast<double*>(q.dH);
+  // dH is q.dH (written here, then read by the directional derivative below)
   for (int i = threadIdx.x; i < N; i += kNkBlock) {
     double Dd = 0.0;
     if (elastic) {
@@ -581,8 +581,8 @@ static cudaError_t krylov_step(LineCtx* c, const double* P, int j, const int* jd
   const int ni = c->n_inst, N = c->N;
   JvArgs q{P, c->H, c->rho, c->drho, c->deta_rel, c->eps, c->psia, c->psib, c->dH, b.znode};
   if (krylov_fused(c)) {
-    k_nk_krylov_small<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, c->done, N, jd, c->gtab, q, c->act,
-                                                  c->rhs);
+    k_nk_krylov_small<<<ni, kNkBlock, 0, c->st>>>(c->inst, b, j, c->sigma, c->done, N, jd, c->gtab, q, c->dH,
+                                                  c->act, c->rhs);
     note_launch();
     return cudaGetLastError();
   }
