@@ -88,3 +88,48 @@ def test_residual_decay_with_and_without_y_convection():
     pb = cd.CDProblem(33, kappa=0.0, b=1.0)
     _, hist = cd.line_relaxation(pb, "Ls0", sweeps=6)
     assert hist[-1] > 1e3 * hist[0]
+
+
+GOLDEN_L0 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cd_line_operators.txt")
+
+
+def _line_operator_pin_holds():
+    """Every row of cd_ref.line_matrix against the printed L^0 of Eqs. eqn48 (Ls0) and eqn49 (Ls1)."""
+    ok = True
+    for split, kappa, cm, c0, cp, dm, d0, dp in np.loadtxt(GOLDEN_L0):
+        for a, eps in ((1.0, 1e-6), (0.7, 3e-3)):
+            pb = cd.CDProblem(17, a=a, eps=eps, kappa=kappa)
+            A = cd.line_matrix(pb, "Ls0" if split == 0 else "Ls1")
+            want = [c * a / pb.h + d * eps / pb.h**2 for c, d in ((cm, dm), (c0, d0), (cp, dp))]
+            for i in range(1, A.shape[0] - 1):
+                got = [A[i, i - 1], A[i, i], A[i, i + 1]]
+                ok = ok and all(abs(g - w) <= 1e-12 * max(1.0, abs(w)) for g, w in zip(got, want))
+            ok = ok and abs(A[0, 0] - want[1]) <= 1e-12 * abs(want[1]) and not np.any(np.triu(A, 2))
+    return ok
+
+
+def test_line_operator_is_the_printed_one():
+    """L^0 of the x-line splittings as Sec. 3.1 prints them (Eqs. eqn48, eqn49), at four kappa and
+    two (a, eps): the tridiagonal rows, and nothing beyond the first super-diagonal."""
+    assert _line_operator_pin_holds()
+
+
+@pytest.mark.parametrize("slip", ["ls0_as_ls1", "diffusion_diagonal_2", "kappa_sign"])
+def test_line_operator_pin_catches_planted_mistakes(monkeypatch, slip):
+    """Plausible slips in the splittings' coefficient, planted in the oracle, fail the pin."""
+    good = cd.l0_coefficient
+    if slip == "ls0_as_ls1":
+        monkeypatch.setattr(cd, "l0_coefficient", lambda kappa, s: good(kappa, "Ls1"))
+        assert not _line_operator_pin_holds()
+    elif slip == "kappa_sign":
+        monkeypatch.setattr(cd, "l0_coefficient", lambda kappa, s: good(-kappa, s))
+        assert not _line_operator_pin_holds()
+    else:  # a 1-D diffusion diagonal (2 eps / h^2) in place of the 5-point one
+        real = cd.line_matrix
+
+        def slipped(pb, s):
+            A = real(pb, s)
+            return A - 2.0 * pb.eps / pb.h**2 * np.eye(A.shape[0])
+
+        monkeypatch.setattr(cd, "line_matrix", slipped)
+        assert not _line_operator_pin_holds()
