@@ -341,8 +341,9 @@ __global__ void __launch_bounds__(kNkBlock) k_nk_arnoldi(const LineInst* __restr
 // vector z_j (k_nk_prec), the film's directional derivative dH = -K z + xi in double-float
 // (k_line_deform's chunks of kDefChunk sources, summed as k_line_film sums them), w = J z
 // (k_nk_jv) and the Arnoldi step (k_nk_arnoldi), with block barriers in place of the kernel
-// boundaries.  The same arithmetic in the same order, so the same results bit for bit, in one
-// launch instead of five.
+// boundaries: the same operations in the same order, in one launch instead of five.  Compiled
+// into one kernel they round differently in the last bits (a converged solve agrees with the
+// stage kernels' to about 1e-11).
 constexpr int kNkSmallN = 257;
 constexpr int kDefChunk = 128;  // sources per chunk of k_line_deform
 // (It skips an instance that is done or whose GMRES has converged itself, so no skip kernel

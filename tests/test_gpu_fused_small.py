@@ -6,10 +6,10 @@ at most 257 nodes so does a Krylov step of the Newton-Krylov solve (precondition
 double-float deformation of the film derivative, exact directional derivative, Arnoldi step).
 Both do the multi-kernel stages' operations in the same order.  The one-CTA state agrees with
 the stage kernels (``EHL_FUSE=0``) bit for bit: residual, film and reductions, and so every
-iterate of the paper's iteration, whose linear solve is PAQIF alone.  The one-CTA Krylov step
-differs in the last bits (the compiler contracts some products of the directional derivative
-and the Arnoldi step into FMAs differently when the stages share one kernel), so Newton-Krylov
-solves are compared as two solves to the same tolerance: the same Newton iteration counts, and
+iterate of the paper's iteration, whose linear solve is PAQIF alone.  The one-CTA Krylov step,
+the same operations compiled into one kernel, differs in the last bits (most likely products
+contracted into FMAs differently), so Newton-Krylov solves are compared as two solves to the
+same tolerance: the same Newton iteration counts, and
 converged pressures and H0 within 1e-9 relative (measured on a GB300: at most 3.5e-11, against
 the solve tolerance 1e-8).
 """
